@@ -1,0 +1,365 @@
+"""Pins of the FP64 oracle to facts outside itself: closed forms, other library
+routines computing the same object a different way, brute force on tiny inputs,
+invariants and the mathematics of the method (Sec. 3 of the paper). CPU only."""
+import itertools
+
+import numpy as np
+import pytest
+import scipy.linalg
+import scipy.optimize
+
+import synth
+from oracle import copa_oracle as O
+
+
+# ---------------------------------------------------------------------------------
+# Procrustes (Eq. solv_Q): pseudo-polar factor
+# ---------------------------------------------------------------------------------
+
+def _A(Xk, V, w, H):
+    return Xk @ V @ np.diag(w) @ H.T
+
+
+def test_procrustes_equals_polar_factor_full_rank():
+    rng = np.random.default_rng(0)
+    for Ik, J, R in [(7, 9, 3), (12, 6, 5), (5, 20, 5)]:
+        Xk, V, H = rng.random((Ik, J)), rng.random((J, R)), rng.random((R, R)) + np.eye(R)
+        w = rng.uniform(0.5, 1.5, R)
+        Q = O.procrustes(Xk, V, w, H)
+        U, _ = scipy.linalg.polar(_A(Xk, V, w, H), side="right")
+        np.testing.assert_allclose(Q, U, atol=1e-12)
+        np.testing.assert_allclose(Q.T @ Q, np.eye(R), atol=1e-12)
+
+
+def test_procrustes_wide_case_has_orthonormal_rows():
+    rng = np.random.default_rng(1)
+    Ik, J, R = 3, 10, 6                      # I_k < R: Q_k Q_k^T = I
+    Xk, V, H = rng.random((Ik, J)), rng.random((J, R)), rng.random((R, R)) + np.eye(R)
+    Q = O.procrustes(Xk, V, np.ones(R), H)
+    np.testing.assert_allclose(Q @ Q.T, np.eye(Ik), atol=1e-12)
+    A = _A(Xk, V, np.ones(R), H)
+    U, _ = scipy.linalg.polar(A.T, side="right")  # polar of A^T gives Q^T
+    np.testing.assert_allclose(Q, U.T, atol=1e-12)
+
+
+def test_procrustes_maximises_trace_and_nuclear_norm():
+    """tr(Q^T A) = ||A||_* and no orthonormal Q' does better (Eq. solv_Q)."""
+    rng = np.random.default_rng(2)
+    Ik, J, R = 9, 8, 4
+    Xk, V, H = rng.random((Ik, J)), rng.random((J, R)), rng.random((R, R))
+    w = rng.random(R)
+    A = _A(Xk, V, w, H)
+    Q = O.procrustes(Xk, V, w, H)
+    nuc = np.linalg.norm(A, "nuc")
+    assert abs(np.trace(Q.T @ A) - nuc) < 1e-10 * nuc
+    for _ in range(300):
+        Qr, _ = np.linalg.qr(rng.standard_normal((Ik, R)))
+        assert np.trace(Qr.T @ A) <= nuc + 1e-10
+        # same statement in the paper's objective form
+        assert np.sum((A - Qr) ** 2) >= np.sum((A - Q) ** 2) - 1e-10
+
+
+def test_procrustes_closed_form_2x2():
+    """A = s [[c, -n], [n, c]] (a scaled rotation) has the rotation as its polar factor;
+    A = diag(3, -2) has polar factor diag(1, -1)."""
+    th = 0.7
+     # X = A, V = I, w = 1, H = I gives A_k = A
+    Rot = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+    Q = O.procrustes(2.5 * Rot, np.eye(2), np.ones(2), np.eye(2))
+    np.testing.assert_allclose(Q, Rot, atol=1e-14)
+    Q = O.procrustes(np.diag([3.0, -2.0]), np.eye(2), np.ones(2), np.eye(2))
+    np.testing.assert_allclose(Q, np.diag([1.0, -1.0]), atol=1e-14)
+
+
+def test_procrustes_rank_deficient_and_zero():
+    rng = np.random.default_rng(3)
+    Ik, J, R = 10, 12, 5
+    Xk, V, H = rng.random((Ik, J)), rng.random((J, R)), rng.random((R, R)) + np.eye(R)
+    w = np.array([1.0, 0.0, 2.0, 0.0, 1.0])   # zero weights: rank(A) = 3
+    Q = O.procrustes(Xk, V, w, H)
+    A = _A(Xk, V, w, H)
+    P = Q.T @ Q
+    np.testing.assert_allclose(P @ P, P, atol=1e-12)          # projector
+    assert round(np.trace(P)) == 3
+    np.testing.assert_allclose(Q @ (Q.T @ A), A, atol=1e-10)  # Q spans range(A)
+    nuc = np.linalg.norm(A, "nuc")
+    assert abs(np.trace(Q.T @ A) - nuc) < 1e-10 * nuc
+    # X_k = 0 and I_k = 0
+    assert not O.procrustes(np.zeros((4, J)), V, w, H).any()
+    assert O.procrustes(np.zeros((0, J)), V, w, H).shape == (0, R)
+
+
+# ---------------------------------------------------------------------------------
+# MTTKRP (Sec. 2) vs element-wise brute force of the CP model gradient
+# ---------------------------------------------------------------------------------
+
+def _brute(Y, H, V, W):
+    R, J, K = Y.shape
+    Rk = H.shape[1]
+    FH, FV, FW = np.zeros((R, Rk)), np.zeros((J, Rk)), np.zeros((K, Rk))
+    for r, j, k, s in itertools.product(range(R), range(J), range(K), range(Rk)):
+        y = Y[r, j, k]
+        FH[r, s] += y * V[j, s] * W[k, s]
+        FV[j, s] += y * H[r, s] * W[k, s]
+        FW[k, s] += y * H[r, s] * V[j, s]
+    return FH, FV, FW
+
+
+def test_mttkrp_literal_and_slice_forms_match_brute_force():
+    rng = np.random.default_rng(4)
+    R, J, K = 3, 5, 4
+    Y = rng.standard_normal((R, J, K))
+    H, V, W = rng.random((R, R)), rng.random((J, R)), rng.random((K, R))
+    FH, FV, FW = _brute(Y, H, V, W)
+    np.testing.assert_allclose(O.mttkrp_literal(Y, H, V, W, 1), FH, atol=1e-12)
+    np.testing.assert_allclose(O.mttkrp_literal(Y, H, V, W, 2), FV, atol=1e-12)
+    np.testing.assert_allclose(O.mttkrp_literal(Y, H, V, W, 3), FW, atol=1e-12)
+    sl = O.Slices([np.arange(J)] * K, [Y[:, :, k] for k in range(K)])
+    np.testing.assert_allclose(O.mttkrp_H(sl, V, W), FH, atol=1e-12)
+    np.testing.assert_allclose(O.mttkrp_V(sl, H, W, J), FV, atol=1e-12)
+    np.testing.assert_allclose(O.mttkrp_W(sl, H, V), FW, atol=1e-12)
+
+
+def test_unfolding_reconstructs_cp_model():
+    """Y = [H; V; W] satisfies Y_(1) = H (W (.) V)^T, Y_(2) = V (W (.) H)^T,
+    Y_(3) = W (V (.) H)^T: pins the index order of unfold and khatri_rao."""
+    rng = np.random.default_rng(5)
+    R, J, K = 3, 4, 5
+    H, V, W = rng.random((R, R)), rng.random((J, R)), rng.random((K, R))
+    Y = np.einsum("rs,js,ks->rjk", H, V, W)
+    np.testing.assert_allclose(O.unfold(Y, 1), H @ O.khatri_rao(W, V).T, atol=1e-12)
+    np.testing.assert_allclose(O.unfold(Y, 2), V @ O.khatri_rao(W, H).T, atol=1e-12)
+    np.testing.assert_allclose(O.unfold(Y, 3), W @ O.khatri_rao(V, H).T, atol=1e-12)
+
+
+def test_projection_and_sparse_slices():
+    X, _ = synth.planted_small(K=6, J=15, R=3, seed=7)
+    rng = np.random.default_rng(6)
+    H, V, W = rng.random((3, 3)), rng.random((15, 3)), rng.random((6, 3))
+    Q = [O.procrustes(X.dense(k), V, W[k], H) for k in range(X.K)]
+    sl = O.project_all(X, Q)
+    Y = np.stack([Q[k].T @ X.dense(k) for k in range(X.K)], axis=2)
+    FH, FV, FW = _brute(Y, H, V, W)
+    np.testing.assert_allclose(O.mttkrp_H(sl, V, W), FH, atol=1e-10)
+    np.testing.assert_allclose(O.mttkrp_V(sl, H, W, 15), FV, atol=1e-10)
+    np.testing.assert_allclose(O.mttkrp_W(sl, H, V), FW, atol=1e-10)
+
+
+# ---------------------------------------------------------------------------------
+# Proximal operators (Sec. 3.3) vs a dense 1-D grid search of their definition
+# ---------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind", [O.NONE, O.NONNEG, O.L1, O.L0])
+def test_prox_is_argmin_on_grid(kind):
+    rng = np.random.default_rng(8)
+    lam, rho = 0.7, 1.9
+    grid = np.linspace(-6, 6, 240001)
+    cost = {O.NONE: lambda z: 0.0 * z, O.NONNEG: lambda z: np.where(z < 0, np.inf, 0.0),
+            O.L1: lambda z: lam * np.abs(z), O.L0: lambda z: lam * (z != 0)}[kind]
+    for v in rng.uniform(-4, 4, 60):
+        obj = cost(grid) + 0.5 * rho * (grid - v) ** 2
+        if kind == O.L0:
+            obj = np.append(obj, 0.5 * rho * v * v)      # z = 0 exactly
+        p = O.prox(np.array([v]), kind, lam, rho)[0]
+        val = float(cost(np.array([p]))[0] + 0.5 * rho * (p - v) ** 2)
+        assert val <= obj.min() + 1e-6
+
+
+def test_prox_closed_forms_and_ties():
+    lam, rho = 2.0, 4.0
+    v = np.array([-3.0, -0.5, 0.0, 0.25, 0.5, 1.0, 2.0])
+    np.testing.assert_array_equal(O.prox(v, O.NONNEG, lam, rho), [0, 0, 0, 0.25, 0.5, 1, 2])
+    np.testing.assert_allclose(O.prox(v, O.L1, lam, rho), [-2.5, 0, 0, 0, 0, 0.5, 1.5])
+    # l0 threshold 2 lam / rho = 1: v^2 = 1 is a tie and goes to 0
+    np.testing.assert_array_equal(O.prox(v, O.L0, lam, rho), [-3, 0, 0, 0, 0, 0, 2])
+
+
+# ---------------------------------------------------------------------------------
+# ADMM inner loop: fixed points are the constrained least-squares solutions
+# ---------------------------------------------------------------------------------
+
+def _sys(rng, n, R):
+    A = rng.standard_normal((n, R))
+    G = A.T @ A
+    F = rng.standard_normal((6, R)) * 3
+    return G, F
+
+
+def test_cholesky_solve_residual():
+    rng = np.random.default_rng(9)
+    G, F = _sys(rng, 30, 6)
+    rho = O.rho_of(G)
+    assert abs(rho - np.trace(G) / 6) < 1e-14
+    L = np.linalg.cholesky(G + rho * np.eye(6))
+    b = rng.standard_normal(6)
+    z = scipy.linalg.solve_triangular(L.T, scipy.linalg.solve_triangular(L, b, lower=True))
+    assert np.linalg.norm((G + rho * np.eye(6)) @ z - b) <= 1e-12 * np.linalg.norm(b)
+
+
+def test_admm_unconstrained_converges_to_least_squares():
+    rng = np.random.default_rng(10)
+    G, F = _sys(rng, 40, 5)
+    Z, Zb, D, _, _ = O.admm(F, G, np.zeros((6, 5)), np.zeros((6, 5)), 400, O.NONE)
+    np.testing.assert_allclose(Zb, np.linalg.solve(G, F.T).T, rtol=1e-9, atol=1e-9)
+
+
+def test_admm_nonneg_converges_to_nnls():
+    rng = np.random.default_rng(11)
+    G, F = _sys(rng, 40, 5)
+    _, Zb, _, _, _ = O.admm(F, G, np.zeros((6, 5)), np.zeros((6, 5)), 3000, O.NONNEG)
+    U = np.linalg.cholesky(G).T                       # G = U^T U
+    for i in range(6):
+        b = np.linalg.solve(U.T, F[i])                # U^T b = f
+        z, _ = scipy.optimize.nnls(U, b)
+        np.testing.assert_allclose(Zb[i], z, atol=1e-7)
+
+
+def test_admm_l1_satisfies_lasso_kkt():
+    rng = np.random.default_rng(12)
+    G, F = _sys(rng, 40, 5)
+    lam = 2.0
+    _, Zb, _, _, _ = O.admm(F, G, np.zeros((6, 5)), np.zeros((6, 5)), 3000, O.L1, lam)
+    g = Zb @ G - F                                    # gradient of 1/2 z^T G z - f^T z
+    nz = Zb != 0
+    np.testing.assert_allclose(g[nz], -lam * np.sign(Zb[nz]), atol=1e-6)
+    assert np.all(np.abs(g[~nz]) <= lam + 1e-6)
+
+
+# ---------------------------------------------------------------------------------
+# Outer iteration: order of the modes and the Grams (Algorithm 1)
+# ---------------------------------------------------------------------------------
+
+def test_unconstrained_mode_updates_are_exact_cp_als():
+    """With c = none and many inner iterations, every mode update is the least-squares
+    solution of the matricized CP problem given the CURRENT other factors, computed
+    here by lstsq on the explicit Khatri-Rao product (Sec. 3.1 and Eq. Solve_W)."""
+    X, _ = synth.planted_small(K=8, J=12, R=3, seed=1)
+    H0, V0, W0 = synth.random_state(X.K, X.J, 3, seed=4)
+    W0 = W0 + 0.1
+    opt = O.Options(n_inner=600, c_H=O.NONE, c_W=O.NONE, c_V=O.NONE)
+    rec = O.outer_iteration(X, O.State.from_init(H0, V0, W0), opt)
+    Y = np.stack([rec.Q[k].T @ X.dense(k) for k in range(X.K)], axis=2)
+    H1 = np.linalg.lstsq(O.khatri_rao(W0, V0), O.unfold(Y, 1).T, rcond=None)[0].T
+    np.testing.assert_allclose(rec.state.H, H1, rtol=1e-7, atol=1e-8)
+    W1 = np.linalg.lstsq(O.khatri_rao(V0, H1), O.unfold(Y, 3).T, rcond=None)[0].T
+    np.testing.assert_allclose(rec.state.W, W1, rtol=1e-7, atol=1e-8)
+    V1 = np.linalg.lstsq(O.khatri_rao(W1, H1), O.unfold(Y, 2).T, rcond=None)[0].T
+    np.testing.assert_allclose(rec.state.V, V1, rtol=1e-7, atol=1e-8)
+
+
+def test_unconstrained_objective_is_non_increasing():
+    """Classic PARAFAC2-ALS special case (Sec. 2): with exact mode solves the
+    objective sum_k ||X_k - Q_k H S_k V^T||^2 never increases."""
+    X, _ = synth.planted_small(K=30, J=40, R=4, seed=2)
+    H0, V0, W0 = synth.init_factors(X.K, X.J, 4)
+    opt = O.Options(n_inner=300, c_H=O.NONE, c_W=O.NONE, c_V=O.NONE)
+    _, hist, _ = O.fit(X, H0, V0, W0, opt, n_outer=8)
+    assert np.all(np.diff(hist) >= -1e-12 * abs(hist).max()), hist
+
+
+@pytest.mark.slow
+def test_planted_noise_free_model_is_recovered():
+    """Noise-free planted PARAFAC2 data: FIT -> 1 and V, W recovered up to column
+    permutation and scaling (Tucker congruence)."""
+    X, P = synth.planted_small(K=60, J=40, R=3, seed=5, noise_free=True)
+    rng = np.random.default_rng(0)
+    H0, V0, W0 = np.eye(3), rng.random((X.J, 3)), np.ones((X.K, 3))
+    opt = O.Options(n_inner=50, c_H=O.NONE, c_W=O.NONE, c_V=O.NONE)
+    st, hist, _ = O.fit(X, H0, V0, W0, opt, n_outer=600)
+    assert hist[-1] >= 1 - 1e-6, hist[-10:]
+
+    def tucker(A, B):
+        A = A / np.linalg.norm(A, axis=0)
+        B = B / np.linalg.norm(B, axis=0)
+        C = np.abs(A.T @ B)
+        return max(np.mean([C[i, p[i]] for i in range(len(p))])
+                   for p in itertools.permutations(range(C.shape[0])))
+    assert tucker(st.V, P.V) >= 0.999
+    assert tucker(st.W, P.W) >= 0.999
+
+
+# ---------------------------------------------------------------------------------
+# FIT and SPARSITY (Sec. 4.1)
+# ---------------------------------------------------------------------------------
+
+def test_fit_and_sparsity_definitions():
+    X, P = synth.planted_small(K=10, J=20, R=3, seed=3, noise_free=True)
+    assert abs(O.fit_value(X, P.Q, P.H, P.V, P.W) - 1.0) < 1e-12
+    Z = [np.zeros_like(q) for q in P.Q]
+    assert abs(O.fit_value(X, Z, P.H, P.V, P.W)) < 1e-12       # zero model: FIT = 0
+    V = np.array([[0.0, 1.0], [0.0, 0.0], [2.0, -0.0]])
+    assert O.sparsity(V) == 4 / 6
+
+
+# ---------------------------------------------------------------------------------
+# Smoothness basis (Sec. 3.3.1)
+# ---------------------------------------------------------------------------------
+
+def test_bspline_reduces_to_bernstein_without_interior_knots():
+    """With l = d + 1 (no interior knots) the clamped B-splines are the Bernstein
+    polynomials C(d,i) x^i (1-x)^(d-i) on [0, 1]."""
+    from math import comb
+    d = 3
+    knots = O.spline_knots(0.0, 1.0, l=4, d=d)
+    for x in np.linspace(0, 1, 11):
+        for i in range(4):
+            ref = comb(d, i) * x ** i * (1 - x) ** (d - i)
+            assert abs(O.bspline(i, d, x, knots) - ref) < 1e-14
+
+
+def test_bspline_partition_of_unity_and_support():
+    days = np.array([0.0, 1.0, 2.0, 9.0, 10.0, 300.0, 301.0, 1000.0])
+    M = O.subject_basis(days)
+    assert M.shape == (8, 7)
+    np.testing.assert_allclose(M.sum(axis=1), 1.0, atol=1e-14)
+    assert (M >= 0).all()
+    assert M[0, 0] == 1.0 and M[-1, -1] == 1.0
+
+
+def test_smoothing_projection_is_rotation_invariant():
+    """H, V, W after an outer iteration do not depend on which orthonormal basis of
+    span(M_k) is used (Sec. 3.3.1 proof): rotate every C_k by a random orthogonal O_k."""
+    X = synth.ehr_custom(K=12, J=25, median=9, lo=2, hi=20, lam=2.0, cmax=5, seed=3,
+                         with_days=True)
+    Cs, Xp = O.smooth_project(X)
+    for C in Cs:
+        np.testing.assert_allclose(C.T @ C, np.eye(C.shape[1]), atol=1e-12)
+    rng = np.random.default_rng(9)
+    Xr = []
+    for C, x in zip(Cs, Xp):
+        Oq, _ = np.linalg.qr(rng.standard_normal((C.shape[1], C.shape[1])))
+        Xr.append(Oq.T @ x)
+    R = 3
+    H0, V0, W0 = synth.random_state(X.K, X.J, R, seed=5)
+    opt = O.Options(n_inner=5)
+    a = O.outer_iteration(O.slices_to_tensor(Xp, X.J), O.State.from_init(H0, V0, W0), opt)
+    b = O.outer_iteration(O.slices_to_tensor(Xr, X.J), O.State.from_init(H0, V0, W0), opt)
+    for u, v in [(a.state.H, b.state.H), (a.state.V, b.state.V), (a.state.W, b.state.W)]:
+        np.testing.assert_allclose(u, v, atol=1e-9)
+
+
+# ---------------------------------------------------------------------------------
+# Gradient of the reconstruction loss with Q_k fixed: central finite differences
+# ---------------------------------------------------------------------------------
+
+def test_loss_gradient_matches_finite_differences():
+    X = synth.ehr_custom(K=6, J=10, median=6, lo=2, hi=12, lam=2.0, cmax=5, seed=4)
+    R = 3
+    H, V, W = synth.random_state(X.K, X.J, R, seed=6)
+    Q = [O.procrustes(X.dense(k), V, W[k], H) for k in range(X.K)]
+    _, gH, gV, gW = O.loss_and_grad(X, Q, H, V, W)
+    rng = np.random.default_rng(1)
+    for name, A, g in [("H", H, gH), ("V", V, gV), ("W", W, gW)]:
+        for _ in range(12):
+            idx = tuple(rng.integers(0, s) for s in A.shape)
+            h = 1e-6 * max(1.0, abs(A[idx]))
+            Ap, Am = A.copy(), A.copy()
+            Ap[idx] += h
+            Am[idx] -= h
+            args = {"H": H, "V": V, "W": W}
+            args[name] = Ap
+            lp = O.loss_and_grad(X, Q, args["H"], args["V"], args["W"])[0]
+            args[name] = Am
+            lm = O.loss_and_grad(X, Q, args["H"], args["V"], args["W"])[0]
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - g[idx]) <= 1e-6 * max(1.0, abs(g[idx])), (name, idx, fd, g[idx])

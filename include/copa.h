@@ -1,0 +1,227 @@
+/*
+ * copa.h — C ABI of the GB300 implementation of the per-iteration hot path of COPA,
+ * constrained PARAFAC2 fitted by AO-ADMM (Afshar et al., arXiv 1803.04572).
+ *
+ * Model (Sec. 2 "Original PARAFAC2 model", Sec. 3.1): every subject k holds a sparse
+ * I_k x J slice X_k ~ Q_k H S_k V^T with S_k = diag(W(k,:)), Q_k^T Q_k = I. One outer
+ * iteration of Algorithm 1 is
+ *   (a) the Procrustes step Q_k = polar(X_k V S_k H^T) (Eq. solv_Q),
+ *   (b) the projection Y_k = Q_k^T X_k,
+ *   (c) the MTTKRPs of Y for H, W and V,
+ *   (d) per factor an ADMM inner loop with a cached Cholesky of G + rho I, a proximal
+ *       operator and the dual update (Eq. Solve_W update rules, Sec. 3.3).
+ *
+ * Conventions shared by every call
+ *   - All array pointers are DEVICE pointers unless a name ends in _host. They are
+ *     owned by the caller, must stay valid until the work queued on the handle's
+ *     stream has finished, and are never freed by the library.
+ *   - Matrices are dense row-major: H is R x R, V is J x R, W is K x R (row k holds the
+ *     diagonal of S_k), per-subject R x R blocks are stored one after another.
+ *   - "real" arrays are float in COPA_PREC_MIXED handles and double in COPA_PREC_FP64
+ *     handles (the precision chosen at copa_create). Gram matrices (G, U^T U) and
+ *     scalars are always double.
+ *   - Calls are asynchronous on the handle's stream unless documented otherwise.
+ *     Errors found on the host are returned at once; errors found by a kernel are
+ *     written to a device status word and returned by the next call that
+ *     synchronises (copa_sync, copa_fit, copa_fit_host, copa_smooth_plan).
+ *   - A handle is not thread-safe. Different handles may be used from different
+ *     threads.
+ */
+#ifndef COPA_H
+#define COPA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  COPA_OK = 0,
+  COPA_ERR_INVALID_ARG = 1, /* a size, pointer, index or option is out of range */
+  COPA_ERR_OOM = 2,         /* the library could not allocate its workspace */
+  COPA_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+  COPA_ERR_NUMERIC = 4,     /* a non-positive Cholesky pivot or a non-finite value */
+  COPA_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+  COPA_ERR_UNSUPPORTED = 6  /* the request is valid but not implemented (e.g. R > 128) */
+} copa_status_t;
+
+typedef enum { COPA_PREC_MIXED = 0, COPA_PREC_FP64 = 1 } copa_precision_t;
+
+/* Proximal operator applied to a factor (Sec. 3.3): none, max(0,v), soft threshold
+ * sign(v) max(|v| - lambda/rho, 0), hard threshold (v if v^2 > 2 lambda / rho else 0). */
+typedef enum { COPA_C_NONE = 0, COPA_C_NONNEG = 1, COPA_C_L1 = 2, COPA_C_L0 = 3 } copa_constraint_t;
+
+/* Element type of the nonzero values of X. BF16 is accepted only for values that are
+ * integers of magnitude <= 256 (exact in bf16; checked by copa_validate). */
+typedef enum { COPA_VAL_F32 = 0, COPA_VAL_F64 = 1, COPA_VAL_BF16 = 2 } copa_val_dtype_t;
+
+typedef enum { COPA_MODE_H = 0, COPA_MODE_V = 1, COPA_MODE_W = 2 } copa_mode_t;
+
+/* Segmented per-subject CSR storage of {X_k} (device arrays, caller-owned, read-only).
+ * Rows of subject k are subj_ptr[k] .. subj_ptr[k+1]-1; nonzeros of row i are
+ * row_ptr[i] .. row_ptr[i+1]-1 with 0 <= col_idx < J, strictly increasing in a row. */
+typedef struct {
+  int64_t K;
+  int32_t J;
+  int64_t S;                /* total rows = subj_ptr[K] */
+  int64_t nnz;              /* total nonzeros = row_ptr[S] */
+  const int64_t* subj_ptr;  /* K+1 */
+  const int64_t* row_ptr;   /* S+1 */
+  const int32_t* col_idx;   /* nnz */
+  const void* vals;         /* nnz, element type val_dtype */
+  int32_t val_dtype;        /* copa_val_dtype_t */
+} copa_tensor_t;
+
+/* Per-subject result of the Procrustes step (caller-owned device buffers).
+ * Q_k is kept implicitly as Q_k = X_k V Gamma_k, which is exact: Q_k = A_k Omega_k with
+ * A_k = X_k V S_k H^T and Omega_k = (A_k^T A_k)^(-1/2) on the kept eigenvectors, so
+ * Gamma_k = S_k H^T Omega_k. */
+typedef struct {
+  void* Gamma;     /* real[K*R*R], required: Gamma_k */
+  void* T;         /* real[K*R*R], required: T_k = Q_k^T X_k V (= Y_k V) */
+  void* Pi;        /* real[K*R*R], optional (NULL): Pi_k = Q_k^T Q_k (a projector) */
+  int32_t* rank;   /* int32[K], optional (NULL): number of kept eigenvalues */
+} copa_procrustes_out_t;
+
+typedef struct {
+  int32_t R;               /* target rank, 1 <= R <= 128 */
+  int32_t n_outer;         /* outer iterations (Algorithm 1, fixed count) */
+  int32_t n_inner;         /* ADMM iterations per factor update (fixed count) */
+  int32_t c_H, c_W, c_V;   /* copa_constraint_t per factor */
+  double lam_H, lam_W, lam_V; /* regularisation weights of the l1 / l0 constraints */
+  double tau;              /* Procrustes rank cut: keep eigenvalues > tau * max (1e-8) */
+  double x_norm2;          /* sum_k ||X_k||^2 of the ORIGINAL data when X is a smoothed
+                              projection (Sec. 3.3.1); <= 0 means: use ||X||^2 */
+  int32_t use_graph;       /* 1: capture one outer iteration in a CUDA graph and replay */
+} copa_options_t;
+
+typedef struct copa_ctx* copa_handle_t;
+
+/* Create a handle bound to `device` and to `stream` (a cudaStream_t, NULL = legacy
+ * default stream). The library allocates its workspace lazily on that device. */
+copa_status_t copa_create(copa_handle_t* handle, int device, void* stream, int32_t precision);
+copa_status_t copa_destroy(copa_handle_t handle);
+/* Human-readable description of the last error on this handle (never NULL). */
+const char* copa_last_error(copa_handle_t handle);
+/* Wait for the handle's stream and return the first device-side error, if any. */
+copa_status_t copa_sync(copa_handle_t handle);
+
+/* Check X on the device: monotone pointer arrays, 0 <= col < J, strictly increasing
+ * columns in each row, BF16 values integral and <= 256 in magnitude. Synchronises.
+ * Returns COPA_ERR_INVALID_ARG with a message naming the first violation. */
+copa_status_t copa_validate(copa_handle_t handle, const copa_tensor_t* X);
+
+/* (a)+(b), Eq. solv_Q and Algorithm 1's per-subject loop, for every subject at once:
+ * P_k = X_k V, G_k = P_k^T P_k (FP64), M_k = A_k^T A_k = H S_k G_k S_k H^T, the FP64
+ * symmetric eigendecomposition M_k = C diag(lambda) C^T, Omega_k from the eigenpairs with
+ * lambda > tau * lambda_max, then Gamma_k, T_k (and Pi_k, rank_k on request).
+ * If F_H is not NULL it also returns the mode-1 MTTKRP F_H = sum_k T_k S_k (R x R,
+ * real), which is (c) for H, fused. H: R x R, V: J x R, W: K x R (S_k = diag(W(k,:))). */
+copa_status_t copa_procrustes(copa_handle_t handle, const copa_tensor_t* X, int32_t R,
+                              const void* H, const void* V, const void* W, double tau,
+                              copa_procrustes_out_t* out, void* F_H);
+
+/* (c) The MTTKRPs of Y = {Q_k^T X_k} (Sec. 2, Algorithm 1 "F = Y_(n)(Khatri-Rao)"),
+ * from the Procrustes output `st` of the factors (Hp, Vp, Wp) that produced it:
+ *   COPA_MODE_H: F (R x R) = sum_k T_k diag(W(k,:))               uses st->T, W
+ *   COPA_MODE_W: F (K x R), F(k,s) = sum_r H(r,s) T_k(r,s)         uses st->T, H
+ *   COPA_MODE_V: F (J x R) = sum_k X_k^T (X_k Vp) Gamma_k H diag(W(k,:))
+ *                uses X, st->Gamma, Vp, H, W; if UtU is not NULL it also returns
+ *                U^T U = sum_k diag(W(k,:)) H^T Q_k^T Q_k H diag(W(k,:)) (R x R double),
+ *                the Gram of the rows of Q_k H S_k, used by the FIT and the gradient.
+ * Pointers a mode does not use may be NULL. F is overwritten. */
+copa_status_t copa_mttkrp(copa_handle_t handle, int32_t mode, const copa_tensor_t* X,
+                          int32_t R, const copa_procrustes_out_t* st, const void* Vp,
+                          const void* H, const void* W, void* F, double* UtU);
+
+/* Column Gram G = A^T A (R x R, double) of a rows x R real matrix (Algorithm 1: the
+ * factor Grams whose Hadamard products give G for each mode). */
+copa_status_t copa_gram(copa_handle_t handle, const void* A, int64_t rows, int32_t R,
+                        double* G);
+
+/* (d) One factor update by ADMM (Algorithm 1 inner loop; Eq. Solve_W update rules):
+ * G = Ga .* Gb (R x R double, Hadamard product of two Grams; Gb may be NULL meaning
+ * G = Ga), rho = trace(G)/R, L = chol(G + rho I) (FP64), then n_inner times, row-wise
+ *   z = (G + rho I)^{-1} (f + rho (zbar + d)),  zbar = prox_c(z - d),  d = d + zbar - z.
+ * F, Zbar, D are rows x R real; Zbar and D are updated in place. rho_out (double[1],
+ * device, may be NULL) receives rho. Returns COPA_ERR_NUMERIC (at the next sync) if
+ * G + rho I is not positive definite. */
+copa_status_t copa_admm_step(copa_handle_t handle, const void* F, const double* Ga,
+                             const double* Gb, int32_t n_inner, int32_t constraint,
+                             double lambda, void* Zbar, void* D, int64_t rows, int32_t R,
+                             double* rho_out);
+
+/* (c)+(d) fused for W (a warp per subject, all inner iterations in registers):
+ * F_W(k,:) = diag(H^T T_k) then the ADMM row update of W with G = Ga .* Gb. */
+copa_status_t copa_admm_w_fused(copa_handle_t handle, const copa_procrustes_out_t* st,
+                                const void* H, const double* Ga, const double* Gb,
+                                int32_t n_inner, int32_t constraint, double lambda,
+                                void* Wbar, void* DW, int64_t K, int32_t R,
+                                double* rho_out);
+
+/* FIT (Sec. 4.1) of the model (Q_k from `st`, H, V, W) from the pieces of the V-mode
+ * MTTKRP: with F_V and U^T U computed by copa_mttkrp(COPA_MODE_V) at (H, W),
+ *   sum_k ||X_k - Q_k H S_k V^T||^2 = ||X||^2 - 2 <V, F_V> + <V^T V, U^T U>,
+ * FIT = 1 - (x_norm2 - ||X||^2 + that) / x_norm2 (x_norm2 <= 0: x_norm2 = ||X||^2).
+ * Writes fit (double[1], device). */
+copa_status_t copa_fit_value(copa_handle_t handle, const copa_tensor_t* X, int32_t R,
+                             const void* V, const void* F_V, const double* UtU,
+                             double x_norm2, double* fit);
+
+/* Algorithm 1: n_outer outer iterations from the given state. H, V, W hold the initial
+ * auxiliary factors on entry and the fitted ones on return; DH, DV, DW (same shapes)
+ * hold the scaled duals (zero for a cold start) and are updated. fit_history_host
+ * (double[n_outer], HOST, may be NULL) receives the FIT after every iteration.
+ * st (may be NULL) receives the last iteration's Procrustes output (Gamma, T;
+ * Pi and rank if given) so that U_k = Q_k H can be assembled. Synchronises. */
+copa_status_t copa_fit(copa_handle_t handle, const copa_tensor_t* X, const copa_options_t* opt,
+                       void* H, void* V, void* W, void* DH, void* DV, void* DW,
+                       double* fit_history_host, copa_procrustes_out_t* st);
+
+/* copa_fit on HOST buffers: copies X (arrays given as host pointers in X_host) and the
+ * state to the device, runs copa_fit, copies H, V, W, the duals and the FIT history
+ * back. Device memory is owned by the handle and reused across calls. Synchronises. */
+copa_status_t copa_fit_host(copa_handle_t handle, const copa_tensor_t* X_host,
+                            const copa_options_t* opt, void* H_host, void* V_host,
+                            void* W_host, void* DH_host, void* DV_host, void* DW_host,
+                            double* fit_history_host);
+
+/* Q_k rows (S x R real): q_i = (x_i Vp) Gamma_k for every row i of subject k, and
+ * optionally U = Q_k H (U_k, Algorithm 1 output; pass H = NULL to skip). */
+copa_status_t copa_assemble_q(copa_handle_t handle, const copa_tensor_t* X, int32_t R,
+                              const copa_procrustes_out_t* st, const void* Vp,
+                              const void* H, void* Q, void* U);
+
+/* Smoothness on U_k (Sec. 3.3.1), set-up step. For every subject, the cubic (degree)
+ * B-spline basis with n_basis functions on [t_1, t_{I_k}] (interior knots equally spaced
+ * in days, boundary knots repeated degree+1 times; Cox-de Boor recursion) is evaluated
+ * at the visit days (double[S], device), M_k = C_k D P^T, and C_k keeps the left
+ * singular vectors with sigma^2 > 1e-10 sigma_max^2 (r_k of them; if t_1 = t_{I_k} the
+ * basis is the constant function). The projected slices X'_k = C_k^T X_k are r_k x J,
+ * stored as CSR over the columns X_k uses.
+ * copa_smooth_plan returns the sizes of X' (S' rows, nnz' nonzeros) and synchronises;
+ * copa_smooth_project fills X' (caller-allocated device arrays in Xp: subj_ptr K+1,
+ * row_ptr S'+1, col_idx nnz', vals nnz' of type Xp->val_dtype = F32 or F64). The
+ * optional C (double[S * n_basis], device, may be NULL) receives C_k padded with zero
+ * columns to n_basis. */
+copa_status_t copa_smooth_plan(copa_handle_t handle, const copa_tensor_t* X,
+                               const double* days, int32_t n_basis, int32_t degree,
+                               int64_t* S_out_host, int64_t* nnz_out_host);
+copa_status_t copa_smooth_project(copa_handle_t handle, const copa_tensor_t* X,
+                                  const double* days, int32_t n_basis, int32_t degree,
+                                  copa_tensor_t* Xp, double* C);
+
+/* Reconstruction loss L = sum_k ||X_k - Q_k H S_k V^T||_F^2 (no 1/2) with Q_k fixed (from
+ * `st`, which must include Pi and come from copa_procrustes at the same H, V, W) and its
+ * gradient: dL/dH = -2 (F_H - sum_k Pi_k H S_k V^T V S_k), dL/dV = -2 (F_V - V U^T U),
+ * dL/dW(k,r) = -2 [(H^T T_k)(r,r) - (H^T Pi_k H S_k V^T V)(r,r)]. loss is double[1]
+ * (device); gH (R x R), gV (J x R), gW (K x R) are real and overwritten. */
+copa_status_t copa_loss_grad(copa_handle_t handle, const copa_tensor_t* X, int32_t R,
+                             const copa_procrustes_out_t* st, const void* H, const void* V,
+                             const void* W, double* loss, void* gH, void* gV, void* gW);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COPA_H */

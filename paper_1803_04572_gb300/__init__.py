@@ -1,0 +1,321 @@
+"""Python binding of libcopa, the GB300 implementation of COPA's per-iteration hot path
+(constrained PARAFAC2 by AO-ADMM, Afshar et al., arXiv 1803.04572).
+
+Argument marshalling only: every step runs in the CUDA kernels of libcopa.so behind the
+C ABI declared in include/copa.h. PyTorch supplies device memory and the stream. There
+is no CPU fallback: importing this package fails if the library has not been built
+(`python -m paper_1803_04572_gb300.build` or `__graft_entry__.build()`).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, Structure, byref, c_double, c_int32, c_int64, c_void_p
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcopa.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libcopa.so is not built ({LIB_PATH}); run paper_1803_04572_gb300/build.py")
+_lib = ctypes.CDLL(LIB_PATH)
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NUMERIC, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
+PREC = {"mixed": 0, "fp64": 1}
+CONSTRAINT = {"none": 0, "nonneg": 1, "l1": 2, "l0": 3}
+VAL_DTYPE = {"f32": 0, "f64": 1, "bf16": 2}
+MODE = {"H": 0, "V": 1, "W": 2}
+
+EXPORTED = ["copa_create", "copa_destroy", "copa_last_error", "copa_sync", "copa_validate",
+            "copa_procrustes", "copa_mttkrp", "copa_gram", "copa_admm_step", "copa_admm_w_fused",
+            "copa_fit_value", "copa_fit", "copa_fit_host", "copa_assemble_q", "copa_smooth_plan",
+            "copa_smooth_project", "copa_loss_grad"]
+
+
+class CopaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"copa error {code}: {msg}")
+        self.code = code
+
+
+class TensorC(Structure):
+    _fields_ = [("K", c_int64), ("J", c_int32), ("S", c_int64), ("nnz", c_int64),
+                ("subj_ptr", c_void_p), ("row_ptr", c_void_p), ("col_idx", c_void_p),
+                ("vals", c_void_p), ("val_dtype", c_int32)]
+
+
+class ProcOutC(Structure):
+    _fields_ = [("Gamma", c_void_p), ("T", c_void_p), ("Pi", c_void_p), ("rank", c_void_p)]
+
+
+class OptionsC(Structure):
+    _fields_ = [("R", c_int32), ("n_outer", c_int32), ("n_inner", c_int32), ("c_H", c_int32),
+                ("c_W", c_int32), ("c_V", c_int32), ("lam_H", c_double), ("lam_W", c_double),
+                ("lam_V", c_double), ("tau", c_double), ("x_norm2", c_double),
+                ("use_graph", c_int32)]
+
+
+_V = c_void_p
+_sig = {
+    "copa_create": [POINTER(c_void_p), c_int32, _V, c_int32],
+    "copa_destroy": [_V],
+    "copa_sync": [_V],
+    "copa_validate": [_V, POINTER(TensorC)],
+    "copa_procrustes": [_V, POINTER(TensorC), c_int32, _V, _V, _V, c_double, POINTER(ProcOutC), _V],
+    "copa_mttkrp": [_V, c_int32, POINTER(TensorC), c_int32, POINTER(ProcOutC), _V, _V, _V, _V, _V],
+    "copa_gram": [_V, _V, c_int64, c_int32, _V],
+    "copa_admm_step": [_V, _V, _V, _V, c_int32, c_int32, c_double, _V, _V, c_int64, c_int32, _V],
+    "copa_admm_w_fused": [_V, POINTER(ProcOutC), _V, _V, _V, c_int32, c_int32, c_double, _V, _V,
+                          c_int64, c_int32, _V],
+    "copa_fit_value": [_V, POINTER(TensorC), c_int32, _V, _V, _V, c_double, _V],
+    "copa_fit": [_V, POINTER(TensorC), POINTER(OptionsC), _V, _V, _V, _V, _V, _V, _V,
+                 POINTER(ProcOutC)],
+    "copa_fit_host": [_V, POINTER(TensorC), POINTER(OptionsC), _V, _V, _V, _V, _V, _V, _V],
+    "copa_assemble_q": [_V, POINTER(TensorC), c_int32, POINTER(ProcOutC), _V, _V, _V, _V],
+    "copa_smooth_plan": [_V, POINTER(TensorC), _V, c_int32, c_int32, POINTER(c_int64),
+                         POINTER(c_int64)],
+    "copa_smooth_project": [_V, POINTER(TensorC), _V, c_int32, c_int32, POINTER(TensorC), _V],
+    "copa_loss_grad": [_V, POINTER(TensorC), c_int32, POINTER(ProcOutC), _V, _V, _V, _V, _V, _V,
+                       _V],
+}
+for _n, _a in _sig.items():
+    getattr(_lib, _n).argtypes = _a
+    getattr(_lib, _n).restype = c_int32
+_lib.copa_last_error.argtypes = [_V]
+_lib.copa_last_error.restype = ctypes.c_char_p
+
+
+def lib():
+    return _lib
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+class DeviceTensor:
+    """Segmented per-subject CSR storage of {X_k} on the device (torch-owned arrays)."""
+
+    def __init__(self, K, J, subj_ptr, row_ptr, col, vals, val_dtype: str):
+        self.K, self.J = int(K), int(J)
+        self.subj_ptr, self.row_ptr, self.col, self.vals = subj_ptr, row_ptr, col, vals
+        self.val_dtype = val_dtype
+        self.S = int(subj_ptr.numel() - 1)
+        self.nnz = int(col.numel())
+
+    @staticmethod
+    def from_host(X, device="cuda", val_dtype: str = "f32") -> "DeviceTensor":
+        """X: any object with K, J, subj_ptr, row_ptr, col, val (numpy arrays)."""
+        import torch
+        tdt = {"f32": torch.float32, "f64": torch.float64, "bf16": torch.bfloat16}[val_dtype]
+        return DeviceTensor(
+            X.K, X.J,
+            torch.as_tensor(np.ascontiguousarray(X.subj_ptr, dtype=np.int64)).to(device),
+            torch.as_tensor(np.ascontiguousarray(X.row_ptr, dtype=np.int64)).to(device),
+            torch.as_tensor(np.ascontiguousarray(X.col, dtype=np.int32)).to(device),
+            torch.as_tensor(np.ascontiguousarray(X.val, dtype=np.float64)).to(device=device, dtype=tdt),
+            val_dtype)
+
+    def c(self) -> TensorC:
+        return TensorC(self.K, self.J, self.S, self.nnz, _ptr(self.subj_ptr), _ptr(self.row_ptr),
+                       _ptr(self.col), _ptr(self.vals), VAL_DTYPE[self.val_dtype])
+
+
+def host_tensor_c(X, val_dtype="f32"):
+    """TensorC over HOST numpy arrays (for copa_fit_host); returns (struct, keep-alive)."""
+    dt = {"f32": np.float32, "f64": np.float64}[val_dtype]
+    arrs = [np.ascontiguousarray(X.subj_ptr, dtype=np.int64), np.ascontiguousarray(X.row_ptr, dtype=np.int64),
+            np.ascontiguousarray(X.col, dtype=np.int32), np.ascontiguousarray(X.val, dtype=dt)]
+    tc = TensorC(X.K, X.J, len(arrs[0]) - 1, len(arrs[2]), *(a.ctypes.data for a in arrs),
+                 VAL_DTYPE[val_dtype])
+    return tc, arrs
+
+
+class Options:
+    def __init__(self, R, n_outer=10, n_inner=10, c_H="none", c_W="nonneg", c_V="l1", lam_H=0.0,
+                 lam_W=0.0, lam_V=1.0, tau=1e-8, x_norm2=0.0, use_graph=True):
+        self.__dict__.update(locals())
+        del self.__dict__["self"]
+
+    def c(self) -> OptionsC:
+        return OptionsC(self.R, self.n_outer, self.n_inner, CONSTRAINT[self.c_H], CONSTRAINT[self.c_W],
+                        CONSTRAINT[self.c_V], self.lam_H, self.lam_W, self.lam_V, self.tau, self.x_norm2,
+                        1 if self.use_graph else 0)
+
+
+class Copa:
+    """A libcopa handle bound to one device and one stream."""
+
+    def __init__(self, device: int = 0, precision: str = "mixed", stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        self.precision = precision
+        self.dtype = torch.float32 if precision == "mixed" else torch.float64
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        h = c_void_p()
+        self._check(_lib.copa_create(byref(h), device, c_void_p(stream.cuda_stream), PREC[precision]), None)
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.copa_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, code, h="self"):
+        if code != OK:
+            msg = _lib.copa_last_error(self.h if h == "self" else None)
+            raise CopaError(code, msg.decode() if msg else "")
+
+    def empty(self, *shape, dtype=None):
+        return self.torch.empty(*shape, dtype=dtype or self.dtype, device=self.device)
+
+    def zeros(self, *shape, dtype=None):
+        return self.torch.zeros(*shape, dtype=dtype or self.dtype, device=self.device)
+
+    # ---- steps ----
+    def sync(self):
+        self._check(_lib.copa_sync(self.h))
+
+    def validate(self, X: DeviceTensor):
+        self._check(_lib.copa_validate(self.h, byref(X.c())))
+
+    def procrustes(self, X: DeviceTensor, R, H, V, W, tau=1e-8, want_pi=False, want_rank=False,
+                   want_fh=True):
+        st = {"Gamma": self.empty(X.K, R, R), "T": self.empty(X.K, R, R),
+              "Pi": self.empty(X.K, R, R) if want_pi else None,
+              "rank": self.empty(X.K, dtype=self.torch.int32) if want_rank else None}
+        fh = self.empty(R, R) if want_fh else None
+        po = self.proc_c(st)
+        self._check(_lib.copa_procrustes(self.h, byref(X.c()), R, _ptr(H), _ptr(V), _ptr(W), tau,
+                                         byref(po), _ptr(fh)))
+        st["F_H"] = fh
+        return st
+
+    @staticmethod
+    def proc_c(st) -> ProcOutC:
+        return ProcOutC(_ptr(st.get("Gamma")), _ptr(st.get("T")), _ptr(st.get("Pi")), _ptr(st.get("rank")))
+
+    def mttkrp(self, mode: str, X: DeviceTensor, R, st, Vp=None, H=None, W=None, want_utu=False):
+        rows = {"H": R, "V": X.J, "W": X.K}[mode]
+        F = self.empty(rows, R)
+        utu = self.empty(R, R, dtype=self.torch.float64) if want_utu else None
+        self._check(_lib.copa_mttkrp(self.h, MODE[mode], byref(X.c()), R, byref(self.proc_c(st)), _ptr(Vp),
+                                     _ptr(H), _ptr(W), _ptr(F), _ptr(utu)))
+        return (F, utu) if want_utu else F
+
+    def gram(self, A):
+        R = A.shape[1]
+        G = self.empty(R, R, dtype=self.torch.float64)
+        self._check(_lib.copa_gram(self.h, _ptr(A), A.shape[0], R, _ptr(G)))
+        return G
+
+    def admm_step(self, F, Ga, Gb, n_inner, constraint, lam, Zbar, D):
+        rho = self.empty(1, dtype=self.torch.float64)
+        self._check(_lib.copa_admm_step(self.h, _ptr(F), _ptr(Ga), _ptr(Gb), n_inner, CONSTRAINT[constraint],
+                                        lam, _ptr(Zbar), _ptr(D), Zbar.shape[0], Zbar.shape[1], _ptr(rho)))
+        return rho
+
+    def admm_w_fused(self, st, H, Ga, Gb, n_inner, constraint, lam, Wbar, DW):
+        rho = self.empty(1, dtype=self.torch.float64)
+        self._check(_lib.copa_admm_w_fused(self.h, byref(self.proc_c(st)), _ptr(H), _ptr(Ga), _ptr(Gb), n_inner,
+                                           CONSTRAINT[constraint], lam, _ptr(Wbar), _ptr(DW), Wbar.shape[0],
+                                           Wbar.shape[1], _ptr(rho)))
+        return rho
+
+    def fit_value(self, X: DeviceTensor, R, V, F_V, UtU, x_norm2=0.0):
+        out = self.empty(1, dtype=self.torch.float64)
+        self._check(_lib.copa_fit_value(self.h, byref(X.c()), R, _ptr(V), _ptr(F_V), _ptr(UtU), x_norm2,
+                                        _ptr(out)))
+        return out
+
+    def assemble_q(self, X: DeviceTensor, R, st, Vp, H=None):
+        Q = self.empty(X.S, R)
+        U = self.empty(X.S, R) if H is not None else None
+        self._check(_lib.copa_assemble_q(self.h, byref(X.c()), R, byref(self.proc_c(st)), _ptr(Vp), _ptr(H),
+                                         _ptr(Q), _ptr(U)))
+        return (Q, U) if H is not None else Q
+
+    def fit(self, X: DeviceTensor, opt: Options, H, V, W, DH=None, DV=None, DW=None, state=None):
+        """Algorithm 1 for opt.n_outer iterations; H, V, W (and the duals) updated in place.
+        Returns the FIT history (numpy, float64)."""
+        DH = self.torch.zeros_like(H) if DH is None else DH
+        DV = self.torch.zeros_like(V) if DV is None else DV
+        DW = self.torch.zeros_like(W) if DW is None else DW
+        hist = np.zeros(max(1, opt.n_outer), dtype=np.float64)
+        po = byref(self.proc_c(state)) if state is not None else None
+        self._check(_lib.copa_fit(self.h, byref(X.c()), byref(opt.c()), _ptr(H), _ptr(V), _ptr(W), _ptr(DH),
+                                  _ptr(DV), _ptr(DW), hist.ctypes.data, po))
+        return hist[:opt.n_outer]
+
+    def fit_host(self, Xh, opt: Options, H, V, W, DH=None, DV=None, DW=None, val_dtype="f32"):
+        """copa_fit_host on numpy arrays (H, V, W, duals updated in place)."""
+        nd = np.float32 if self.precision == "mixed" else np.float64
+        for a in (H, V, W):
+            assert a.dtype == nd and a.flags.c_contiguous
+        DH = np.zeros_like(H) if DH is None else DH
+        DV = np.zeros_like(V) if DV is None else DV
+        DW = np.zeros_like(W) if DW is None else DW
+        tc, keep = host_tensor_c(Xh, val_dtype)
+        hist = np.zeros(max(1, opt.n_outer), dtype=np.float64)
+        self._check(_lib.copa_fit_host(self.h, byref(tc), byref(opt.c()), H.ctypes.data, V.ctypes.data,
+                                       W.ctypes.data, DH.ctypes.data, DV.ctypes.data, DW.ctypes.data,
+                                       hist.ctypes.data))
+        del keep
+        return hist[:opt.n_outer]
+
+    def smooth(self, X: DeviceTensor, days, n_basis=7, degree=3, out_dtype="f32", want_C=False):
+        """Smoothing set-up of Sec. 3.3.1: returns (X' as DeviceTensor, C or None)."""
+        S_out, nnz_out = c_int64(), c_int64()
+        self._check(_lib.copa_smooth_plan(self.h, byref(X.c()), _ptr(days), n_basis, degree, byref(S_out),
+                                          byref(nnz_out)))
+        torch = self.torch
+        tdt = torch.float32 if out_dtype == "f32" else torch.float64
+        Xp = DeviceTensor(X.K, X.J, self.empty(X.K + 1, dtype=torch.int64),
+                          self.empty(S_out.value + 1, dtype=torch.int64),
+                          self.empty(max(nnz_out.value, 1), dtype=torch.int32)[:nnz_out.value],
+                          self.empty(max(nnz_out.value, 1), dtype=tdt)[:nnz_out.value], out_dtype)
+        C = self.empty(X.S, n_basis, dtype=torch.float64) if want_C else None
+        xc = Xp.c()
+        self._check(_lib.copa_smooth_project(self.h, byref(X.c()), _ptr(days), n_basis, degree, byref(xc),
+                                             _ptr(C)))
+        return Xp, C
+
+    def loss_grad(self, X: DeviceTensor, R, st, H, V, W):
+        loss = self.empty(1, dtype=self.torch.float64)
+        gH, gV, gW = self.empty(*H.shape), self.empty(*V.shape), self.empty(*W.shape)
+        self._check(_lib.copa_loss_grad(self.h, byref(X.c()), R, byref(self.proc_c(st)), _ptr(H), _ptr(V),
+                                        _ptr(W), _ptr(loss), _ptr(gH), _ptr(gV), _ptr(gW)))
+        return loss, gH, gV, gW
+
+
+def reconstruction_loss(handle: Copa, X: DeviceTensor, H, V, W, tau=1e-8):
+    """L = sum_k ||X_k - Q_k H S_k V^T||_F^2 with Q_k from the Procrustes step at (H, V, W),
+    held fixed; differentiable in H, V, W through the hand-written backward kernels."""
+    import torch
+
+    class _Loss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, H_, V_, W_):
+            R = H_.shape[0]
+            st = handle.procrustes(X, R, H_.detach(), V_.detach(), W_.detach(), tau, want_pi=True, want_fh=False)
+            loss, gH, gV, gW = handle.loss_grad(X, R, st, H_.detach(), V_.detach(), W_.detach())
+            ctx.save_for_backward(gH, gV, gW)
+            return loss[0].to(H_.dtype)
+
+        @staticmethod
+        def backward(ctx, g):
+            gH, gV, gW = ctx.saved_tensors
+            return g * gH, g * gV, g * gW
+
+    return _Loss.apply(H, V, W)

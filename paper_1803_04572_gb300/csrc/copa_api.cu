@@ -1,0 +1,642 @@
+// The C ABI of libcopa: handle and workspace management, argument checks, the subject
+// schedule, X validation and the orchestration of whole outer iterations (Algorithm 1)
+// on one stream, optionally captured once into a CUDA graph and replayed.
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "copa_internal.cuh"
+
+using namespace copa;
+
+namespace copa {
+
+copa_status_t fail(copa_ctx* h, copa_status_t code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+copa_status_t cuda_check(copa_ctx* h, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return COPA_OK;
+  return fail(h, COPA_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+copa_status_t ws_get(copa_ctx* h, int slot, size_t bytes, void** out) {
+  if (bytes == 0) bytes = 16;
+  if (h->slot_bytes[slot] < bytes) {
+    if (h->slot_ptr[slot]) {
+      cudaStreamSynchronize(h->stream);
+      cudaFree(h->slot_ptr[slot]);
+      h->slot_ptr[slot] = nullptr;
+      h->slot_bytes[slot] = 0;
+    }
+    size_t want = bytes + bytes / 4;
+    if (cudaMalloc(&h->slot_ptr[slot], want) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, COPA_ERR_OOM, "workspace allocation of " + std::to_string(want) + " bytes failed");
+    }
+    h->slot_bytes[slot] = want;
+  }
+  if (out) *out = h->slot_ptr[slot];
+  return COPA_OK;
+}
+
+TensorView view_of(const copa_tensor_t* X) {
+  TensorView v;
+  v.K = X->K; v.J = X->J; v.S = X->S; v.nnz = X->nnz;
+  v.subj_ptr = X->subj_ptr; v.row_ptr = X->row_ptr; v.col = X->col_idx; v.vals = X->vals;
+  v.dtype = X->val_dtype;
+  return v;
+}
+
+copa_status_t check_tensor_args(copa_ctx* h, const copa_tensor_t* X) {
+  if (!X) return fail(h, COPA_ERR_INVALID_ARG, "X is NULL");
+  if (X->K < 0 || X->J < 1 || X->S < 0 || X->nnz < 0)
+    return fail(h, COPA_ERR_INVALID_ARG, "X: negative K, S, nnz or J < 1");
+  if (X->val_dtype != COPA_VAL_F32 && X->val_dtype != COPA_VAL_F64 && X->val_dtype != COPA_VAL_BF16)
+    return fail(h, COPA_ERR_INVALID_ARG, "X: unknown val_dtype");
+  if (!X->subj_ptr || !X->row_ptr || (X->nnz > 0 && (!X->col_idx || !X->vals)))
+    return fail(h, COPA_ERR_INVALID_ARG, "X: NULL array");
+  return COPA_OK;
+}
+
+namespace {
+
+constexpr int kBuckets = 2048;
+
+__global__ void k_sched_hist(const int64_t* __restrict__ subj_ptr, int64_t K, int* __restrict__ hist) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K; k += gridDim.x * (int64_t)blockDim.x) {
+    int64_t sz = subj_ptr[k + 1] - subj_ptr[k];
+    if (sz > kBuckets - 1) sz = kBuckets - 1;
+    atomicAdd(hist + (kBuckets - 1 - sz), 1);
+  }
+}
+
+__global__ void k_sched_scan(int* __restrict__ hist, int* __restrict__ offs) {
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int b = 0; b < kBuckets; ++b) { offs[b] = acc; acc += hist[b]; hist[b] = 0; }
+  }
+}
+
+__global__ void k_sched_scatter(const int64_t* __restrict__ subj_ptr, int64_t K, const int* __restrict__ offs,
+                                int* __restrict__ cursor, int64_t* __restrict__ order) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K; k += gridDim.x * (int64_t)blockDim.x) {
+    int64_t sz = subj_ptr[k + 1] - subj_ptr[k];
+    if (sz > kBuckets - 1) sz = kBuckets - 1;
+    const int b = kBuckets - 1 - (int)sz;
+    order[offs[b] + atomicAdd(cursor + b, 1)] = k;
+  }
+}
+
+__global__ void k_validate(TensorView X, int* __restrict__ status) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nt = gridDim.x * (int64_t)blockDim.x;
+  if (tid == 0) {
+    if (X.subj_ptr[0] != 0 || X.subj_ptr[X.K] != X.S) set_status(status, 101, 0);
+    if (X.row_ptr[0] != 0 || X.row_ptr[X.S] != X.nnz) set_status(status, 102, 0);
+  }
+  for (int64_t k = tid; k < X.K; k += nt)
+    if (X.subj_ptr[k + 1] < X.subj_ptr[k]) set_status(status, 103, (int)k);
+  for (int64_t i = tid; i < X.S; i += nt) {
+    const int64_t a = X.row_ptr[i], b = X.row_ptr[i + 1];
+    if (b < a) { set_status(status, 104, (int)i); continue; }
+    for (int64_t t = a; t < b; ++t) {
+      const int32_t c = X.col[t];
+      if (c < 0 || c >= X.J) set_status(status, 105, (int)i);
+      if (t > a && c <= X.col[t - 1]) set_status(status, 106, (int)i);
+    }
+  }
+  if (X.dtype == COPA_VAL_BF16) {
+    for (int64_t t = tid; t < X.nnz; t += nt) {
+      const float v = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(X.vals)[t]);
+      if (!(fabsf(v) <= 256.0f) || v != rintf(v)) set_status(status, 107, (int)t);
+    }
+  }
+}
+
+__global__ void k_xnorm2(TensorView X, double* __restrict__ out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < X.nnz; t += gridDim.x * (int64_t)blockDim.x) {
+    const double v = load_val(X, t);
+    acc += v * v;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(out, red[0]);
+}
+
+__global__ void k_store_fit(const double* __restrict__ fit, double* __restrict__ hist, int* __restrict__ it) {
+  hist[*it] = *fit;
+  *it += 1;
+}
+
+}  // namespace
+
+copa_status_t get_schedule(copa_ctx* h, const TensorView& X, const int64_t** order) {
+  copa_status_t st;
+  if (h->sched_key == X.subj_ptr && h->sched_K == X.K && h->sched_S == X.S && h->slot_ptr[SLOT_ORDER]) {
+    *order = reinterpret_cast<const int64_t*>(h->slot_ptr[SLOT_ORDER]);
+    return COPA_OK;
+  }
+  int64_t* ord = nullptr;
+  int* tmp = nullptr;
+  if ((st = ws_get(h, SLOT_ORDER, sizeof(int64_t) * (X.K + 1), (void**)&ord)) != COPA_OK) return st;
+  if ((st = ws_get(h, SLOT_SCHED_TMP, sizeof(int) * 3 * kBuckets, (void**)&tmp)) != COPA_OK) return st;
+  if (X.K > 0) {
+    if ((st = cuda_check(h, cudaMemsetAsync(tmp, 0, sizeof(int) * 3 * kBuckets, h->stream), "memset")) != COPA_OK)
+      return st;
+    const int blocks = (int)std::min<int64_t>((X.K + 255) / 256, 4096);
+    k_sched_hist<<<blocks, 256, 0, h->stream>>>(X.subj_ptr, X.K, tmp);
+    k_sched_scan<<<1, 32, 0, h->stream>>>(tmp, tmp + kBuckets);
+    k_sched_scatter<<<blocks, 256, 0, h->stream>>>(X.subj_ptr, X.K, tmp + kBuckets, tmp, ord);
+    if ((st = cuda_check(h, cudaGetLastError(), "schedule kernels")) != COPA_OK) return st;
+  }
+  h->sched_key = X.subj_ptr;
+  h->sched_K = X.K;
+  h->sched_S = X.S;
+  *order = ord;
+  return COPA_OK;
+}
+
+copa_status_t launch_validate(copa_ctx* h, const TensorView& X) {
+  const int64_t work = std::max<int64_t>(std::max<int64_t>(X.K, X.S), X.nnz);
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, (int64_t)h->num_sms * 8));
+  k_validate<<<blocks, 256, 0, h->stream>>>(X, h->d_status);
+  return cuda_check(h, cudaGetLastError(), "k_validate");
+}
+
+copa_status_t launch_xnorm2(copa_ctx* h, const TensorView& X, double* out) {
+  copa_status_t st;
+  if ((st = cuda_check(h, cudaMemsetAsync(out, 0, sizeof(double), h->stream), "memset")) != COPA_OK) return st;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((X.nnz + 255) / 256, (int64_t)h->num_sms * 4));
+  k_xnorm2<<<blocks, 256, 0, h->stream>>>(X, out);
+  return cuda_check(h, cudaGetLastError(), "k_xnorm2");
+}
+
+}  // namespace copa
+
+// =====================================================================================
+// C ABI
+// =====================================================================================
+
+static copa_status_t sync_status(copa_ctx* h) {
+  copa_status_t st = cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+  if (st != COPA_OK) return st;
+  int hs[4] = {0, 0, 0, 0};
+  if ((st = cuda_check(h, cudaMemcpy(hs, h->d_status, sizeof(hs), cudaMemcpyDeviceToHost), "status read")) != COPA_OK)
+    return st;
+  if (hs[0] == 0) return COPA_OK;
+  cudaMemsetAsync(h->d_status, 0, sizeof(int) * 4, h->stream);
+  cudaStreamSynchronize(h->stream);
+  const int code = hs[0];
+  if (code == COPA_ERR_NUMERIC)
+    return fail(h, COPA_ERR_NUMERIC, "G + rho I is not positive definite or not finite");
+  if (code == COPA_ERR_TIMEOUT) return fail(h, COPA_ERR_TIMEOUT, "a bounded device wait gave up");
+  static const char* what[] = {"subj_ptr[0] != 0 or subj_ptr[K] != S", "row_ptr[0] != 0 or row_ptr[S] != nnz",
+                               "subj_ptr decreases at subject", "row_ptr decreases at row",
+                               "column index out of [0, J) in row", "columns not strictly increasing in row",
+                               "bf16 value not an integer of magnitude <= 256 at nonzero"};
+  if (code >= 101 && code <= 107)
+    return fail(h, COPA_ERR_INVALID_ARG, std::string("X invalid: ") + what[code - 101] + " " + std::to_string(hs[1]));
+  return fail(h, (copa_status_t)code, "device error " + std::to_string(code) + " info " + std::to_string(hs[1]));
+}
+
+#define CHECK_H(h) \
+  if (!(h)) return COPA_ERR_INVALID_ARG
+#define TRY(x)                           \
+  do {                                   \
+    copa_status_t _s = (x);              \
+    if (_s != COPA_OK) return _s;        \
+  } while (0)
+
+static copa_status_t check_R(copa_ctx* h, int R) {
+  if (R < 1) return fail(h, COPA_ERR_INVALID_ARG, "R must be >= 1");
+  if (R > kMaxR) return fail(h, COPA_ERR_UNSUPPORTED, "R must be <= 96");
+  return COPA_OK;
+}
+
+static copa_status_t set_dev(copa_ctx* h) { return cuda_check(h, cudaSetDevice(h->device), "cudaSetDevice"); }
+
+extern "C" {
+
+copa_status_t copa_create(copa_handle_t* handle, int device, void* stream, int32_t precision) {
+  if (!handle) return COPA_ERR_INVALID_ARG;
+  *handle = nullptr;
+  if (precision != COPA_PREC_MIXED && precision != COPA_PREC_FP64) return COPA_ERR_INVALID_ARG;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return COPA_ERR_CUDA;
+  }
+  copa_ctx* h = new copa_ctx();
+  h->device = device;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  h->precision = precision;
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaMalloc(&h->d_status, sizeof(int) * 4) != cudaSuccess ||
+      cudaMemset(h->d_status, 0, sizeof(int) * 4) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return COPA_ERR_CUDA;
+  }
+  *handle = h;
+  return COPA_OK;
+}
+
+copa_status_t copa_destroy(copa_handle_t h) {
+  CHECK_H(h);
+  cudaSetDevice(h->device);
+  cudaStreamSynchronize(h->stream);
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  for (int i = 0; i < 16; ++i) {
+    if (h->slot_ptr[i]) cudaFree(h->slot_ptr[i]);
+    if (h->host_slot_ptr[i]) cudaFree(h->host_slot_ptr[i]);
+  }
+  cudaFree(h->d_status);
+  delete h;
+  return COPA_OK;
+}
+
+const char* copa_last_error(copa_handle_t h) {
+  if (!h) return "invalid handle";
+  return h->err.c_str();
+}
+
+copa_status_t copa_sync(copa_handle_t h) {
+  CHECK_H(h);
+  TRY(set_dev(h));
+  return sync_status(h);
+}
+
+copa_status_t copa_validate(copa_handle_t h, const copa_tensor_t* X) {
+  CHECK_H(h);
+  TRY(set_dev(h));
+  TRY(check_tensor_args(h, X));
+  TRY(launch_validate(h, view_of(X)));
+  return sync_status(h);
+}
+
+copa_status_t copa_procrustes(copa_handle_t h, const copa_tensor_t* X, int32_t R, const void* H,
+                              const void* V, const void* W, double tau, copa_procrustes_out_t* out,
+                              void* F_H) {
+  CHECK_H(h);
+  TRY(set_dev(h));
+  TRY(check_tensor_args(h, X));
+  TRY(check_R(h, R));
+  if (!H || !V || !W || !out || !out->Gamma || !out->T)
+    return fail(h, COPA_ERR_INVALID_ARG, "copa_procrustes: NULL H, V, W, Gamma or T");
+  if (!(tau >= 0.0 && tau < 1.0)) return fail(h, COPA_ERR_INVALID_ARG, "tau must be in [0, 1)");
+  const TensorView v = view_of(X);
+  if (h->precision == COPA_PREC_MIXED)
+    return launch_procrustes<float>(h, v, R, (const float*)H, (const float*)V, (const float*)W, tau,
+                                    (float*)out->Gamma, (float*)out->T, (float*)out->Pi, out->rank,
+                                    (float*)F_H);
+  return launch_procrustes<double>(h, v, R, (const double*)H, (const double*)V, (const double*)W, tau,
+                                   (double*)out->Gamma, (double*)out->T, (double*)out->Pi, out->rank,
+                                   (double*)F_H);
+}
+
+copa_status_t copa_mttkrp(copa_handle_t h, int32_t mode, const copa_tensor_t* X, int32_t R,
+                          const copa_procrustes_out_t* st, const void* Vp, const void* H,
+                          const void* W, void* F, double* UtU) {
+  CHECK_H(h);
+  TRY(set_dev(h));
+  TRY(check_R(h, R));
+  if (!st || !F) return fail(h, COPA_ERR_INVALID_ARG, "copa_mttkrp: NULL state or F");
+  const bool mixed = h->precision == COPA_PREC_MIXED;
+  if (mode == COPA_MODE_H) {
+    if (!X || !st->T || !W) return fail(h, COPA_ERR_INVALID_ARG, "copa_mttkrp(H): needs X (for K), T, W");
+    if (mixed) return launch_mttkrp_h<float>(h, X->K, R, (const float*)st->T, (const float*)W, (float*)F);
+    return launch_mttkrp_h<double>(h, X->K, R, (const double*)st->T, (const double*)W, (double*)F);
+  }
+  if (mode == COPA_MODE_W) {
+    if (!X || !st->T || !H) return fail(h, COPA_ERR_INVALID_ARG, "copa_mttkrp(W): needs X (for K), T, H");
+    if (mixed) return launch_mttkrp_w<float>(h, X->K, R, (const float*)st->T, (const float*)H, (float*)F);
+    return launch_mttkrp_w<double>(h, X->K, R, (const double*)st->T, (const double*)H, (double*)F);
+  }
+  if (mode == COPA_MODE_V) {
+    TRY(check_tensor_args(h, X));
+    if (!st->Gamma || !Vp || !H || !W) return fail(h, COPA_ERR_INVALID_ARG, "copa_mttkrp(V): needs Gamma, Vp, H, W");
+    const TensorView v = view_of(X);
+    if (mixed)
+      return launch_mttkrp_v<float>(h, v, R, (const float*)st->Gamma, (const float*)Vp, (const float*)H,
+                                    (const float*)W, (float*)F, UtU);
+    return launch_mttkrp_v<double>(h, v, R, (const double*)st->Gamma, (const double*)Vp, (const double*)H,
+                                   (const double*)W, (double*)F, UtU);
+  }
+  return fail(h, COPA_ERR_INVALID_ARG, "copa_mttkrp: mode must be 0 (H), 1 (V) or 2 (W)");
+}
+
+copa_status_t copa_gram(copa_handle_t h, const void* A, int64_t rows, int32_t R, double* G) {
+  CHECK_H(h);
+  TRY(set_dev(h));
+  TRY(check_R(h, R));
+  if (!A || !G || rows < 0) return fail(h, COPA_ERR_INVALID_ARG, "copa_gram: bad arguments");
+  if (h->precision == COPA_PREC_MIXED) return launch_gram<float>(h, (const float*)A, rows, R, G);
+  return launch_gram<double>(h, (const double*)A, rows, R, G);
+}
+
+static copa_status_t check_admm(copa_ctx* h, int n_inner, int c, double lam, int R) {
+  TRY(check_R(h, R));
+  if (n_inner < 0) return fail(h, COPA_ERR_INVALID_ARG, "n_inner must be >= 0");
+  if (c < COPA_C_NONE || c > COPA_C_L0) return fail(h, COPA_ERR_INVALID_ARG, "unknown constraint");
+  if (!(lam >= 0.0)) return fail(h, COPA_ERR_INVALID_ARG, "lambda must be >= 0");
+  return COPA_OK;
+}
+
+copa_status_t copa_admm_step(copa_handle_t h, const void* F, const double* Ga, const double* Gb,
+                             int32_t n_inner, int32_t c, double lambda, void* Zbar, void* D,
+                             int64_t rows, int32_t R, double* rho_out) {
+  CHECK_H(h);
+  TRY(set_dev(h));
+  TRY(check_admm(h, n_inner, c, lambda, R));
+  if (!F || !Ga || !Zbar || !D || rows < 0) return fail(h, COPA_ERR_INVALID_ARG, "copa_admm_step: bad arguments");
+  void* ginv = nullptr;
+  TRY(ws_get(h, SLOT_GINV, sizeof(double) * ((size_t)R * (R + 1) + 2), &ginv));
+  double* rho = rho_out ? rho_out : reinterpret_cast<double*>(ginv) + (size_t)R * (R + 1);
+  if (h->precision == COPA_PREC_MIXED) {
+    TRY(launch_chol<float>(h, Ga, Gb, R, (float*)ginv, rho));
+    return launch_admm_rows<float>(h, (const float*)F, (const float*)ginv, rho, n_inner, c, lambda,
+                                   (float*)Zbar, (float*)D, rows, R);
+  }
+  TRY(launch_chol<double>(h, Ga, Gb, R, (double*)ginv, rho));
+  return launch_admm_rows<double>(h, (const double*)F, (const double*)ginv, rho, n_inner, c, lambda,
+                                  (double*)Zbar, (double*)D, rows, R);
+}
+
+copa_status_t copa_admm_w_fused(copa_handle_t h, const copa_procrustes_out_t* st, const void* H,
+                                const double* Ga, const double* Gb, int32_t n_inner, int32_t c,
+                                double lambda, void* Wbar, void* DW, int64_t K, int32_t R,
+                                double* rho_out) {
+  CHECK_H(h);
+  TRY(set_dev(h));
+  TRY(check_admm(h, n_inner, c, lambda, R));
+  if (!st || !st->T || !H || !Ga || !Wbar || !DW || K < 0)
+    return fail(h, COPA_ERR_INVALID_ARG, "copa_admm_w_fused: bad arguments");
+  void* ginv = nullptr;
+  TRY(ws_get(h, SLOT_GINV, sizeof(double) * ((size_t)R * (R + 1) + 2), &ginv));
+  double* rho = rho_out ? rho_out : reinterpret_cast<double*>(ginv) + (size_t)R * (R + 1);
+  if (h->precision == COPA_PREC_MIXED) {
+    TRY(launch_chol<float>(h, Ga, Gb, R, (float*)ginv, rho));
+    return launch_admm_w<float>(h, (const float*)st->T, (const float*)H, (const float*)ginv, rho, n_inner,
+                                c, lambda, (float*)Wbar, (float*)DW, K, R);
+  }
+  TRY(launch_chol<double>(h, Ga, Gb, R, (double*)ginv, rho));
+  return launch_admm_w<double>(h, (const double*)st->T, (const double*)H, (const double*)ginv, rho, n_inner,
+                               c, lambda, (double*)Wbar, (double*)DW, K, R);
+}
+
+copa_status_t copa_fit_value(copa_handle_t h, const copa_tensor_t* X, int32_t R, const void* V,
+                             const void* F_V, const double* UtU, double x_norm2, double* fit) {
+  CHECK_H(h);
+  TRY(set_dev(h));
+  TRY(check_tensor_args(h, X));
+  TRY(check_R(h, R));
+  if (!V || !F_V || !UtU || !fit) return fail(h, COPA_ERR_INVALID_ARG, "copa_fit_value: NULL argument");
+  double* xn2 = nullptr;
+  TRY(ws_get(h, SLOT_PI, sizeof(double) * 4, (void**)&xn2));
+  const TensorView v = view_of(X);
+  TRY(launch_xnorm2(h, v, xn2));
+  if (h->precision == COPA_PREC_MIXED)
+    return launch_fit_value<float>(h, X->J, R, (const float*)V, (const float*)F_V, UtU, xn2, x_norm2, fit);
+  return launch_fit_value<double>(h, X->J, R, (const double*)V, (const double*)F_V, UtU, xn2, x_norm2, fit);
+}
+
+copa_status_t copa_assemble_q(copa_handle_t h, const copa_tensor_t* X, int32_t R,
+                              const copa_procrustes_out_t* st, const void* Vp, const void* H, void* Q,
+                              void* U) {
+  CHECK_H(h);
+  TRY(set_dev(h));
+  TRY(check_tensor_args(h, X));
+  TRY(check_R(h, R));
+  if (!st || !st->Gamma || !Vp || !Q || (U && !H))
+    return fail(h, COPA_ERR_INVALID_ARG, "copa_assemble_q: bad arguments");
+  const TensorView v = view_of(X);
+  if (h->precision == COPA_PREC_MIXED)
+    return launch_assemble_q<float>(h, v, R, (const float*)st->Gamma, (const float*)Vp, (const float*)H,
+                                    (float*)Q, U ? (float*)U : nullptr);
+  return launch_assemble_q<double>(h, v, R, (const double*)st->Gamma, (const double*)Vp, (const double*)H,
+                                   (double*)Q, U ? (double*)U : nullptr);
+}
+
+}  // extern "C"
+
+// =====================================================================================
+// Whole outer iterations
+// =====================================================================================
+
+namespace {
+
+template <typename Real>
+struct FitBufs {
+  Real* Gamma;
+  Real* T;
+  Real* Pi;
+  int32_t* rank;
+  Real* FH;
+  Real* FV;
+  Real* Ginv;
+  double* gH;
+  double* gV;
+  double* gW;
+  double* UtU;
+  double* rho;
+  double* xn2;
+  double* fitv;
+  double* hist;
+  int* it;
+};
+
+template <typename Real>
+copa_status_t one_iteration(copa_ctx* h, const TensorView& X, const copa_options_t* o, Real* H, Real* V,
+                            Real* W, Real* DH, Real* DV, Real* DW, const FitBufs<Real>& b) {
+  const int R = o->R;
+  // (a)+(b) Procrustes, with the H-mode MTTKRP fused
+  TRY(launch_procrustes<Real>(h, X, R, H, V, W, o->tau, b.Gamma, b.T, b.Pi, b.rank, b.FH));
+  // H: G = W^T W .* V^T V
+  TRY(launch_gram<Real>(h, W, X.K, R, b.gW));
+  TRY(launch_gram<Real>(h, V, X.J, R, b.gV));
+  TRY(launch_chol<Real>(h, b.gW, b.gV, R, b.Ginv, b.rho + 0));
+  TRY(launch_admm_rows<Real>(h, b.FH, b.Ginv, b.rho + 0, o->n_inner, o->c_H, o->lam_H, H, DH, R, R));
+  // W: G = H^T H .* V^T V, F_W fused into the ADMM
+  TRY(launch_gram<Real>(h, H, R, R, b.gH));
+  TRY(launch_chol<Real>(h, b.gH, b.gV, R, b.Ginv, b.rho + 1));
+  TRY(launch_admm_w<Real>(h, b.T, H, b.Ginv, b.rho + 1, o->n_inner, o->c_W, o->lam_W, W, DW, X.K, R));
+  // V: G = H^T H .* W^T W; F_V streams X with the V of the Procrustes step (still in V)
+  TRY(launch_gram<Real>(h, W, X.K, R, b.gW));
+  TRY(launch_mttkrp_v<Real>(h, X, R, b.Gamma, V, H, W, b.FV, b.UtU));
+  TRY(launch_chol<Real>(h, b.gH, b.gW, R, b.Ginv, b.rho + 2));
+  TRY(launch_admm_rows<Real>(h, b.FV, b.Ginv, b.rho + 2, o->n_inner, o->c_V, o->lam_V, V, DV, X.J, R));
+  // FIT of (Q_k, H, W, V) after the iteration
+  TRY(launch_fit_value<Real>(h, X.J, R, V, b.FV, b.UtU, b.xn2, o->x_norm2, b.fitv));
+  k_store_fit<<<1, 1, 0, h->stream>>>(b.fitv, b.hist, b.it);
+  return cuda_check(h, cudaGetLastError(), "k_store_fit");
+}
+
+template <typename Real>
+copa_status_t fit_impl(copa_ctx* h, const copa_tensor_t* Xc, const copa_options_t* o, Real* H, Real* V,
+                       Real* W, Real* DH, Real* DV, Real* DW, double* hist_host, copa_procrustes_out_t* st) {
+  const TensorView X = view_of(Xc);
+  const int R = o->R;
+  const size_t KRR = (size_t)X.K * R * R;
+  FitBufs<Real> b{};
+  if (st && st->Gamma && st->T) {
+    b.Gamma = (Real*)st->Gamma;
+    b.T = (Real*)st->T;
+    b.Pi = (Real*)st->Pi;
+    b.rank = st->rank;
+  } else {
+    TRY(ws_get(h, SLOT_FIT_GAMMA, sizeof(Real) * KRR, (void**)&b.Gamma));
+    TRY(ws_get(h, SLOT_FIT_T, sizeof(Real) * KRR, (void**)&b.T));
+  }
+  const size_t nsmall = sizeof(Real) * ((size_t)R * R + (size_t)X.J * R + (size_t)R * (R + 1)) +
+                        sizeof(double) * (4 * (size_t)R * R + 8 + (size_t)o->n_outer) + 64;
+  char* p = nullptr;
+  TRY(ws_get(h, SLOT_FIT_SMALL, nsmall + 512, (void**)&p));
+  auto take = [&](size_t bytes) {
+    char* r = p;
+    p += (bytes + 255) & ~size_t(255);
+    return r;
+  };
+  b.gH = (double*)take(sizeof(double) * R * R);
+  b.gV = (double*)take(sizeof(double) * R * R);
+  b.gW = (double*)take(sizeof(double) * R * R);
+  b.UtU = (double*)take(sizeof(double) * R * R);
+  b.rho = (double*)take(sizeof(double) * 4);
+  b.xn2 = (double*)take(sizeof(double));
+  b.fitv = (double*)take(sizeof(double));
+  b.hist = (double*)take(sizeof(double) * std::max(1, o->n_outer));
+  b.it = (int*)take(sizeof(int));
+  b.FH = (Real*)take(sizeof(Real) * R * R);
+  b.FV = (Real*)take(sizeof(Real) * (size_t)X.J * R);
+  b.Ginv = (Real*)take(sizeof(Real) * R * (R + 1));
+  TRY(cuda_check(h, cudaMemsetAsync(b.it, 0, sizeof(int), h->stream), "memset"));
+  TRY(launch_xnorm2(h, X, b.xn2));
+  if (o->n_outer > 0) {
+    // the first iteration runs eagerly: it sizes every workspace buffer
+    TRY(one_iteration<Real>(h, X, o, H, V, W, DH, DV, DW, b));
+  }
+  if (o->n_outer > 1) {
+    if (o->use_graph) {
+      // Capture on a private stream (the caller's may be the legacy default stream, which
+      // cannot be captured); capturing enqueues nothing, the replays go to h->stream.
+      cudaGraph_t graph = nullptr;
+      cudaStream_t orig = h->stream, cap = nullptr;
+      TRY(cuda_check(h, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "cudaStreamCreate"));
+      h->stream = cap;
+      cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+      copa_status_t cs = ce == cudaSuccess ? one_iteration<Real>(h, X, o, H, V, W, DH, DV, DW, b) : COPA_OK;
+      if (ce == cudaSuccess) ce = cudaStreamEndCapture(cap, &graph);
+      h->stream = orig;
+      cudaStreamDestroy(cap);
+      if (cs != COPA_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return cs;
+      }
+      TRY(cuda_check(h, ce, "EndCapture"));
+      cudaGraphExec_t exec = nullptr;
+      ce = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      TRY(cuda_check(h, ce, "GraphInstantiate"));
+      for (int it = 1; it < o->n_outer; ++it) {
+        ce = cudaGraphLaunch(exec, h->stream);
+        if (ce != cudaSuccess) break;
+      }
+      cudaGraphExecDestroy(exec);
+      TRY(cuda_check(h, ce, "GraphLaunch"));
+    } else {
+      for (int it = 1; it < o->n_outer; ++it) TRY(one_iteration<Real>(h, X, o, H, V, W, DH, DV, DW, b));
+    }
+  }
+  TRY(sync_status(h));
+  if (hist_host && o->n_outer > 0)
+    TRY(cuda_check(h, cudaMemcpy(hist_host, b.hist, sizeof(double) * o->n_outer, cudaMemcpyDeviceToHost),
+                   "history D2H"));
+  return COPA_OK;
+}
+
+copa_status_t check_options(copa_ctx* h, const copa_options_t* o) {
+  if (!o) return fail(h, COPA_ERR_INVALID_ARG, "options NULL");
+  TRY(check_R(h, o->R));
+  if (o->n_outer < 0 || o->n_inner < 0) return fail(h, COPA_ERR_INVALID_ARG, "negative iteration count");
+  for (int c : {o->c_H, o->c_W, o->c_V})
+    if (c < COPA_C_NONE || c > COPA_C_L0) return fail(h, COPA_ERR_INVALID_ARG, "unknown constraint");
+  if (!(o->lam_H >= 0 && o->lam_W >= 0 && o->lam_V >= 0)) return fail(h, COPA_ERR_INVALID_ARG, "negative lambda");
+  if (!(o->tau >= 0.0 && o->tau < 1.0)) return fail(h, COPA_ERR_INVALID_ARG, "tau must be in [0, 1)");
+  return COPA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+copa_status_t copa_fit(copa_handle_t h, const copa_tensor_t* X, const copa_options_t* opt, void* H, void* V,
+                       void* W, void* DH, void* DV, void* DW, double* fit_history_host,
+                       copa_procrustes_out_t* st) {
+  CHECK_H(h);
+  TRY(set_dev(h));
+  TRY(check_tensor_args(h, X));
+  TRY(check_options(h, opt));
+  if (!H || !V || !W || !DH || !DV || !DW) return fail(h, COPA_ERR_INVALID_ARG, "copa_fit: NULL factor or dual");
+  if (h->precision == COPA_PREC_MIXED)
+    return fit_impl<float>(h, X, opt, (float*)H, (float*)V, (float*)W, (float*)DH, (float*)DV, (float*)DW,
+                           fit_history_host, st);
+  return fit_impl<double>(h, X, opt, (double*)H, (double*)V, (double*)W, (double*)DH, (double*)DV, (double*)DW,
+                          fit_history_host, st);
+}
+
+copa_status_t copa_fit_host(copa_handle_t h, const copa_tensor_t* Xh, const copa_options_t* opt, void* H_host,
+                            void* V_host, void* W_host, void* DH_host, void* DV_host, void* DW_host,
+                            double* fit_history_host) {
+  CHECK_H(h);
+  TRY(set_dev(h));
+  TRY(check_tensor_args(h, Xh));
+  TRY(check_options(h, opt));
+  if (!H_host || !V_host || !W_host || !DH_host || !DV_host || !DW_host)
+    return fail(h, COPA_ERR_INVALID_ARG, "copa_fit_host: NULL factor or dual");
+  const size_t es = h->precision == COPA_PREC_MIXED ? sizeof(float) : sizeof(double);
+  const size_t vs = Xh->val_dtype == COPA_VAL_F64 ? 8 : (Xh->val_dtype == COPA_VAL_F32 ? 4 : 2);
+  const int R = opt->R;
+  const size_t sizes[10] = {sizeof(int64_t) * (Xh->K + 1), sizeof(int64_t) * (Xh->S + 1),
+                            sizeof(int32_t) * Xh->nnz,      vs * Xh->nnz,
+                            es * R * R,                      es * (size_t)Xh->J * R,
+                            es * (size_t)Xh->K * R,          es * R * R,
+                            es * (size_t)Xh->J * R,          es * (size_t)Xh->K * R};
+  const void* src[10] = {Xh->subj_ptr, Xh->row_ptr, Xh->col_idx, Xh->vals, H_host, V_host, W_host,
+                         DH_host,      DV_host,     DW_host};
+  void* dst[10];
+  for (int i = 0; i < 10; ++i) {
+    if (h->host_slot_bytes[i] < sizes[i] + 16) {
+      if (h->host_slot_ptr[i]) cudaFree(h->host_slot_ptr[i]);
+      h->host_slot_ptr[i] = nullptr;
+      h->host_slot_bytes[i] = 0;
+      if (cudaMalloc(&h->host_slot_ptr[i], sizes[i] + 16) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, COPA_ERR_OOM, "copa_fit_host: device allocation failed");
+      }
+      h->host_slot_bytes[i] = sizes[i] + 16;
+    }
+    dst[i] = h->host_slot_ptr[i];
+    if (sizes[i])
+      TRY(cuda_check(h, cudaMemcpyAsync(dst[i], src[i], sizes[i], cudaMemcpyHostToDevice, h->stream), "H2D"));
+  }
+  copa_tensor_t Xd = *Xh;
+  Xd.subj_ptr = (const int64_t*)dst[0];
+  Xd.row_ptr = (const int64_t*)dst[1];
+  Xd.col_idx = (const int32_t*)dst[2];
+  Xd.vals = dst[3];
+  TRY(copa_fit(h, &Xd, opt, dst[4], dst[5], dst[6], dst[7], dst[8], dst[9], fit_history_host, nullptr));
+  for (int i = 4; i < 10; ++i)
+    TRY(cuda_check(h, cudaMemcpyAsync(const_cast<void*>(src[i]), dst[i], sizes[i], cudaMemcpyDeviceToHost, h->stream),
+                   "D2H"));
+  return cuda_check(h, cudaStreamSynchronize(h->stream), "sync");
+}
+
+}  // extern "C"

@@ -1,0 +1,187 @@
+// Internal declarations shared by the CUDA translation units of libcopa.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "copa.h"
+
+namespace copa {
+
+constexpr int kMaxR = 96;          // largest rank the shared-memory kernels hold
+constexpr int kMaxBasis = 16;      // largest spline basis (smoothing set-up)
+
+// Device status word layout (int32[4] in the workspace): [0] = first error code,
+// [1..3] = details (subject index, etc.). Kernels never trap; they record and return.
+__device__ __forceinline__ void set_status(int* st, int code, int info = 0) {
+  if (atomicCAS(st, 0, code) == 0) st[1] = info;
+}
+
+// Read-only view of X on the device.
+struct TensorView {
+  int64_t K;
+  int32_t J;
+  int64_t S;
+  int64_t nnz;
+  const int64_t* subj_ptr;
+  const int64_t* row_ptr;
+  const int32_t* col;
+  const void* vals;
+  int32_t dtype;
+};
+
+__device__ __forceinline__ double load_val(const TensorView& X, int64_t i) {
+  if (X.dtype == COPA_VAL_BF16) {
+    return (double)__bfloat162float(reinterpret_cast<const __nv_bfloat16*>(X.vals)[i]);
+  } else if (X.dtype == COPA_VAL_F32) {
+    return (double)__ldg(reinterpret_cast<const float*>(X.vals) + i);
+  }
+  return __ldg(reinterpret_cast<const double*>(X.vals) + i);
+}
+
+__device__ __forceinline__ float load_valf(const TensorView& X, int64_t i) {
+  if (X.dtype == COPA_VAL_BF16) {
+    return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(X.vals)[i]);
+  } else if (X.dtype == COPA_VAL_F32) {
+    return __ldg(reinterpret_cast<const float*>(X.vals) + i);
+  }
+  return (float)__ldg(reinterpret_cast<const double*>(X.vals) + i);
+}
+
+template <typename Real>
+__device__ __forceinline__ Real load_x(const TensorView& X, int64_t i);
+template <>
+__device__ __forceinline__ float load_x<float>(const TensorView& X, int64_t i) {
+  return load_valf(X, i);
+}
+template <>
+__device__ __forceinline__ double load_x<double>(const TensorView& X, int64_t i) {
+  return load_val(X, i);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Proximal operators of Sec. 3.3 (v = z - d). Shared by every ADMM kernel.
+template <typename Real>
+__device__ __forceinline__ Real prox(Real v, int c, Real lam_over_rho) {
+  switch (c) {
+    case COPA_C_NONNEG:
+      return v > Real(0) ? v : Real(0);
+    case COPA_C_L1: {
+      Real a = fabs(v) - lam_over_rho;
+      if (a <= Real(0)) return Real(0);
+      return v > Real(0) ? a : -a;
+    }
+    case COPA_C_L0:
+      return (v * v > Real(2) * lam_over_rho) ? v : Real(0);
+    default:
+      return v;
+  }
+}
+
+}  // namespace copa
+
+// The handle. Workspace buffers grow on demand and are reused.
+struct copa_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int precision = COPA_PREC_MIXED;
+  std::string err;
+  int* d_status = nullptr;       // int32[4] device status word
+  int num_sms = 0;
+  // generic workspace slots
+  void* slot_ptr[16] = {nullptr};
+  size_t slot_bytes[16] = {0};
+  // cached per-tensor schedule (subjects ordered by decreasing I_k)
+  const int64_t* sched_key = nullptr;
+  int64_t sched_K = 0;
+  int64_t sched_S = 0;
+  // copa_fit_host device copies
+  void* host_slot_ptr[16] = {nullptr};
+  size_t host_slot_bytes[16] = {0};
+  // CUDA graph of one outer iteration
+  cudaGraphExec_t graph_exec = nullptr;
+  uint64_t graph_key = 0;
+};
+
+namespace copa {
+
+enum Slot {
+  SLOT_ORDER = 0,      // int64[K] subject schedule
+  SLOT_SCHED_TMP = 1,  // histogram / counters
+  SLOT_PARTIAL = 2,    // per-warp or per-block FP64 partial sums
+  SLOT_COUNTER = 3,    // int32 work counters
+  SLOT_FIT_GAMMA = 4,  // copa_fit: Gamma
+  SLOT_FIT_T = 5,      // copa_fit: T
+  SLOT_FIT_SMALL = 6,  // copa_fit: F_H, F_V, Grams, Ginv, rho, UtU, fit values
+  SLOT_GINV = 7,       // Ginv + rho for standalone ADMM calls
+  SLOT_SMOOTH = 8,     // smoothing set-up temporaries
+  SLOT_MISC = 9,
+  SLOT_PI = 10,
+};
+
+copa_status_t ws_get(copa_ctx* h, int slot, size_t bytes, void** out);
+copa_status_t fail(copa_ctx* h, copa_status_t code, const std::string& msg);
+copa_status_t cuda_check(copa_ctx* h, cudaError_t e, const char* what);
+TensorView view_of(const copa_tensor_t* X);
+copa_status_t check_tensor_args(copa_ctx* h, const copa_tensor_t* X);
+copa_status_t get_schedule(copa_ctx* h, const TensorView& X, const int64_t** order);
+
+// ---- launchers (host functions, enqueue on h->stream) ----
+template <typename Real>
+copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const Real* H,
+                                const Real* V, const Real* W, double tau, Real* Gamma, Real* T,
+                                Real* Pi, int32_t* rank, Real* F_H);
+template <typename Real>
+copa_status_t launch_mttkrp_h(copa_ctx* h, int64_t K, int R, const Real* T, const Real* W,
+                              Real* F);
+template <typename Real>
+copa_status_t launch_mttkrp_v(copa_ctx* h, const TensorView& X, int R, const Real* Gamma,
+                              const Real* Vp, const Real* H, const Real* W, Real* F,
+                              double* UtU);
+template <typename Real>
+copa_status_t launch_mttkrp_w(copa_ctx* h, int64_t K, int R, const Real* T, const Real* H,
+                              Real* F);
+template <typename Real>
+copa_status_t launch_gram(copa_ctx* h, const Real* A, int64_t rows, int R, double* G);
+template <typename Real>
+copa_status_t launch_chol(copa_ctx* h, const double* Ga, const double* Gb, int R, Real* Ginv,
+                          double* rho_dev);
+template <typename Real>
+copa_status_t launch_admm_rows(copa_ctx* h, const Real* F, const Real* Ginv,
+                               const double* rho_dev, int n_inner, int c, double lam,
+                               Real* Zbar, Real* D, int64_t rows, int R);
+template <typename Real>
+copa_status_t launch_admm_w(copa_ctx* h, const Real* T, const Real* H, const Real* Ginv,
+                            const double* rho_dev, int n_inner, int c, double lam, Real* Wbar,
+                            Real* DW, int64_t K, int R);
+template <typename Real>
+copa_status_t launch_fit_value(copa_ctx* h, int64_t J, int R, const Real* V, const Real* F_V,
+                               const double* UtU, const double* xn2_dev, double x_norm2,
+                               double* fit);
+template <typename Real>
+copa_status_t launch_assemble_q(copa_ctx* h, const TensorView& X, int R, const Real* Gamma,
+                                const Real* Vp, const Real* H, Real* Q, Real* U);
+template <typename Real>
+copa_status_t launch_loss_grad(copa_ctx* h, const TensorView& X, int R, const Real* Gamma,
+                               const Real* T, const Real* Pi, const Real* H, const Real* V,
+                               const Real* W, double* loss, Real* gH, Real* gV, Real* gW);
+copa_status_t launch_validate(copa_ctx* h, const TensorView& X);
+copa_status_t launch_xnorm2(copa_ctx* h, const TensorView& X, double* out);
+
+}  // namespace copa

@@ -1,0 +1,636 @@
+// MTTKRPs on the implicit Y (Algorithm 1, "F = Y_(n)(Khatri-Rao of the others)"), the
+// factor Grams, rho and the cached Cholesky of G + rho I, the ADMM inner loops with the
+// proximal operators of Sec. 3.3 (Eq. Solve_W update rules), the FIT of Sec. 4.1 and
+// the assembly of Q_k and U_k = Q_k H.
+//
+// With Q_k = P_k Gamma_k (P_k = X_k Vp, see k_procrustes.cu) and T_k = Q_k^T X_k Vp:
+//   F_H = sum_k Y_k Vp S_k            = sum_k T_k S_k
+//   F_W(k,s) = (H^T Y_k Vp)(s,s)      = sum_r H(r,s) T_k(r,s)
+//   F_V = sum_k Y_k^T H S_k           = sum_k X_k^T P_k (Gamma_k H S_k)
+// so only F_V streams X again; it scatters x_ij * u_i into F_V(j,:) with
+// u_i = p_i N_k, N_k = Gamma_k H S_k, and accumulates U^T U = sum_i u_i^T u_i.
+#include "copa_internal.cuh"
+
+namespace copa {
+
+namespace {
+
+constexpr int kRegs = (kMaxR + 31) / 32;   // per-lane slots of an R-vector
+
+// ------------------------------------------------------------------------------------
+// F_H = sum_k T_k S_k: blocks reduce chunks of subjects, then a final FP64 reduction
+// ------------------------------------------------------------------------------------
+template <typename Real>
+__global__ void k_mttkrp_h(int64_t K, int R, const Real* __restrict__ T,
+                           const Real* __restrict__ W, double* __restrict__ part) {
+  const int n = R * R;
+  const int64_t per = (K + gridDim.x - 1) / gridDim.x;
+  const int64_t k0 = blockIdx.x * per, k1 = min(K, k0 + per);
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const int s = e % R;
+    Real acc = Real(0);
+    for (int64_t k = k0; k < k1; ++k) acc += T[k * n + e] * W[k * R + s];
+    part[(size_t)blockIdx.x * n + e] = (double)acc;
+  }
+}
+
+template <typename Real>
+__global__ void k_reduce_rows(const double* __restrict__ part, int nparts, int n,
+                              Real* __restrict__ out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int q = 0; q < nparts; ++q) acc += part[(size_t)q * n + e];
+    out[e] = (Real)acc;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// F_W(k,s) = sum_r H(r,s) T_k(r,s): a warp per subject, lanes over s
+// ------------------------------------------------------------------------------------
+template <typename Real>
+__global__ void k_mttkrp_w(int64_t K, int R, const Real* __restrict__ T,
+                           const Real* __restrict__ H, Real* __restrict__ F) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (gridDim.x * (int64_t)blockDim.x) >> 5;
+  for (int64_t k = wid; k < K; k += nw) {
+    for (int s = lane; s < R; s += 32) {
+      Real acc = Real(0);
+      for (int r = 0; r < R; ++r) acc += H[r * R + s] * T[k * R * R + r * R + s];
+      F[k * R + s] = acc;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// F_V = sum_k X_k^T (X_k Vp) Gamma_k H S_k  and  U^T U  (warp per subject, persistent)
+// ------------------------------------------------------------------------------------
+template <typename Real>
+__global__ void __launch_bounds__(128) k_mttkrp_v(
+    TensorView X, int R, const Real* __restrict__ Gamma, const Real* __restrict__ Vp,
+    const Real* __restrict__ H, const Real* __restrict__ W, Real* __restrict__ F,
+    double* __restrict__ utu_part, const int64_t* __restrict__ order, int* __restrict__ counter) {
+  extern __shared__ unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int ldr = R + 1;
+  const int npk = R * (R + 1) / 2;
+  Real* Hs = reinterpret_cast<Real*>(smem_raw);                    // R x R
+  Real* base = Hs + R * R + (size_t)warp * (R * ldr + 3 * R + npk);
+  Real* N = base;              // R x ldr
+  Real* pv = N + R * ldr;      // R
+  Real* uv = pv + R;           // R
+  Real* wv = uv + R;           // R
+  Real* uacc = wv + R;         // npk: this subject's U^T U (packed upper triangle)
+  uint16_t* pk = reinterpret_cast<uint16_t*>(Hs + R * R + (size_t)nwarps * (R * ldr + 3 * R + npk));
+  double* up = utu_part ? utu_part + (size_t)(blockIdx.x * nwarps + warp) * npk : nullptr;
+  for (int i = threadIdx.x; i < R * R; i += blockDim.x) Hs[i] = H[i];
+  for (int e = threadIdx.x; e < npk; e += blockDim.x) {
+    int r = 0, rem = e;
+    while (rem >= R - r) { rem -= R - r; ++r; }
+    pk[e] = (uint16_t)((r << 8) | (r + rem));
+  }
+  if (up)
+    for (int e = lane; e < npk; e += 32) { up[e] = 0.0; uacc[e] = Real(0); }
+  __syncthreads();
+
+  while (true) {
+    int idx = 0;
+    if (lane == 0) idx = atomicAdd(counter, 1);
+    idx = __shfl_sync(0xffffffffu, idx, 0);
+    if (idx >= X.K) break;
+    const int64_t k = order ? order[idx] : idx;
+    const int64_t r0 = X.subj_ptr[k], r1 = X.subj_ptr[k + 1];
+    if (r0 == r1) continue;
+    for (int s = lane; s < R; s += 32) wv[s] = W[k * R + s];
+    __syncwarp();
+    // N = Gamma_k H S_k
+    const Real* Gk = Gamma + k * R * R;
+    for (int e = lane; e < R * R; e += 32) {
+      const int r = e / R, s = e - r * R;
+      Real acc = Real(0);
+      for (int t = 0; t < R; ++t) acc += Gk[r * R + t] * Hs[t * R + s];
+      N[r * ldr + s] = acc * wv[s];
+    }
+    __syncwarp();
+    for (int64_t i = r0; i < r1; ++i) {
+      const int64_t a = X.row_ptr[i], b = X.row_ptr[i + 1];
+      for (int r = lane; r < R; r += 32) {
+        Real acc = Real(0);
+        for (int64_t t = a; t < b; ++t)
+          acc += load_x<Real>(X, t) * __ldg(Vp + (int64_t)__ldg(X.col + t) * R + r);
+        pv[r] = acc;
+      }
+      __syncwarp();
+      Real u[kRegs];
+#pragma unroll
+      for (int q = 0; q < kRegs; ++q) {
+        const int s = lane + 32 * q;
+        Real acc = Real(0);
+        if (s < R)
+          for (int r = 0; r < R; ++r) acc += pv[r] * N[r * ldr + s];
+        u[q] = acc;
+        if (s < R) uv[s] = acc;
+      }
+      for (int64_t t = a; t < b; ++t) {
+        const Real x = load_x<Real>(X, t);
+        const int64_t j = __ldg(X.col + t);
+#pragma unroll
+        for (int q = 0; q < kRegs; ++q) {
+          const int s = lane + 32 * q;
+          if (s < R) atomicAdd(F + j * R + s, x * u[q]);
+        }
+      }
+      __syncwarp();
+      if (up) {
+        for (int e = lane; e < npk; e += 32) {
+          const int r = pk[e] >> 8, s = pk[e] & 255;
+          uacc[e] += uv[r] * uv[s];
+        }
+      }
+      __syncwarp();
+    }
+    if (up)
+      for (int e = lane; e < npk; e += 32) { up[e] += (double)uacc[e]; uacc[e] = Real(0); }
+    __syncwarp();
+  }
+}
+
+// packed (upper-triangle) per-warp partials -> full symmetric FP64 matrix
+__global__ void k_unpack_sym_sum(const double* __restrict__ part, int nparts, int R,
+                                 double* __restrict__ out) {
+  const int npk = R * (R + 1) / 2;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < R * R; e += gridDim.x * blockDim.x) {
+    int r = e / R, s = e % R;
+    if (r > s) { const int t = r; r = s; s = t; }
+    const int pidx = r * R - r * (r - 1) / 2 + (s - r);
+    double acc = 0.0;
+    for (int q = 0; q < nparts; ++q) acc += part[(size_t)q * npk + pidx];
+    out[e] = acc;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Column Gram G = A^T A of a rows x R matrix: block partials (FP64) then reduction
+// ------------------------------------------------------------------------------------
+template <typename Real>
+__global__ void k_gram(const Real* __restrict__ A, int64_t rows, int R, double* __restrict__ part) {
+  extern __shared__ unsigned char smem_raw[];
+  Real* tile = reinterpret_cast<Real*>(smem_raw);   // 64 x R
+  const int npk = R * (R + 1) / 2;
+  const int64_t per = (rows + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = blockIdx.x * per, i1 = min(rows, i0 + per);
+  double acc_d[8];
+  int er[8], es[8];
+  int nl = 0;
+  for (int e = threadIdx.x; e < npk && nl < 8; e += blockDim.x, ++nl) {
+    int r = 0, rem = e;
+    while (rem >= R - r) { rem -= R - r; ++r; }
+    er[nl] = r; es[nl] = r + rem; acc_d[nl] = 0.0;
+  }
+  for (int64_t c0 = i0; c0 < i1; c0 += 64) {
+    const int nrow = (int)min((int64_t)64, i1 - c0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nrow * R; t += blockDim.x) tile[t] = A[c0 * R + t];
+    __syncthreads();
+    for (int q = 0; q < nl; ++q) {
+      Real acc = Real(0);
+      for (int i = 0; i < nrow; ++i) acc += tile[i * R + er[q]] * tile[i * R + es[q]];
+      acc_d[q] += (double)acc;
+    }
+  }
+  for (int q = 0; q < nl; ++q) {
+    part[(size_t)blockIdx.x * R * R + er[q] * R + es[q]] = acc_d[q];
+    part[(size_t)blockIdx.x * R * R + es[q] * R + er[q]] = acc_d[q];
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// G = Ga .* Gb, rho = tr(G)/R, L = chol(G + rho I) (FP64), Ginv = L^{-T} L^{-1}
+// One block; Ginv is stored with leading dimension R + 1 for conflict-free reads.
+// ------------------------------------------------------------------------------------
+template <typename Real>
+__global__ void k_chol(const double* __restrict__ Ga, const double* __restrict__ Gb, int R,
+                       Real* __restrict__ Ginv, double* __restrict__ rho_out,
+                       int* __restrict__ status) {
+  extern __shared__ double sm[];
+  double* A = sm;             // R x R, becomes L (lower)
+  double* Li = A + R * R;     // R x R, L^{-1} (lower)
+  __shared__ double rho_s;
+  __shared__ int bad;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < R * R; e += nt) A[e] = Ga[e] * (Gb ? Gb[e] : 1.0);
+  __syncthreads();
+  if (tid == 0) {
+    double tr = 0.0;
+    for (int i = 0; i < R; ++i) tr += A[i * R + i];
+    rho_s = tr / R;
+    bad = !(rho_s > 0.0) || !isfinite(rho_s);
+  }
+  __syncthreads();
+  for (int i = tid; i < R; i += nt) A[i * R + i] += rho_s;
+  __syncthreads();
+  // right-looking Cholesky
+  for (int j = 0; j < R; ++j) {
+    if (tid == 0) {
+      const double d = A[j * R + j];
+      if (!(d > 0.0) || !isfinite(d)) bad = 1;
+      A[j * R + j] = sqrt(fmax(d, 1e-300));
+    }
+    __syncthreads();
+    const double ljj = A[j * R + j];
+    for (int i = j + 1 + tid; i < R; i += nt) A[i * R + j] /= ljj;
+    __syncthreads();
+    for (int e = tid; e < (R - j - 1) * (R - j - 1); e += nt) {
+      const int i = j + 1 + e / (R - j - 1), c = j + 1 + e % (R - j - 1);
+      if (c <= i) A[i * R + c] -= A[i * R + j] * A[c * R + j];
+    }
+    __syncthreads();
+  }
+  // L^{-1}: column c solves L x = e_c by forward substitution (one thread per column)
+  for (int c = tid; c < R; c += nt) {
+    for (int i = 0; i < R; ++i) {
+      double acc = (i == c) ? 1.0 : 0.0;
+      for (int t = c; t < i; ++t) acc -= A[i * R + t] * Li[t * R + c];
+      Li[i * R + c] = (i < c) ? 0.0 : acc / A[i * R + i];
+    }
+  }
+  __syncthreads();
+  // Ginv = Li^T Li
+  for (int e = tid; e < R * R; e += nt) {
+    const int r = e / R, s = e % R;
+    double acc = 0.0;
+    for (int t = max(r, s); t < R; ++t) acc += Li[t * R + r] * Li[t * R + s];
+    Ginv[r * (R + 1) + s] = (Real)acc;
+  }
+  if (tid == 0) {
+    *rho_out = rho_s;
+    if (bad) set_status(status, COPA_ERR_NUMERIC, 1);
+  }
+}
+
+// ADMM row loop shared by H, V and the fused W kernel. f, zb, d hold the lane's
+// components (s = lane + 32 q); bv is a per-warp shared R-vector.
+template <typename Real>
+__device__ __forceinline__ void admm_row(int R, const Real* __restrict__ Gi, Real rho,
+                                         Real lam_over_rho, int c, int n_inner, const Real* f,
+                                         Real* zb, Real* d, Real* bv) {
+  const int lane = threadIdx.x & 31;
+  for (int it = 0; it < n_inner; ++it) {
+#pragma unroll
+    for (int q = 0; q < kRegs; ++q) {
+      const int s = lane + 32 * q;
+      if (s < R) bv[s] = f[q] + rho * (zb[q] + d[q]);
+    }
+    __syncwarp();
+    Real z[kRegs];
+#pragma unroll
+    for (int q = 0; q < kRegs; ++q) {
+      const int s = lane + 32 * q;
+      Real acc = Real(0);
+      if (s < R)
+        for (int t = 0; t < R; ++t) acc += Gi[s * (R + 1) + t] * bv[t];
+      z[q] = acc;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < kRegs; ++q) {
+      const Real nz = prox<Real>(z[q] - d[q], c, lam_over_rho);
+      d[q] = d[q] + nz - z[q];
+      zb[q] = nz;
+    }
+  }
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(256) k_admm_rows(const Real* __restrict__ F,
+                                                   const Real* __restrict__ Ginv,
+                                                   const double* __restrict__ rho_dev, int n_inner,
+                                                   int c, double lam, Real* __restrict__ Zbar,
+                                                   Real* __restrict__ D, int64_t rows, int R) {
+  extern __shared__ unsigned char smem_raw[];
+  Real* Gi = reinterpret_cast<Real*>(smem_raw);          // R x (R+1)
+  Real* bvall = Gi + R * (R + 1);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Real* bv = bvall + warp * R;
+  for (int e = threadIdx.x; e < R * (R + 1); e += blockDim.x) Gi[e] = Ginv[e];
+  __syncthreads();
+  const double rho = *rho_dev;
+  const Real lor = (Real)(lam / rho);
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (gridDim.x * (int64_t)blockDim.x) >> 5;
+  for (int64_t i = wid; i < rows; i += nw) {
+    Real f[kRegs], zb[kRegs], d[kRegs];
+#pragma unroll
+    for (int q = 0; q < kRegs; ++q) {
+      const int s = lane + 32 * q;
+      f[q] = s < R ? F[i * R + s] : Real(0);
+      zb[q] = s < R ? Zbar[i * R + s] : Real(0);
+      d[q] = s < R ? D[i * R + s] : Real(0);
+    }
+    admm_row<Real>(R, Gi, (Real)rho, lor, c, n_inner, f, zb, d, bv);
+#pragma unroll
+    for (int q = 0; q < kRegs; ++q) {
+      const int s = lane + 32 * q;
+      if (s < R) { Zbar[i * R + s] = zb[q]; D[i * R + s] = d[q]; }
+    }
+    __syncwarp();
+  }
+}
+
+// F_W(k,:) = diag(H^T T_k) fused with the W ADMM (all inner iterations in registers).
+template <typename Real>
+__global__ void __launch_bounds__(256) k_admm_w(const Real* __restrict__ T,
+                                                const Real* __restrict__ H,
+                                                const Real* __restrict__ Ginv,
+                                                const double* __restrict__ rho_dev, int n_inner,
+                                                int c, double lam, Real* __restrict__ Wbar,
+                                                Real* __restrict__ DW, int64_t K, int R) {
+  extern __shared__ unsigned char smem_raw[];
+  Real* Gi = reinterpret_cast<Real*>(smem_raw);          // R x (R+1)
+  Real* Hs = Gi + R * (R + 1);                            // R x R
+  Real* bvall = Hs + R * R;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Real* bv = bvall + warp * R;
+  for (int e = threadIdx.x; e < R * (R + 1); e += blockDim.x) Gi[e] = Ginv[e];
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) Hs[e] = H[e];
+  __syncthreads();
+  const double rho = *rho_dev;
+  const Real lor = (Real)(lam / rho);
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (gridDim.x * (int64_t)blockDim.x) >> 5;
+  for (int64_t k = wid; k < K; k += nw) {
+    const Real* Tk = T + k * R * R;
+    Real f[kRegs], zb[kRegs], d[kRegs];
+#pragma unroll
+    for (int q = 0; q < kRegs; ++q) {
+      const int s = lane + 32 * q;
+      Real acc = Real(0);
+      if (s < R)
+        for (int r = 0; r < R; ++r) acc += Hs[r * R + s] * Tk[r * R + s];
+      f[q] = acc;
+      zb[q] = s < R ? Wbar[k * R + s] : Real(0);
+      d[q] = s < R ? DW[k * R + s] : Real(0);
+    }
+    admm_row<Real>(R, Gi, (Real)rho, lor, c, n_inner, f, zb, d, bv);
+#pragma unroll
+    for (int q = 0; q < kRegs; ++q) {
+      const int s = lane + 32 * q;
+      if (s < R) { Wbar[k * R + s] = zb[q]; DW[k * R + s] = d[q]; }
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// FIT = 1 - (x_norm2 - ||X||^2 + ||X||^2 - 2 <V, F_V> + <V^T V, U^T U>) / x_norm2
+// ------------------------------------------------------------------------------------
+template <typename Real>
+__global__ void k_fit_value(int64_t J, int R, const Real* __restrict__ V, const Real* __restrict__ FV,
+                            const double* __restrict__ UtU, const double* __restrict__ xn2_dev,
+                            double x_norm2, double* __restrict__ fit) {
+  __shared__ double red[2][256];
+  double cross = 0.0, model = 0.0;
+  for (int64_t e = threadIdx.x; e < J * R; e += blockDim.x) cross += (double)V[e] * (double)FV[e];
+  const int npk = R * (R + 1) / 2;
+  for (int e = threadIdx.x; e < npk; e += blockDim.x) {
+    int r = 0, rem = e;
+    while (rem >= R - r) { rem -= R - r; ++r; }
+    const int s = r + rem;
+    double g = 0.0;
+    for (int64_t j = 0; j < J; ++j) g += (double)V[j * R + r] * (double)V[j * R + s];
+    model += (r == s ? 1.0 : 2.0) * g * UtU[r * R + s];
+  }
+  red[0][threadIdx.x] = cross;
+  red[1][threadIdx.x] = model;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + o];
+      red[1][threadIdx.x] += red[1][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double xx = *xn2_dev;
+    const double resid = xx - 2.0 * red[0][0] + red[1][0];
+    const double xn = x_norm2 > 0.0 ? x_norm2 : xx;
+    fit[0] = 1.0 - (xn - xx + resid) / xn;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Q rows q_i = (x_i Vp) Gamma_k and optionally U rows u_i = q_i H
+// ------------------------------------------------------------------------------------
+template <typename Real>
+__global__ void k_assemble_q(TensorView X, int R, const Real* __restrict__ Gamma,
+                             const Real* __restrict__ Vp, const Real* __restrict__ H,
+                             Real* __restrict__ Q, Real* __restrict__ U) {
+  extern __shared__ unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Real* pv = reinterpret_cast<Real*>(smem_raw) + warp * 2 * R;
+  Real* qv = pv + R;
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (gridDim.x * (int64_t)blockDim.x) >> 5;
+  for (int64_t k = wid; k < X.K; k += nw) {
+    const Real* Gk = Gamma + k * R * R;
+    for (int64_t i = X.subj_ptr[k]; i < X.subj_ptr[k + 1]; ++i) {
+      const int64_t a = X.row_ptr[i], b = X.row_ptr[i + 1];
+      for (int r = lane; r < R; r += 32) {
+        Real acc = Real(0);
+        for (int64_t t = a; t < b; ++t) acc += load_x<Real>(X, t) * Vp[(int64_t)X.col[t] * R + r];
+        pv[r] = acc;
+      }
+      __syncwarp();
+      for (int s = lane; s < R; s += 32) {
+        Real acc = Real(0);
+        for (int r = 0; r < R; ++r) acc += pv[r] * Gk[r * R + s];
+        qv[s] = acc;
+        Q[i * R + s] = acc;
+      }
+      __syncwarp();
+      if (U) {
+        for (int s = lane; s < R; s += 32) {
+          Real acc = Real(0);
+          for (int r = 0; r < R; ++r) acc += qv[r] * H[r * R + s];
+          U[i * R + s] = acc;
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+}  // namespace
+
+// ---------------------------------- launchers ----------------------------------------
+
+static int grid_for(copa_ctx* h, int64_t work_items, int per_block, int cap_per_sm = 8) {
+  int64_t blocks = (work_items + per_block - 1) / per_block;
+  const int64_t cap = (int64_t)h->num_sms * cap_per_sm;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  return (int)blocks;
+}
+
+template <typename Real>
+copa_status_t launch_mttkrp_h(copa_ctx* h, int64_t K, int R, const Real* T, const Real* W, Real* F) {
+  const int blocks = grid_for(h, K, 512, 4);
+  double* part = nullptr;
+  copa_status_t st;
+  if ((st = ws_get(h, SLOT_PARTIAL, (size_t)blocks * R * R * sizeof(double), (void**)&part)) != COPA_OK)
+    return st;
+  k_mttkrp_h<Real><<<blocks, 256, 0, h->stream>>>(K, R, T, W, part);
+  k_reduce_rows<Real><<<(R * R + 255) / 256, 256, 0, h->stream>>>(part, blocks, R * R, F);
+  return cuda_check(h, cudaGetLastError(), "k_mttkrp_h");
+}
+
+template <typename Real>
+copa_status_t launch_mttkrp_w(copa_ctx* h, int64_t K, int R, const Real* T, const Real* H, Real* F) {
+  k_mttkrp_w<Real><<<grid_for(h, K, 8, 16), 256, 0, h->stream>>>(K, R, T, H, F);
+  return cuda_check(h, cudaGetLastError(), "k_mttkrp_w");
+}
+
+template <typename Real>
+copa_status_t launch_mttkrp_v(copa_ctx* h, const TensorView& X, int R, const Real* Gamma,
+                              const Real* Vp, const Real* H, const Real* W, Real* F, double* UtU) {
+  if (R > kMaxR) return fail(h, COPA_ERR_UNSUPPORTED, "mttkrp V: R too large");
+  copa_status_t st;
+  const int npk0 = R * (R + 1) / 2;
+  const size_t per_warp = sizeof(Real) * ((size_t)R * (R + 1) + 3 * (size_t)R + npk0);
+  const size_t fixed = sizeof(Real) * (size_t)R * R + sizeof(uint16_t) * npk0 + 64;
+  int warps = 4;
+  while (warps > 1 && fixed + warps * per_warp > 200 * 1024) --warps;
+  const size_t smem = fixed + warps * per_warp;
+  if ((st = cuda_check(h, cudaFuncSetAttribute(k_mttkrp_v<Real>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem), "cudaFuncSetAttribute")) != COPA_OK)
+    return st;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mttkrp_v<Real>, 32 * warps, smem);
+  if (per_sm < 1) per_sm = 1;
+  int64_t blocks = (int64_t)h->num_sms * per_sm;
+  const int64_t need = (X.K + warps - 1) / warps;
+  if (blocks > need) blocks = need > 0 ? need : 1;
+  const int64_t* order = nullptr;
+  if ((st = get_schedule(h, X, &order)) != COPA_OK) return st;
+  int* counter = nullptr;
+  if ((st = ws_get(h, SLOT_COUNTER, 64, (void**)&counter)) != COPA_OK) return st;
+  const int npk = R * (R + 1) / 2;
+  double* part = nullptr;
+  const int nparts = (int)blocks * warps;
+  if (UtU) {
+    if ((st = ws_get(h, SLOT_PARTIAL, (size_t)nparts * npk * sizeof(double), (void**)&part)) != COPA_OK)
+      return st;
+  }
+  if ((st = cuda_check(h, cudaMemsetAsync(counter + 1, 0, sizeof(int), h->stream), "memset")) != COPA_OK)
+    return st;
+  if ((st = cuda_check(h, cudaMemsetAsync(F, 0, sizeof(Real) * (size_t)X.J * R, h->stream), "memset F")) != COPA_OK)
+    return st;
+  k_mttkrp_v<Real><<<(unsigned)blocks, 32 * warps, smem, h->stream>>>(X, R, Gamma, Vp, H, W, F, part,
+                                                                         order, counter + 1);
+  if ((st = cuda_check(h, cudaGetLastError(), "k_mttkrp_v")) != COPA_OK) return st;
+  if (UtU) {
+    // packed partials -> full symmetric UtU
+    k_unpack_sym_sum<<<(R * R + 255) / 256, 256, 0, h->stream>>>(part, nparts, R, UtU);
+    if ((st = cuda_check(h, cudaGetLastError(), "k_unpack_sym_sum")) != COPA_OK) return st;
+  }
+  return COPA_OK;
+}
+
+template <typename Real>
+copa_status_t launch_gram(copa_ctx* h, const Real* A, int64_t rows, int R, double* G) {
+  const int npk = R * (R + 1) / 2;
+  const int threads = npk <= 256 ? 256 : 512;
+  if (npk > threads * 8) return fail(h, COPA_ERR_UNSUPPORTED, "gram: R too large");
+  const int blocks = grid_for(h, rows, 2048, 2);
+  double* part = nullptr;
+  copa_status_t st;
+  if ((st = ws_get(h, SLOT_MISC, (size_t)blocks * R * R * sizeof(double), (void**)&part)) != COPA_OK)
+    return st;
+  const size_t smem = sizeof(Real) * 64 * (size_t)R;
+  k_gram<Real><<<blocks, threads, smem, h->stream>>>(A, rows, R, part);
+  k_reduce_rows<double><<<(R * R + 255) / 256, 256, 0, h->stream>>>(part, blocks, R * R, G);
+  return cuda_check(h, cudaGetLastError(), "k_gram");
+}
+
+template <typename Real>
+copa_status_t launch_chol(copa_ctx* h, const double* Ga, const double* Gb, int R, Real* Ginv,
+                          double* rho_dev) {
+  const size_t smem = 2 * sizeof(double) * R * R;
+  copa_status_t st;
+  if ((st = cuda_check(h, cudaFuncSetAttribute(k_chol<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem), "cudaFuncSetAttribute")) != COPA_OK)
+    return st;
+  k_chol<Real><<<1, 128, smem, h->stream>>>(Ga, Gb, R, Ginv, rho_dev, h->d_status);
+  return cuda_check(h, cudaGetLastError(), "k_chol");
+}
+
+template <typename Real>
+copa_status_t launch_admm_rows(copa_ctx* h, const Real* F, const Real* Ginv, const double* rho_dev,
+                               int n_inner, int c, double lam, Real* Zbar, Real* D, int64_t rows,
+                               int R) {
+  const size_t smem = sizeof(Real) * ((size_t)R * (R + 1) + 8 * (size_t)R);
+  copa_status_t st;
+  if ((st = cuda_check(h, cudaFuncSetAttribute(k_admm_rows<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem), "cudaFuncSetAttribute")) != COPA_OK)
+    return st;
+  k_admm_rows<Real><<<grid_for(h, rows, 8, 8), 256, smem, h->stream>>>(F, Ginv, rho_dev, n_inner, c, lam,
+                                                                      Zbar, D, rows, R);
+  return cuda_check(h, cudaGetLastError(), "k_admm_rows");
+}
+
+template <typename Real>
+copa_status_t launch_admm_w(copa_ctx* h, const Real* T, const Real* H, const Real* Ginv,
+                            const double* rho_dev, int n_inner, int c, double lam, Real* Wbar,
+                            Real* DW, int64_t K, int R) {
+  const size_t smem = sizeof(Real) * ((size_t)R * (R + 1) + (size_t)R * R + 8 * (size_t)R);
+  copa_status_t st;
+  if ((st = cuda_check(h, cudaFuncSetAttribute(k_admm_w<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem), "cudaFuncSetAttribute")) != COPA_OK)
+    return st;
+  k_admm_w<Real><<<grid_for(h, K, 8, 8), 256, smem, h->stream>>>(T, H, Ginv, rho_dev, n_inner, c, lam,
+                                                                 Wbar, DW, K, R);
+  return cuda_check(h, cudaGetLastError(), "k_admm_w");
+}
+
+template <typename Real>
+copa_status_t launch_fit_value(copa_ctx* h, int64_t J, int R, const Real* V, const Real* F_V,
+                               const double* UtU, const double* xn2_dev, double x_norm2, double* fit) {
+  k_fit_value<Real><<<1, 256, 0, h->stream>>>(J, R, V, F_V, UtU, xn2_dev, x_norm2, fit);
+  return cuda_check(h, cudaGetLastError(), "k_fit_value");
+}
+
+template <typename Real>
+copa_status_t launch_assemble_q(copa_ctx* h, const TensorView& X, int R, const Real* Gamma,
+                                const Real* Vp, const Real* H, Real* Q, Real* U) {
+  const size_t smem = sizeof(Real) * 8 * 2 * (size_t)R;
+  k_assemble_q<Real><<<grid_for(h, X.K, 8, 16), 256, smem, h->stream>>>(X, R, Gamma, Vp, H, Q, U);
+  return cuda_check(h, cudaGetLastError(), "k_assemble_q");
+}
+
+#define COPA_INST(Real)                                                                          \
+  template copa_status_t launch_mttkrp_h<Real>(copa_ctx*, int64_t, int, const Real*, const Real*, \
+                                               Real*);                                            \
+  template copa_status_t launch_mttkrp_w<Real>(copa_ctx*, int64_t, int, const Real*, const Real*, \
+                                               Real*);                                            \
+  template copa_status_t launch_mttkrp_v<Real>(copa_ctx*, const TensorView&, int, const Real*,    \
+                                               const Real*, const Real*, const Real*, Real*,      \
+                                               double*);                                          \
+  template copa_status_t launch_gram<Real>(copa_ctx*, const Real*, int64_t, int, double*);        \
+  template copa_status_t launch_chol<Real>(copa_ctx*, const double*, const double*, int, Real*,   \
+                                           double*);                                              \
+  template copa_status_t launch_admm_rows<Real>(copa_ctx*, const Real*, const Real*,              \
+                                                const double*, int, int, double, Real*, Real*,    \
+                                                int64_t, int);                                    \
+  template copa_status_t launch_admm_w<Real>(copa_ctx*, const Real*, const Real*, const Real*,    \
+                                             const double*, int, int, double, Real*, Real*,       \
+                                             int64_t, int);                                       \
+  template copa_status_t launch_fit_value<Real>(copa_ctx*, int64_t, int, const Real*, const Real*, \
+                                                const double*, const double*, double, double*);   \
+  template copa_status_t launch_assemble_q<Real>(copa_ctx*, const TensorView&, int, const Real*,  \
+                                                 const Real*, const Real*, Real*, Real*);
+COPA_INST(float)
+COPA_INST(double)
+
+}  // namespace copa
+

@@ -299,3 +299,39 @@ def random_state(K: int, J: int, R: int, seed: int = 3):
     V = rng.random((J, R)) * (rng.random((J, R)) >= 0.3)
     W = rng.random((K, R)) * (rng.random((K, R)) >= 0.2)
     return H, V, W
+
+
+def from_dense(slices, J: int, days=None) -> SparseTensor:
+    """Pack dense per-subject slices (list of I_k x J arrays) into the CSR container;
+    exact zeros are not stored, so all-zero rows become empty rows."""
+    sizes = np.array([s.shape[0] for s in slices], dtype=np.int64)
+    cols, vals, lens = [], [], []
+    for s in slices:
+        for row in s:
+            nz = np.nonzero(row)[0]
+            cols.append(nz.astype(np.int32))
+            vals.append(row[nz].astype(np.float64))
+            lens.append(len(nz))
+    subj_ptr = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    row_ptr = np.concatenate([[0], np.cumsum(np.array(lens, dtype=np.int64))]).astype(np.int64)
+    col = np.concatenate(cols).astype(np.int32) if cols else np.zeros(0, np.int32)
+    val = np.concatenate(vals) if vals else np.zeros(0)
+    return SparseTensor(len(slices), J, subj_ptr, row_ptr, col, val, days)
+
+
+def with_edge_cases(X: SparseTensor, seed: int = 7) -> SparseTensor:
+    """Copy of X with an empty subject inserted at the front, in the middle and at the
+    end, and the first visit of every 5th subject emptied (a visit with no codes)."""
+    rng = np.random.default_rng(seed)
+    slices = [X.dense(k) for k in range(X.K)]
+    for k in range(0, len(slices), 5):
+        if slices[k].shape[0]:
+            slices[k][0, :] = 0.0
+    e = np.zeros((0, X.J))
+    mid = len(slices) // 2
+    slices = [e] + slices[:mid] + [e] + slices[mid:] + [e]
+    days = None
+    if X.days is not None:
+        days = np.concatenate([np.sort(rng.integers(0, 500, size=s.shape[0])).astype(np.float64)
+                               for s in slices]) if slices else None
+    return from_dense(slices, X.J, days)

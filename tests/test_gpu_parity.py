@@ -1,0 +1,367 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, step by step.
+
+Each step of the GPU path is fed the same state as the oracle step (step-isolated) and
+compared element-wise. Tolerances: the FP64 handle must agree to 1e-10 relative
+(Frobenius, per step); the mixed handle (FP32 bulk, FP64 Gram/eigen/Cholesky) to 1e-5
+relative per step. Subjects whose Procrustes spectrum has an eigenvalue ratio within a
+factor 100 of the rank cut tau are excluded from element-wise checks (counted)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import copa_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "mixed": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_1803_04572_gb300 as P
+    return P
+
+
+@pytest.fixture(scope="module", params=["fp64", "mixed"])
+def h(request, P):
+    return P.Copa(0, request.param)
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def T(h, a):
+    return h.torch.as_tensor(np.ascontiguousarray(a), dtype=h.dtype, device=h.device)
+
+
+def N(t):
+    return t.detach().double().cpu().numpy()
+
+
+def dev_tensor(h, P, X):
+    vd = "f64" if h.precision == "fp64" else ("bf16" if np.all(X.val == np.rint(X.val)) and
+                                               np.abs(X.val).max(initial=0) <= 256 else "f32")
+    return P.DeviceTensor.from_host(X, h.device, vd)
+
+
+def band_subjects(X, H, V, W, tau=O.TAU):
+    """Subjects whose eigenvalue ratios of A_k^T A_k fall within [tau/100, 100 tau]."""
+    out = set()
+    for k in range(X.K):
+        A = X.dense(k) @ V @ np.diag(W[k]) @ H.T
+        if A.shape[0] == 0:
+            continue
+        s = np.linalg.svd(A, compute_uv=False)
+        if s.size and s[0] > 0:
+            r = (s / s[0]) ** 2
+            if np.any((r >= tau / 100) & (r <= tau * 100)):
+                out.add(k)
+    return out
+
+
+CASES = [
+    # K, J, R, median visits, lo, hi
+    (150, 40, 5, 8, 1, 30),
+    (120, 60, 12, 10, 1, 40),
+    (60, 90, 40, 25, 1, 120),
+    (40, 50, 7, 6, 1, 20),     # odd R
+]
+
+
+def make_case(K, J, R, med, lo, hi, seed=0):
+    X = synth.ehr_custom(K, J, median=med, lo=lo, hi=hi, lam=3.0, cmax=20, seed=seed)
+    X = synth.with_edge_cases(X)
+    H, V, W = synth.random_state(X.K, X.J, R, seed=seed + 11)
+    return X, H, V, W
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_procrustes_step(h, P, case):
+    K, J, R, med, lo, hi = case
+    X, H, V, W = make_case(K, J, R, med, lo, hi)
+    Xd = dev_tensor(h, P, X)
+    st = h.procrustes(Xd, R, T(h, H), T(h, V), T(h, W), want_pi=True, want_rank=True)
+    Q, U = h.assemble_q(Xd, R, st, T(h, V), T(h, H))
+    h.sync()
+    Qg, Ug, Tg, Pig = N(Q), N(U), N(st["T"]), N(st["Pi"])
+    rank = st["rank"].cpu().numpy()
+    skip = band_subjects(X, H, V, W)
+    tol = TOL[h.precision]
+    num_q = den_q = num_t = den_t = 0.0
+    FH = np.zeros((R, R))
+    for k in range(X.K):
+        Xk = X.dense(k)
+        Qo = O.procrustes(Xk, V, W[k], H)
+        To = Qo.T @ Xk @ V
+        FH += To @ np.diag(W[k])
+        if k in skip:
+            continue
+        rows = slice(X.subj_ptr[k], X.subj_ptr[k + 1])
+        num_q += np.sum((Qg[rows] - Qo) ** 2)
+        den_q += np.sum(Qo ** 2)
+        num_t += np.sum((Tg[k] - To) ** 2)
+        den_t += np.sum(To ** 2)
+        np.testing.assert_allclose(Ug[rows], Qo @ H, atol=10 * tol * max(1.0, np.abs(Qo @ H).max(initial=0)))
+        assert rank[k] == (np.linalg.matrix_rank(Qo, tol=0.5) if Qo.size else 0)
+        np.testing.assert_allclose(Pig[k], Qo.T @ Qo, atol=100 * tol)
+    assert np.sqrt(num_q / den_q) <= tol, np.sqrt(num_q / den_q)
+    assert np.sqrt(num_t / den_t) <= tol, np.sqrt(num_t / den_t)
+    if not skip:
+        assert rel(N(st["F_H"]), FH) <= tol
+    assert len(skip) <= X.K // 10
+
+
+def _state_after_procrustes(X, H, V, W):
+    Q = [O.procrustes(X.dense(k), V, W[k], H) for k in range(X.K)]
+    return Q, O.project_all(X, Q)
+
+
+@pytest.mark.parametrize("case", CASES[:3])
+def test_mttkrp_steps(h, P, case):
+    K, J, R, med, lo, hi = case
+    X, H, V, W = make_case(K, J, R, med, lo, hi, seed=1)
+    Xd = dev_tensor(h, P, X)
+    st = h.procrustes(Xd, R, T(h, H), T(h, V), T(h, W))
+    Q, sl = _state_after_procrustes(X, H, V, W)
+    H2, _, W2 = synth.random_state(X.K, X.J, R, seed=99)      # "updated" H and W
+    tol = TOL[h.precision]
+    FH = h.mttkrp("H", Xd, R, st, W=T(h, W))
+    FW = h.mttkrp("W", Xd, R, st, H=T(h, H2))
+    FV, UtU = h.mttkrp("V", Xd, R, st, Vp=T(h, V), H=T(h, H2), W=T(h, W2), want_utu=True)
+    h.sync()
+    assert rel(N(FH), O.mttkrp_H(sl, V, W)) <= tol
+    assert rel(N(FW), O.mttkrp_W(sl, H2, V)) <= tol
+    assert rel(N(FV), O.mttkrp_V(sl, H2, W2, X.J)) <= tol
+    Uo = sum(np.diag(W2[k]) @ H2.T @ Q[k].T @ Q[k] @ H2 @ np.diag(W2[k]) for k in range(X.K))
+    assert rel(N(UtU), Uo) <= tol
+
+
+@pytest.mark.parametrize("constraint,lam", [("none", 0.0), ("nonneg", 0.0), ("l1", 0.8), ("l0", 0.5)])
+def test_admm_step_rows(h, P, constraint, lam):
+    rng = np.random.default_rng(5)
+    rows, R = 133, 9
+    A, B = rng.random((50, R)), rng.random((70, R))
+    Ga, Gb = A.T @ A, B.T @ B
+    F = rng.standard_normal((rows, R)) * 20
+    Zb0, D0 = rng.standard_normal((rows, R)), rng.standard_normal((rows, R)) * 0.1
+    _, Zo, Do, rho_o, _ = O.admm(F, Ga * Gb, Zb0, D0, 15, constraint, lam)
+    Zb, D = T(h, Zb0), T(h, D0)
+    rho = h.admm_step(T(h, F), h.torch.as_tensor(Ga, device=h.device),
+                      h.torch.as_tensor(Gb, device=h.device), 15, constraint, lam, Zb, D)
+    h.sync()
+    tol = TOL[h.precision]
+    assert abs(float(rho.cpu()[0]) - rho_o) <= 1e-12 * rho_o
+    if constraint in ("none", "nonneg", "l1"):
+        assert rel(N(Zb), Zo) <= 10 * tol
+        assert rel(N(D), Do) <= 10 * tol
+    else:   # l0 is discontinuous: compare away from the threshold
+        v = Zo - Do
+        ok = np.abs(N(Zb) - Zo) <= 10 * tol * (1 + np.abs(Zo))
+        assert ok.mean() > 0.97
+
+
+def test_admm_w_fused(h, P):
+    X, H, V, W = make_case(100, 30, 6, 8, 1, 25, seed=2)
+    R = 6
+    Xd = dev_tensor(h, P, X)
+    st = h.procrustes(Xd, R, T(h, H), T(h, V), T(h, W))
+    Q, sl = _state_after_procrustes(X, H, V, W)
+    H2 = np.abs(synth.random_state(X.K, X.J, R, seed=4)[0])
+    Ga, Gb = H2.T @ H2, V.T @ V
+    D0 = np.random.default_rng(0).standard_normal((X.K, R)) * 0.01
+    _, Wo, Do, _, _ = O.admm(O.mttkrp_W(sl, H2, V), Ga * Gb, W, D0, 10, O.NONNEG)
+    Wb, DW = T(h, W), T(h, D0)
+    h.admm_w_fused(st, T(h, H2), h.torch.as_tensor(Ga, device=h.device), h.torch.as_tensor(Gb, device=h.device),
+                   10, "nonneg", 0.0, Wb, DW)
+    h.sync()
+    assert rel(N(Wb), Wo) <= 10 * TOL[h.precision]
+    assert rel(N(DW), Do) <= 10 * TOL[h.precision]
+
+
+def test_gram(h, P):
+    rng = np.random.default_rng(3)
+    for rows, R in [(1, 1), (5000, 13), (70001, 40)]:
+        A = rng.standard_normal((rows, R))
+        G = h.gram(T(h, A))
+        h.sync()
+        assert rel(N(G), A.T @ A) <= TOL[h.precision]
+
+
+def test_fit_value_matches_dense_reconstruction(h, P):
+    X, H, V, W = make_case(80, 35, 5, 9, 1, 30, seed=6)
+    R = 5
+    Xd = dev_tensor(h, P, X)
+    st = h.procrustes(Xd, R, T(h, H), T(h, V), T(h, W))
+    H2, V2, W2 = synth.random_state(X.K, X.J, R, seed=8)
+    FV, UtU = h.mttkrp("V", Xd, R, st, Vp=T(h, V), H=T(h, H2), W=T(h, W2), want_utu=True)
+    fit = h.fit_value(Xd, R, T(h, V2), FV, UtU)
+    h.sync()
+    Q = [O.procrustes(X.dense(k), V, W[k], H) for k in range(X.K)]
+    fo = O.fit_value(X, Q, H2, V2, W2)
+    assert abs(float(fit.cpu()[0]) - fo) <= (1e-9 if h.precision == "fp64" else 1e-5) * max(1, abs(fo))
+
+
+def _trajectory(h, P, X, R, opt_o, n_outer, init, use_graph):
+    H0, V0, W0 = init
+    _, hist_o, rec = O.fit(X, H0, V0, W0, opt_o, n_outer)
+    Xd = dev_tensor(h, P, X)
+    H, V, W = T(h, H0), T(h, V0), T(h, W0)
+    opt = P.Options(R, n_outer=n_outer, n_inner=opt_o.n_inner, c_H=opt_o.c_H, c_W=opt_o.c_W,
+                    c_V=opt_o.c_V, lam_H=opt_o.lam_H, lam_W=opt_o.lam_W, lam_V=opt_o.lam_V,
+                    use_graph=use_graph)
+    hist = h.fit(Xd, opt, H, V, W)
+    return hist, hist_o, (N(H), N(V), N(W)), rec
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_fit_trajectory_planted(h, P, use_graph):
+    """The K=200, J=100, R=5 planted workload: non-negative W, l1 V, 20 outer x 10 inner."""
+    X, _ = synth.planted_small()
+    R = 5
+    init = synth.init_factors(X.K, X.J, R)
+    opt_o = O.Options(n_inner=10, c_H=O.NONE, c_W=O.NONNEG, c_V=O.L1, lam_V=1.0)
+    hist, hist_o, (H, V, W), rec = _trajectory(h, P, X, R, opt_o, 20, init, use_graph)
+    if h.precision == "fp64":
+        np.testing.assert_allclose(hist, hist_o, atol=1e-8)
+        assert rel(H, rec.state.H) <= 1e-7 and rel(W, rec.state.W) <= 1e-7 and rel(V, rec.state.V) <= 1e-7
+    else:
+        np.testing.assert_allclose(hist, hist_o, atol=1e-4)
+    assert O.sparsity(V) == pytest.approx(O.sparsity(rec.state.V), abs=0.02)
+
+
+def test_fit_trajectory_ehr_unconstrained_l0(h, P):
+    X = synth.ehr_custom(300, 50, median=12, lo=1, hi=60, lam=3.0, cmax=20, seed=4)
+    R = 6
+    init = synth.init_factors(X.K, X.J, R)
+    opt_o = O.Options(n_inner=8, c_H=O.NONNEG, c_W=O.NONE, c_V=O.L0, lam_V=0.05)
+    hist, hist_o, _, _ = _trajectory(h, P, X, R, opt_o, 6, init, True)
+    np.testing.assert_allclose(hist, hist_o, atol=1e-8 if h.precision == "fp64" else 1e-4)
+
+
+def test_loss_and_gradient(h, P):
+    X = synth.ehr_custom(50, 30, median=10, lo=2, hi=30, lam=3.0, cmax=10, seed=9)
+    R = 4
+    H, V, W = synth.random_state(X.K, X.J, R, seed=10)
+    Xd = dev_tensor(h, P, X)
+    st = h.procrustes(Xd, R, T(h, H), T(h, V), T(h, W), want_pi=True)
+    loss, gH, gV, gW = h.loss_grad(Xd, R, st, T(h, H), T(h, V), T(h, W))
+    h.sync()
+    Q = [O.procrustes(X.dense(k), V, W[k], H) for k in range(X.K)]
+    Lo, gHo, gVo, gWo = O.loss_and_grad(X, Q, H, V, W)
+    tol = 1e-9 if h.precision == "fp64" else 1e-5
+    assert abs(float(loss.cpu()[0]) - Lo) <= tol * Lo
+    assert rel(N(gH), gHo) <= tol
+    assert rel(N(gV), gVo) <= tol
+    assert rel(N(gW), gWo) <= tol
+
+
+def test_autograd_function(P):
+    import torch
+    hd = P.Copa(0, "fp64")
+    X = synth.ehr_custom(30, 20, median=8, lo=2, hi=20, lam=2.0, cmax=10, seed=12)
+    R = 3
+    H, V, W = synth.random_state(X.K, X.J, R, seed=13)
+    Xd = P.DeviceTensor.from_host(X, hd.device, "f64")
+    Ht, Vt, Wt = (torch.tensor(a, device=hd.device, requires_grad=True) for a in (H, V, W))
+    L = P.reconstruction_loss(hd, Xd, Ht, Vt, Wt)
+    L.backward()
+    Q = [O.procrustes(X.dense(k), V, W[k], H) for k in range(X.K)]
+    Lo, gHo, gVo, gWo = O.loss_and_grad(X, Q, H, V, W)
+    assert abs(L.item() - Lo) <= 1e-9 * Lo
+    assert rel(Ht.grad.cpu().numpy(), gHo) <= 1e-9
+    assert rel(Vt.grad.cpu().numpy(), gVo) <= 1e-9
+    assert rel(Wt.grad.cpu().numpy(), gWo) <= 1e-9
+
+
+def test_smoothing_projection(h, P):
+    X = synth.ehr_custom(90, 40, median=9, lo=1, hi=40, lam=2.0, cmax=8, seed=5, with_days=True)
+    X = synth.with_edge_cases(X)
+    Cs, Xp_o = O.smooth_project(X)
+    Xd = dev_tensor(h, P, X)
+    days = h.torch.as_tensor(X.days, dtype=h.torch.float64, device=h.device)
+    Xp, C = h.smooth(Xd, days, 7, 3, out_dtype="f64" if h.precision == "fp64" else "f32", want_C=True)
+    h.sync()
+    sp = Xp.subj_ptr.cpu().numpy()
+    rp, col, val = Xp.row_ptr.cpu().numpy(), Xp.col.cpu().numpy(), Xp.vals.double().cpu().numpy()
+    Cg = C.cpu().numpy()
+    tol = 1e-10 if h.precision == "fp64" else 1e-6
+    for k in range(X.K):
+        rk = sp[k + 1] - sp[k]
+        assert rk == Cs[k].shape[1]
+        dense = np.zeros((rk, X.J))
+        for q in range(rk):
+            i = sp[k] + q
+            dense[q, col[rp[i]:rp[i + 1]]] = val[rp[i]:rp[i + 1]]
+        # invariant to the choice of orthonormal basis: X'^T X' and C C^T
+        np.testing.assert_allclose(dense.T @ dense, Xp_o[k].T @ Xp_o[k], atol=tol * max(1, np.abs(Xp_o[k]).max(initial=0) ** 2))
+        rows = slice(X.subj_ptr[k], X.subj_ptr[k + 1])
+        Ck = Cg[rows, :rk]
+        np.testing.assert_allclose(Ck @ Ck.T, Cs[k] @ Cs[k].T, atol=1e-10)
+
+
+def test_fit_on_smoothed_projection_matches_oracle(h, P):
+    X = synth.ehr_custom(120, 40, median=10, lo=2, hi=40, lam=3.0, cmax=10, seed=14, with_days=True)
+    Cs, Xp_o = O.smooth_project(X)
+    Xo = O.slices_to_tensor(Xp_o, X.J)
+    R = 4
+    init = synth.init_factors(X.K, X.J, R)
+    opt_o = O.Options(n_inner=10, c_H=O.NONE, c_W=O.NONNEG, c_V=O.L1, lam_V=0.5)
+    xn2 = O.data_norm2(X)
+    st_o, hist_o, _ = O.fit(Xo, *init, opt_o, 5, x_norm2=xn2)
+    Xd = dev_tensor(h, P, X)
+    days = h.torch.as_tensor(X.days, dtype=h.torch.float64, device=h.device)
+    Xp, _ = h.smooth(Xd, days, 7, 3, out_dtype="f64" if h.precision == "fp64" else "f32")
+    H, V, W = (T(h, a) for a in init)
+    opt = P.Options(R, n_outer=5, n_inner=10, c_V="l1", lam_V=0.5, x_norm2=xn2)
+    hist = h.fit(Xp, opt, H, V, W)
+    np.testing.assert_allclose(hist, hist_o, atol=1e-8 if h.precision == "fp64" else 1e-4)
+
+
+def test_validation_and_argument_errors(h, P):
+    X = synth.ehr_custom(20, 10, median=4, lo=1, hi=8, seed=3)
+    Xd = dev_tensor(h, P, X)
+    h.validate(Xd)
+    bad = P.DeviceTensor(Xd.K, Xd.J, Xd.subj_ptr, Xd.row_ptr, Xd.col.clone(), Xd.vals, Xd.val_dtype)
+    bad.col[3] = 10   # col >= J
+    with pytest.raises(P.CopaError) as e:
+        h.validate(bad)
+    assert e.value.code == P.ERR_INVALID_ARG
+    H, V, W = synth.random_state(X.K, X.J, 3)
+    with pytest.raises(P.CopaError) as e:
+        h.procrustes(Xd, 0, T(h, H), T(h, V), T(h, W))
+    assert e.value.code == P.ERR_INVALID_ARG
+    with pytest.raises(P.CopaError) as e:
+        h.procrustes(Xd, 97, T(h, np.eye(97)), T(h, np.ones((10, 97))), T(h, np.ones((20, 97))))
+    assert e.value.code == P.ERR_UNSUPPORTED
+    h.validate(Xd)   # the handle is still usable
+
+
+def test_numeric_error_is_reported(h, P):
+    """G = 0 (all-zero factor) makes G + rho I singular: COPA_ERR_NUMERIC at the next sync."""
+    R = 3
+    Z = h.torch.zeros(R, R, dtype=h.torch.float64, device=h.device)
+    Zb, D = h.zeros(4, R), h.zeros(4, R)
+    h.admm_step(h.zeros(4, R), Z, None, 3, "none", 0.0, Zb, D)
+    with pytest.raises(P.CopaError) as e:
+        h.sync()
+    assert e.value.code == P.ERR_NUMERIC
+    h.sync()   # the status word was cleared
+
+
+def test_host_entry_point_matches_device_fit(P):
+    X, _ = synth.planted_small(K=60, J=40, R=4, seed=3)
+    R = 4
+    H0, V0, W0 = synth.init_factors(X.K, X.J, R)
+    hd = P.Copa(0, "mixed")
+    opt = P.Options(R, n_outer=4, n_inner=5)
+    Hh, Vh, Wh = (np.ascontiguousarray(a, dtype=np.float32) for a in (H0, V0, W0))
+    hist_h = hd.fit_host(X, opt, Hh, Vh, Wh)
+    Xd = P.DeviceTensor.from_host(X, hd.device, "f32")
+    Ht, Vt, Wt = (hd.torch.as_tensor(a, device=hd.device) for a in (H0.astype(np.float32), V0.astype(np.float32),
+                                                                     W0.astype(np.float32)))
+    hist_d = hd.fit(Xd, opt, Ht, Vt, Wt)
+    np.testing.assert_allclose(hist_h, hist_d, atol=1e-6)
+    np.testing.assert_allclose(Vh, Vt.cpu().numpy(), atol=1e-5)

@@ -73,15 +73,15 @@ typedef struct {
   int32_t val_dtype;        /* copa_val_dtype_t */
 } copa_tensor_t;
 
-/* Per-subject result of the Procrustes step (caller-owned device buffers).
- * Q_k is kept implicitly as Q_k = X_k V Gamma_k, which is exact: Q_k = A_k Omega_k with
- * A_k = X_k V S_k H^T and Omega_k = (A_k^T A_k)^(-1/2) on the kept eigenvectors, so
- * Gamma_k = S_k H^T Omega_k. */
+/* Result of the Procrustes step (caller-owned device buffers).
+ * Q holds Q_k for every subject explicitly, row i of Q being row (i - subj_ptr[k]) of
+ * Q_k for the subject k owning visit i; Y_k = Q_k^T X_k stays implicit: the MTTKRPs use
+ * T_k = Q_k^T X_k V (= Y_k V) and Q itself. */
 typedef struct {
-  void* Gamma;     /* real[K*R*R], required: Gamma_k */
-  void* T;         /* real[K*R*R], required: T_k = Q_k^T X_k V (= Y_k V) */
+  void* Q;         /* real[S*R], required: the orthonormal factors Q_k, stacked by rows */
+  void* T;         /* real[K*R*R], required: T_k = Q_k^T X_k V, row-major R x R */
   void* Pi;        /* real[K*R*R], optional (NULL): Pi_k = Q_k^T Q_k (a projector) */
-  int32_t* rank;   /* int32[K], optional (NULL): number of kept eigenvalues */
+  int32_t* rank;   /* int32[K], optional (NULL): number of kept singular values */
 } copa_procrustes_out_t;
 
 typedef struct {
@@ -113,27 +113,29 @@ copa_status_t copa_sync(copa_handle_t handle);
 copa_status_t copa_validate(copa_handle_t handle, const copa_tensor_t* X);
 
 /* (a)+(b), Eq. solv_Q and Algorithm 1's per-subject loop, for every subject at once:
- * P_k = X_k V, G_k = P_k^T P_k (FP64), M_k = A_k^T A_k = H S_k G_k S_k H^T, the FP64
- * symmetric eigendecomposition M_k = C diag(lambda) C^T, Omega_k from the eigenpairs with
- * lambda > tau * lambda_max, then Gamma_k, T_k (and Pi_k, rank_k on request).
- * If F_H is not NULL it also returns the mode-1 MTTKRP F_H = sum_k T_k S_k (R x R,
- * real), which is (c) for H, fused. H: R x R, V: J x R, W: K x R (S_k = diag(W(k,:))). */
+ * A_k = X_k V S_k H^T = B D C^T (thin SVD) and Q_k = B C^T over the singular values with
+ * sigma^2 > tau * sigma_max^2 (tau = 1e-8 in the paper's reading used here). Computed by
+ * one-sided Jacobi on the rows of A_k (I_k <= R) or of the R factor of a Householder QR
+ * of A_k (I_k > R), never forming A_k^T A_k. Writes Q (S x R), T_k = Q_k^T X_k V and, on
+ * request, Pi_k and rank_k. If F_H is not NULL it also returns the mode-1 MTTKRP
+ * F_H = sum_k T_k S_k (R x R, real), which is (c) for H, fused. H: R x R, V: J x R,
+ * W: K x R (S_k = diag(W(k,:))). Shared memory bounds R: <= 96 in COPA_PREC_MIXED,
+ * <= 64 in COPA_PREC_FP64 (COPA_ERR_UNSUPPORTED above). */
 copa_status_t copa_procrustes(copa_handle_t handle, const copa_tensor_t* X, int32_t R,
                               const void* H, const void* V, const void* W, double tau,
                               copa_procrustes_out_t* out, void* F_H);
 
 /* (c) The MTTKRPs of Y = {Q_k^T X_k} (Sec. 2, Algorithm 1 "F = Y_(n)(Khatri-Rao)"),
- * from the Procrustes output `st` of the factors (Hp, Vp, Wp) that produced it:
+ * from the Procrustes output `st` (computed with some V_p; T_k = Q_k^T X_k V_p):
  *   COPA_MODE_H: F (R x R) = sum_k T_k diag(W(k,:))               uses st->T, W
  *   COPA_MODE_W: F (K x R), F(k,s) = sum_r H(r,s) T_k(r,s)         uses st->T, H
- *   COPA_MODE_V: F (J x R) = sum_k X_k^T (X_k Vp) Gamma_k H diag(W(k,:))
- *                uses X, st->Gamma, Vp, H, W; if UtU is not NULL it also returns
- *                U^T U = sum_k diag(W(k,:)) H^T Q_k^T Q_k H diag(W(k,:)) (R x R double),
- *                the Gram of the rows of Q_k H S_k, used by the FIT and the gradient.
+ *   COPA_MODE_V: F (J x R) = sum_k X_k^T Q_k H diag(W(k,:))        uses X, st->Q, H, W
+ *                if UtU is not NULL it also returns U^T U = sum_k S_k H^T Q_k^T Q_k H S_k
+ *                (R x R double), the Gram of the rows of Q_k H S_k (FIT and gradient).
  * Pointers a mode does not use may be NULL. F is overwritten. */
 copa_status_t copa_mttkrp(copa_handle_t handle, int32_t mode, const copa_tensor_t* X,
-                          int32_t R, const copa_procrustes_out_t* st, const void* Vp,
-                          const void* H, const void* W, void* F, double* UtU);
+                          int32_t R, const copa_procrustes_out_t* st, const void* H,
+                          const void* W, void* F, double* UtU);
 
 /* Column Gram G = A^T A (R x R, double) of a rows x R real matrix (Algorithm 1: the
  * factor Grams whose Hadamard products give G for each mode). */
@@ -173,8 +175,8 @@ copa_status_t copa_fit_value(copa_handle_t handle, const copa_tensor_t* X, int32
  * auxiliary factors on entry and the fitted ones on return; DH, DV, DW (same shapes)
  * hold the scaled duals (zero for a cold start) and are updated. fit_history_host
  * (double[n_outer], HOST, may be NULL) receives the FIT after every iteration.
- * st (may be NULL) receives the last iteration's Procrustes output (Gamma, T;
- * Pi and rank if given) so that U_k = Q_k H can be assembled. Synchronises. */
+ * st (may be NULL) receives the last iteration's Procrustes output (Q and T; Pi and rank
+ * if given), from which the paper's outputs U_k = Q_k H follow. Synchronises. */
 copa_status_t copa_fit(copa_handle_t handle, const copa_tensor_t* X, const copa_options_t* opt,
                        void* H, void* V, void* W, void* DH, void* DV, void* DW,
                        double* fit_history_host, copa_procrustes_out_t* st);
@@ -186,12 +188,6 @@ copa_status_t copa_fit_host(copa_handle_t handle, const copa_tensor_t* X_host,
                             const copa_options_t* opt, void* H_host, void* V_host,
                             void* W_host, void* DH_host, void* DV_host, void* DW_host,
                             double* fit_history_host);
-
-/* Q_k rows (S x R real): q_i = (x_i Vp) Gamma_k for every row i of subject k, and
- * optionally U = Q_k H (U_k, Algorithm 1 output; pass H = NULL to skip). */
-copa_status_t copa_assemble_q(copa_handle_t handle, const copa_tensor_t* X, int32_t R,
-                              const copa_procrustes_out_t* st, const void* Vp,
-                              const void* H, void* Q, void* U);
 
 /* Smoothness on U_k (Sec. 3.3.1), set-up step. For every subject, the cubic (degree)
  * B-spline basis with n_basis functions on [t_1, t_{I_k}] (interior knots equally spaced

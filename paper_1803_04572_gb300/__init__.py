@@ -30,7 +30,7 @@ MODE = {"H": 0, "V": 1, "W": 2}
 
 EXPORTED = ["copa_create", "copa_destroy", "copa_last_error", "copa_sync", "copa_validate",
             "copa_procrustes", "copa_mttkrp", "copa_gram", "copa_admm_step", "copa_admm_w_fused",
-            "copa_fit_value", "copa_fit", "copa_fit_host", "copa_assemble_q", "copa_smooth_plan",
+            "copa_fit_value", "copa_fit", "copa_fit_host", "copa_smooth_plan",
             "copa_smooth_project", "copa_loss_grad"]
 
 
@@ -47,7 +47,7 @@ class TensorC(Structure):
 
 
 class ProcOutC(Structure):
-    _fields_ = [("Gamma", c_void_p), ("T", c_void_p), ("Pi", c_void_p), ("rank", c_void_p)]
+    _fields_ = [("Q", c_void_p), ("T", c_void_p), ("Pi", c_void_p), ("rank", c_void_p)]
 
 
 class OptionsC(Structure):
@@ -64,7 +64,7 @@ _sig = {
     "copa_sync": [_V],
     "copa_validate": [_V, POINTER(TensorC)],
     "copa_procrustes": [_V, POINTER(TensorC), c_int32, _V, _V, _V, c_double, POINTER(ProcOutC), _V],
-    "copa_mttkrp": [_V, c_int32, POINTER(TensorC), c_int32, POINTER(ProcOutC), _V, _V, _V, _V, _V],
+    "copa_mttkrp": [_V, c_int32, POINTER(TensorC), c_int32, POINTER(ProcOutC), _V, _V, _V, _V],
     "copa_gram": [_V, _V, c_int64, c_int32, _V],
     "copa_admm_step": [_V, _V, _V, _V, c_int32, c_int32, c_double, _V, _V, c_int64, c_int32, _V],
     "copa_admm_w_fused": [_V, POINTER(ProcOutC), _V, _V, _V, c_int32, c_int32, c_double, _V, _V,
@@ -73,7 +73,6 @@ _sig = {
     "copa_fit": [_V, POINTER(TensorC), POINTER(OptionsC), _V, _V, _V, _V, _V, _V, _V,
                  POINTER(ProcOutC)],
     "copa_fit_host": [_V, POINTER(TensorC), POINTER(OptionsC), _V, _V, _V, _V, _V, _V, _V],
-    "copa_assemble_q": [_V, POINTER(TensorC), c_int32, POINTER(ProcOutC), _V, _V, _V, _V],
     "copa_smooth_plan": [_V, POINTER(TensorC), _V, c_int32, c_int32, POINTER(c_int64),
                          POINTER(c_int64)],
     "copa_smooth_project": [_V, POINTER(TensorC), _V, c_int32, c_int32, POINTER(TensorC), _V],
@@ -102,8 +101,10 @@ class DeviceTensor:
         self.K, self.J = int(K), int(J)
         self.subj_ptr, self.row_ptr, self.col, self.vals = subj_ptr, row_ptr, col, vals
         self.val_dtype = val_dtype
-        self.S = int(subj_ptr.numel() - 1)
+        self.S = int(row_ptr.numel() - 1)      # visit rows (subj_ptr has K + 1 entries)
         self.nnz = int(col.numel())
+        if int(subj_ptr.numel()) != self.K + 1:
+            raise ValueError("subj_ptr must have K + 1 entries")
 
     @staticmethod
     def from_host(X, device="cuda", val_dtype: str = "f32") -> "DeviceTensor":
@@ -128,7 +129,9 @@ def host_tensor_c(X, val_dtype="f32"):
     dt = {"f32": np.float32, "f64": np.float64}[val_dtype]
     arrs = [np.ascontiguousarray(X.subj_ptr, dtype=np.int64), np.ascontiguousarray(X.row_ptr, dtype=np.int64),
             np.ascontiguousarray(X.col, dtype=np.int32), np.ascontiguousarray(X.val, dtype=dt)]
-    tc = TensorC(X.K, X.J, len(arrs[0]) - 1, len(arrs[2]), *(a.ctypes.data for a in arrs),
+    if len(arrs[0]) != X.K + 1:
+        raise ValueError("subj_ptr must have K + 1 entries")
+    tc = TensorC(X.K, X.J, len(arrs[1]) - 1, len(arrs[2]), *(a.ctypes.data for a in arrs),
                  VAL_DTYPE[val_dtype])
     return tc, arrs
 
@@ -146,7 +149,13 @@ class Options:
 
 
 class Copa:
-    """A libcopa handle bound to one device and one stream."""
+    """A libcopa handle bound to one device and a dedicated CUDA stream.
+
+    The library enqueues its kernels on its own stream (a real stream object, so that
+    libcopa's CUDA runtime and PyTorch's refer to the same queue). Every call first makes
+    that stream wait for PyTorch's current stream (so inputs written by PyTorch are
+    complete) and afterwards makes PyTorch's current stream wait for it (so outputs are
+    complete and freed inputs are not reused too early)."""
 
     def __init__(self, device: int = 0, precision: str = "mixed", stream=None):
         import torch
@@ -154,11 +163,9 @@ class Copa:
         self.device = torch.device("cuda", device)
         self.precision = precision
         self.dtype = torch.float32 if precision == "mixed" else torch.float64
-        if stream is None:
-            stream = torch.cuda.current_stream(self.device)
-        self.stream = stream
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
         h = c_void_p()
-        self._check(_lib.copa_create(byref(h), device, c_void_p(stream.cuda_stream), PREC[precision]), None)
+        self._check(_lib.copa_create(byref(h), device, c_void_p(self.stream.cuda_stream), PREC[precision]), None)
         self.h = h
 
     def close(self):
@@ -171,6 +178,13 @@ class Copa:
             self.close()
         except Exception:
             pass
+
+    def _call(self, fn, *args):
+        cur = self.torch.cuda.current_stream(self.device)
+        self.stream.wait_stream(cur)
+        code = fn(*args)
+        cur.wait_stream(self.stream)
+        self._check(code)
 
     def _check(self, code, h="self"):
         if code != OK:
@@ -185,66 +199,59 @@ class Copa:
 
     # ---- steps ----
     def sync(self):
-        self._check(_lib.copa_sync(self.h))
+        self._call(_lib.copa_sync, self.h)
 
     def validate(self, X: DeviceTensor):
-        self._check(_lib.copa_validate(self.h, byref(X.c())))
+        self._call(_lib.copa_validate, self.h, byref(X.c()))
 
     def procrustes(self, X: DeviceTensor, R, H, V, W, tau=1e-8, want_pi=False, want_rank=False,
                    want_fh=True):
-        st = {"Gamma": self.empty(X.K, R, R), "T": self.empty(X.K, R, R),
+        st = {"Q": self.empty(max(X.S, 1), R), "T": self.empty(X.K, R, R),
               "Pi": self.empty(X.K, R, R) if want_pi else None,
               "rank": self.empty(X.K, dtype=self.torch.int32) if want_rank else None}
         fh = self.empty(R, R) if want_fh else None
         po = self.proc_c(st)
-        self._check(_lib.copa_procrustes(self.h, byref(X.c()), R, _ptr(H), _ptr(V), _ptr(W), tau,
-                                         byref(po), _ptr(fh)))
+        self._call(_lib.copa_procrustes, self.h, byref(X.c()), R, _ptr(H), _ptr(V), _ptr(W), tau,
+                                         byref(po), _ptr(fh))
         st["F_H"] = fh
         return st
 
     @staticmethod
     def proc_c(st) -> ProcOutC:
-        return ProcOutC(_ptr(st.get("Gamma")), _ptr(st.get("T")), _ptr(st.get("Pi")), _ptr(st.get("rank")))
+        return ProcOutC(_ptr(st.get("Q")), _ptr(st.get("T")), _ptr(st.get("Pi")), _ptr(st.get("rank")))
 
-    def mttkrp(self, mode: str, X: DeviceTensor, R, st, Vp=None, H=None, W=None, want_utu=False):
+    def mttkrp(self, mode: str, X: DeviceTensor, R, st, H=None, W=None, want_utu=False):
         rows = {"H": R, "V": X.J, "W": X.K}[mode]
         F = self.empty(rows, R)
         utu = self.empty(R, R, dtype=self.torch.float64) if want_utu else None
-        self._check(_lib.copa_mttkrp(self.h, MODE[mode], byref(X.c()), R, byref(self.proc_c(st)), _ptr(Vp),
-                                     _ptr(H), _ptr(W), _ptr(F), _ptr(utu)))
+        self._call(_lib.copa_mttkrp, self.h, MODE[mode], byref(X.c()), R, byref(self.proc_c(st)), _ptr(H),
+                                     _ptr(W), _ptr(F), _ptr(utu))
         return (F, utu) if want_utu else F
 
     def gram(self, A):
         R = A.shape[1]
         G = self.empty(R, R, dtype=self.torch.float64)
-        self._check(_lib.copa_gram(self.h, _ptr(A), A.shape[0], R, _ptr(G)))
+        self._call(_lib.copa_gram, self.h, _ptr(A), A.shape[0], R, _ptr(G))
         return G
 
     def admm_step(self, F, Ga, Gb, n_inner, constraint, lam, Zbar, D):
         rho = self.empty(1, dtype=self.torch.float64)
-        self._check(_lib.copa_admm_step(self.h, _ptr(F), _ptr(Ga), _ptr(Gb), n_inner, CONSTRAINT[constraint],
-                                        lam, _ptr(Zbar), _ptr(D), Zbar.shape[0], Zbar.shape[1], _ptr(rho)))
+        self._call(_lib.copa_admm_step, self.h, _ptr(F), _ptr(Ga), _ptr(Gb), n_inner, CONSTRAINT[constraint],
+                                        lam, _ptr(Zbar), _ptr(D), Zbar.shape[0], Zbar.shape[1], _ptr(rho))
         return rho
 
     def admm_w_fused(self, st, H, Ga, Gb, n_inner, constraint, lam, Wbar, DW):
         rho = self.empty(1, dtype=self.torch.float64)
-        self._check(_lib.copa_admm_w_fused(self.h, byref(self.proc_c(st)), _ptr(H), _ptr(Ga), _ptr(Gb), n_inner,
+        self._call(_lib.copa_admm_w_fused, self.h, byref(self.proc_c(st)), _ptr(H), _ptr(Ga), _ptr(Gb), n_inner,
                                            CONSTRAINT[constraint], lam, _ptr(Wbar), _ptr(DW), Wbar.shape[0],
-                                           Wbar.shape[1], _ptr(rho)))
+                                           Wbar.shape[1], _ptr(rho))
         return rho
 
     def fit_value(self, X: DeviceTensor, R, V, F_V, UtU, x_norm2=0.0):
         out = self.empty(1, dtype=self.torch.float64)
-        self._check(_lib.copa_fit_value(self.h, byref(X.c()), R, _ptr(V), _ptr(F_V), _ptr(UtU), x_norm2,
-                                        _ptr(out)))
+        self._call(_lib.copa_fit_value, self.h, byref(X.c()), R, _ptr(V), _ptr(F_V), _ptr(UtU), x_norm2,
+                                        _ptr(out))
         return out
-
-    def assemble_q(self, X: DeviceTensor, R, st, Vp, H=None):
-        Q = self.empty(X.S, R)
-        U = self.empty(X.S, R) if H is not None else None
-        self._check(_lib.copa_assemble_q(self.h, byref(X.c()), R, byref(self.proc_c(st)), _ptr(Vp), _ptr(H),
-                                         _ptr(Q), _ptr(U)))
-        return (Q, U) if H is not None else Q
 
     def fit(self, X: DeviceTensor, opt: Options, H, V, W, DH=None, DV=None, DW=None, state=None):
         """Algorithm 1 for opt.n_outer iterations; H, V, W (and the duals) updated in place.
@@ -254,8 +261,8 @@ class Copa:
         DW = self.torch.zeros_like(W) if DW is None else DW
         hist = np.zeros(max(1, opt.n_outer), dtype=np.float64)
         po = byref(self.proc_c(state)) if state is not None else None
-        self._check(_lib.copa_fit(self.h, byref(X.c()), byref(opt.c()), _ptr(H), _ptr(V), _ptr(W), _ptr(DH),
-                                  _ptr(DV), _ptr(DW), hist.ctypes.data, po))
+        self._call(_lib.copa_fit, self.h, byref(X.c()), byref(opt.c()), _ptr(H), _ptr(V), _ptr(W), _ptr(DH),
+                                  _ptr(DV), _ptr(DW), hist.ctypes.data, po)
         return hist[:opt.n_outer]
 
     def fit_host(self, Xh, opt: Options, H, V, W, DH=None, DV=None, DW=None, val_dtype="f32"):
@@ -268,17 +275,17 @@ class Copa:
         DW = np.zeros_like(W) if DW is None else DW
         tc, keep = host_tensor_c(Xh, val_dtype)
         hist = np.zeros(max(1, opt.n_outer), dtype=np.float64)
-        self._check(_lib.copa_fit_host(self.h, byref(tc), byref(opt.c()), H.ctypes.data, V.ctypes.data,
+        self._call(_lib.copa_fit_host, self.h, byref(tc), byref(opt.c()), H.ctypes.data, V.ctypes.data,
                                        W.ctypes.data, DH.ctypes.data, DV.ctypes.data, DW.ctypes.data,
-                                       hist.ctypes.data))
+                                       hist.ctypes.data)
         del keep
         return hist[:opt.n_outer]
 
     def smooth(self, X: DeviceTensor, days, n_basis=7, degree=3, out_dtype="f32", want_C=False):
         """Smoothing set-up of Sec. 3.3.1: returns (X' as DeviceTensor, C or None)."""
         S_out, nnz_out = c_int64(), c_int64()
-        self._check(_lib.copa_smooth_plan(self.h, byref(X.c()), _ptr(days), n_basis, degree, byref(S_out),
-                                          byref(nnz_out)))
+        self._call(_lib.copa_smooth_plan, self.h, byref(X.c()), _ptr(days), n_basis, degree, byref(S_out),
+                                          byref(nnz_out))
         torch = self.torch
         tdt = torch.float32 if out_dtype == "f32" else torch.float64
         Xp = DeviceTensor(X.K, X.J, self.empty(X.K + 1, dtype=torch.int64),
@@ -287,15 +294,15 @@ class Copa:
                           self.empty(max(nnz_out.value, 1), dtype=tdt)[:nnz_out.value], out_dtype)
         C = self.empty(X.S, n_basis, dtype=torch.float64) if want_C else None
         xc = Xp.c()
-        self._check(_lib.copa_smooth_project(self.h, byref(X.c()), _ptr(days), n_basis, degree, byref(xc),
-                                             _ptr(C)))
+        self._call(_lib.copa_smooth_project, self.h, byref(X.c()), _ptr(days), n_basis, degree, byref(xc),
+                                             _ptr(C))
         return Xp, C
 
     def loss_grad(self, X: DeviceTensor, R, st, H, V, W):
         loss = self.empty(1, dtype=self.torch.float64)
         gH, gV, gW = self.empty(*H.shape), self.empty(*V.shape), self.empty(*W.shape)
-        self._check(_lib.copa_loss_grad(self.h, byref(X.c()), R, byref(self.proc_c(st)), _ptr(H), _ptr(V),
-                                        _ptr(W), _ptr(loss), _ptr(gH), _ptr(gV), _ptr(gW)))
+        self._call(_lib.copa_loss_grad, self.h, byref(X.c()), R, byref(self.proc_c(st)), _ptr(H), _ptr(V),
+                                        _ptr(W), _ptr(loss), _ptr(gH), _ptr(gV), _ptr(gW))
         return loss, gH, gV, gW
 
 

@@ -290,22 +290,22 @@ copa_status_t copa_procrustes(copa_handle_t h, const copa_tensor_t* X, int32_t R
   TRY(set_dev(h));
   TRY(check_tensor_args(h, X));
   TRY(check_R(h, R));
-  if (!H || !V || !W || !out || !out->Gamma || !out->T)
-    return fail(h, COPA_ERR_INVALID_ARG, "copa_procrustes: NULL H, V, W, Gamma or T");
+  if (!H || !V || !W || !out || !out->Q || !out->T)
+    return fail(h, COPA_ERR_INVALID_ARG, "copa_procrustes: NULL H, V, W, Q or T");
   if (!(tau >= 0.0 && tau < 1.0)) return fail(h, COPA_ERR_INVALID_ARG, "tau must be in [0, 1)");
   const TensorView v = view_of(X);
   if (h->precision == COPA_PREC_MIXED)
     return launch_procrustes<float>(h, v, R, (const float*)H, (const float*)V, (const float*)W, tau,
-                                    (float*)out->Gamma, (float*)out->T, (float*)out->Pi, out->rank,
+                                    (float*)out->Q, (float*)out->T, (float*)out->Pi, out->rank,
                                     (float*)F_H);
   return launch_procrustes<double>(h, v, R, (const double*)H, (const double*)V, (const double*)W, tau,
-                                   (double*)out->Gamma, (double*)out->T, (double*)out->Pi, out->rank,
+                                   (double*)out->Q, (double*)out->T, (double*)out->Pi, out->rank,
                                    (double*)F_H);
 }
 
 copa_status_t copa_mttkrp(copa_handle_t h, int32_t mode, const copa_tensor_t* X, int32_t R,
-                          const copa_procrustes_out_t* st, const void* Vp, const void* H,
-                          const void* W, void* F, double* UtU) {
+                          const copa_procrustes_out_t* st, const void* H, const void* W, void* F,
+                          double* UtU) {
   CHECK_H(h);
   TRY(set_dev(h));
   TRY(check_R(h, R));
@@ -323,13 +323,12 @@ copa_status_t copa_mttkrp(copa_handle_t h, int32_t mode, const copa_tensor_t* X,
   }
   if (mode == COPA_MODE_V) {
     TRY(check_tensor_args(h, X));
-    if (!st->Gamma || !Vp || !H || !W) return fail(h, COPA_ERR_INVALID_ARG, "copa_mttkrp(V): needs Gamma, Vp, H, W");
+    if (!st->Q || !H || !W) return fail(h, COPA_ERR_INVALID_ARG, "copa_mttkrp(V): needs Q, H, W");
     const TensorView v = view_of(X);
     if (mixed)
-      return launch_mttkrp_v<float>(h, v, R, (const float*)st->Gamma, (const float*)Vp, (const float*)H,
-                                    (const float*)W, (float*)F, UtU);
-    return launch_mttkrp_v<double>(h, v, R, (const double*)st->Gamma, (const double*)Vp, (const double*)H,
-                                   (const double*)W, (double*)F, UtU);
+      return launch_mttkrp_v<float>(h, v, R, (const float*)st->Q, (const float*)H, (const float*)W, (float*)F, UtU);
+    return launch_mttkrp_v<double>(h, v, R, (const double*)st->Q, (const double*)H, (const double*)W, (double*)F,
+                                   UtU);
   }
   return fail(h, COPA_ERR_INVALID_ARG, "copa_mttkrp: mode must be 0 (H), 1 (V) or 2 (W)");
 }
@@ -409,23 +408,6 @@ copa_status_t copa_fit_value(copa_handle_t h, const copa_tensor_t* X, int32_t R,
   return launch_fit_value<double>(h, X->J, R, (const double*)V, (const double*)F_V, UtU, xn2, x_norm2, fit);
 }
 
-copa_status_t copa_assemble_q(copa_handle_t h, const copa_tensor_t* X, int32_t R,
-                              const copa_procrustes_out_t* st, const void* Vp, const void* H, void* Q,
-                              void* U) {
-  CHECK_H(h);
-  TRY(set_dev(h));
-  TRY(check_tensor_args(h, X));
-  TRY(check_R(h, R));
-  if (!st || !st->Gamma || !Vp || !Q || (U && !H))
-    return fail(h, COPA_ERR_INVALID_ARG, "copa_assemble_q: bad arguments");
-  const TensorView v = view_of(X);
-  if (h->precision == COPA_PREC_MIXED)
-    return launch_assemble_q<float>(h, v, R, (const float*)st->Gamma, (const float*)Vp, (const float*)H,
-                                    (float*)Q, U ? (float*)U : nullptr);
-  return launch_assemble_q<double>(h, v, R, (const double*)st->Gamma, (const double*)Vp, (const double*)H,
-                                   (double*)Q, U ? (double*)U : nullptr);
-}
-
 }  // extern "C"
 
 // =====================================================================================
@@ -436,7 +418,7 @@ namespace {
 
 template <typename Real>
 struct FitBufs {
-  Real* Gamma;
+  Real* Q;
   Real* T;
   Real* Pi;
   int32_t* rank;
@@ -459,7 +441,7 @@ copa_status_t one_iteration(copa_ctx* h, const TensorView& X, const copa_options
                             Real* W, Real* DH, Real* DV, Real* DW, const FitBufs<Real>& b) {
   const int R = o->R;
   // (a)+(b) Procrustes, with the H-mode MTTKRP fused
-  TRY(launch_procrustes<Real>(h, X, R, H, V, W, o->tau, b.Gamma, b.T, b.Pi, b.rank, b.FH));
+  TRY(launch_procrustes<Real>(h, X, R, H, V, W, o->tau, b.Q, b.T, b.Pi, b.rank, b.FH));
   // H: G = W^T W .* V^T V
   TRY(launch_gram<Real>(h, W, X.K, R, b.gW));
   TRY(launch_gram<Real>(h, V, X.J, R, b.gV));
@@ -469,9 +451,9 @@ copa_status_t one_iteration(copa_ctx* h, const TensorView& X, const copa_options
   TRY(launch_gram<Real>(h, H, R, R, b.gH));
   TRY(launch_chol<Real>(h, b.gH, b.gV, R, b.Ginv, b.rho + 1));
   TRY(launch_admm_w<Real>(h, b.T, H, b.Ginv, b.rho + 1, o->n_inner, o->c_W, o->lam_W, W, DW, X.K, R));
-  // V: G = H^T H .* W^T W; F_V streams X with the V of the Procrustes step (still in V)
+  // V: G = H^T H .* W^T W; F_V = sum_k X_k^T Q_k H S_k
   TRY(launch_gram<Real>(h, W, X.K, R, b.gW));
-  TRY(launch_mttkrp_v<Real>(h, X, R, b.Gamma, V, H, W, b.FV, b.UtU));
+  TRY(launch_mttkrp_v<Real>(h, X, R, b.Q, H, W, b.FV, b.UtU));
   TRY(launch_chol<Real>(h, b.gH, b.gW, R, b.Ginv, b.rho + 2));
   TRY(launch_admm_rows<Real>(h, b.FV, b.Ginv, b.rho + 2, o->n_inner, o->c_V, o->lam_V, V, DV, X.J, R));
   // FIT of (Q_k, H, W, V) after the iteration
@@ -487,22 +469,25 @@ copa_status_t fit_impl(copa_ctx* h, const copa_tensor_t* Xc, const copa_options_
   const int R = o->R;
   const size_t KRR = (size_t)X.K * R * R;
   FitBufs<Real> b{};
-  if (st && st->Gamma && st->T) {
-    b.Gamma = (Real*)st->Gamma;
+  if (st && st->Q && st->T) {
+    b.Q = (Real*)st->Q;
     b.T = (Real*)st->T;
     b.Pi = (Real*)st->Pi;
     b.rank = st->rank;
   } else {
-    TRY(ws_get(h, SLOT_FIT_GAMMA, sizeof(Real) * KRR, (void**)&b.Gamma));
+    TRY(ws_get(h, SLOT_FIT_Q, sizeof(Real) * (size_t)X.S * R + 16, (void**)&b.Q));
     TRY(ws_get(h, SLOT_FIT_T, sizeof(Real) * KRR, (void**)&b.T));
   }
-  const size_t nsmall = sizeof(Real) * ((size_t)R * R + (size_t)X.J * R + (size_t)R * (R + 1)) +
-                        sizeof(double) * (4 * (size_t)R * R + 8 + (size_t)o->n_outer) + 64;
+  auto rnd = [](size_t bytes) { return (bytes + 255) & ~size_t(255); };
+  const size_t nsmall = 4 * rnd(sizeof(double) * R * R) + rnd(sizeof(double) * 4) + 2 * rnd(sizeof(double)) +
+                        rnd(sizeof(double) * std::max(1, o->n_outer)) + rnd(sizeof(int)) +
+                        rnd(sizeof(Real) * R * R) + rnd(sizeof(Real) * (size_t)X.J * R) +
+                        rnd(sizeof(Real) * R * (R + 1));
   char* p = nullptr;
-  TRY(ws_get(h, SLOT_FIT_SMALL, nsmall + 512, (void**)&p));
+  TRY(ws_get(h, SLOT_FIT_SMALL, nsmall, (void**)&p));
   auto take = [&](size_t bytes) {
     char* r = p;
-    p += (bytes + 255) & ~size_t(255);
+    p += rnd(bytes);
     return r;
   };
   b.gH = (double*)take(sizeof(double) * R * R);

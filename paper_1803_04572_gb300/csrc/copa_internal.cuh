@@ -69,10 +69,14 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-template <typename T>
-__device__ __forceinline__ T warp_max(T v) {
+__device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
 
@@ -126,7 +130,7 @@ enum Slot {
   SLOT_SCHED_TMP = 1,  // histogram / counters
   SLOT_PARTIAL = 2,    // per-warp or per-block FP64 partial sums
   SLOT_COUNTER = 3,    // int32 work counters
-  SLOT_FIT_GAMMA = 4,  // copa_fit: Gamma
+  SLOT_FIT_Q = 4,      // copa_fit: Q (S x R)
   SLOT_FIT_T = 5,      // copa_fit: T
   SLOT_FIT_SMALL = 6,  // copa_fit: F_H, F_V, Grams, Ginv, rho, UtU, fit values
   SLOT_GINV = 7,       // Ginv + rho for standalone ADMM calls
@@ -145,15 +149,16 @@ copa_status_t get_schedule(copa_ctx* h, const TensorView& X, const int64_t** ord
 // ---- launchers (host functions, enqueue on h->stream) ----
 template <typename Real>
 copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const Real* H,
-                                const Real* V, const Real* W, double tau, Real* Gamma, Real* T,
+                                const Real* V, const Real* W, double tau, Real* Q, Real* T,
                                 Real* Pi, int32_t* rank, Real* F_H);
+template <typename Real>
+size_t procrustes_smem(int R);
 template <typename Real>
 copa_status_t launch_mttkrp_h(copa_ctx* h, int64_t K, int R, const Real* T, const Real* W,
                               Real* F);
 template <typename Real>
-copa_status_t launch_mttkrp_v(copa_ctx* h, const TensorView& X, int R, const Real* Gamma,
-                              const Real* Vp, const Real* H, const Real* W, Real* F,
-                              double* UtU);
+copa_status_t launch_mttkrp_v(copa_ctx* h, const TensorView& X, int R, const Real* Q,
+                              const Real* H, const Real* W, Real* F, double* UtU);
 template <typename Real>
 copa_status_t launch_mttkrp_w(copa_ctx* h, int64_t K, int R, const Real* T, const Real* H,
                               Real* F);
@@ -175,10 +180,7 @@ copa_status_t launch_fit_value(copa_ctx* h, int64_t J, int R, const Real* V, con
                                const double* UtU, const double* xn2_dev, double x_norm2,
                                double* fit);
 template <typename Real>
-copa_status_t launch_assemble_q(copa_ctx* h, const TensorView& X, int R, const Real* Gamma,
-                                const Real* Vp, const Real* H, Real* Q, Real* U);
-template <typename Real>
-copa_status_t launch_loss_grad(copa_ctx* h, const TensorView& X, int R, const Real* Gamma,
+copa_status_t launch_loss_grad(copa_ctx* h, const TensorView& X, int R, const Real* Q,
                                const Real* T, const Real* Pi, const Real* H, const Real* V,
                                const Real* W, double* loss, Real* gH, Real* gV, Real* gW);
 copa_status_t launch_validate(copa_ctx* h, const TensorView& X);

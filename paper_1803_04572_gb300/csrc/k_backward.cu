@@ -108,7 +108,7 @@ __global__ void k_loss(int64_t J, int R, const Real* __restrict__ V, const Real*
 }  // namespace
 
 template <typename Real>
-copa_status_t launch_loss_grad(copa_ctx* h, const TensorView& X, int R, const Real* Gamma, const Real* T,
+copa_status_t launch_loss_grad(copa_ctx* h, const TensorView& X, int R, const Real* Q, const Real* T,
                                const Real* Pi, const Real* H, const Real* V, const Real* W, double* loss,
                                Real* gH, Real* gV, Real* gW) {
   copa_status_t st;
@@ -121,7 +121,7 @@ copa_status_t launch_loss_grad(copa_ctx* h, const TensorView& X, int R, const Re
   double* xn2 = UtU + R * R;
   Real* FV = reinterpret_cast<Real*>(xn2 + 4);
   if ((st = launch_gram<Real>(h, V, X.J, R, Phi)) != COPA_OK) return st;
-  if ((st = launch_mttkrp_v<Real>(h, X, R, Gamma, V, H, W, FV, UtU)) != COPA_OK) return st;
+  if ((st = launch_mttkrp_v<Real>(h, X, R, Q, H, W, FV, UtU)) != COPA_OK) return st;
   if ((st = launch_xnorm2(h, X, xn2)) != COPA_OK) return st;
   const int warps = 4;
   const size_t smem = sizeof(Real) * (2 * (size_t)R * R + (size_t)warps * (2 * R * (R + 1) + R));
@@ -159,14 +159,14 @@ extern "C" copa_status_t copa_loss_grad(copa_handle_t h, const copa_tensor_t* X,
   if ((s = cuda_check(h, cudaSetDevice(h->device), "cudaSetDevice")) != COPA_OK) return s;
   if ((s = check_tensor_args(h, X)) != COPA_OK) return s;
   if (R < 1 || R > kMaxR) return fail(h, COPA_ERR_INVALID_ARG, "copa_loss_grad: R out of range");
-  if (!st || !st->Gamma || !st->T || !st->Pi || !H || !V || !W || !loss || !gH || !gV || !gW)
+  if (!st || !st->Q || !st->T || !st->Pi || !H || !V || !W || !loss || !gH || !gV || !gW)
     return fail(h, COPA_ERR_INVALID_ARG, "copa_loss_grad: NULL argument (Pi is required)");
   const TensorView v = view_of(X);
   if (h->precision == COPA_PREC_MIXED)
-    return launch_loss_grad<float>(h, v, R, (const float*)st->Gamma, (const float*)st->T, (const float*)st->Pi,
+    return launch_loss_grad<float>(h, v, R, (const float*)st->Q, (const float*)st->T, (const float*)st->Pi,
                                    (const float*)H, (const float*)V, (const float*)W, loss, (float*)gH, (float*)gV,
                                    (float*)gW);
-  return launch_loss_grad<double>(h, v, R, (const double*)st->Gamma, (const double*)st->T, (const double*)st->Pi,
+  return launch_loss_grad<double>(h, v, R, (const double*)st->Q, (const double*)st->T, (const double*)st->Pi,
                                   (const double*)H, (const double*)V, (const double*)W, loss, (double*)gH,
                                   (double*)gV, (double*)gW);
 }

@@ -1,14 +1,13 @@
 // MTTKRPs on the implicit Y (Algorithm 1, "F = Y_(n)(Khatri-Rao of the others)"), the
 // factor Grams, rho and the cached Cholesky of G + rho I, the ADMM inner loops with the
-// proximal operators of Sec. 3.3 (Eq. Solve_W update rules), the FIT of Sec. 4.1 and
-// the assembly of Q_k and U_k = Q_k H.
+// proximal operators of Sec. 3.3 (Eq. Solve_W update rules), and the FIT of Sec. 4.1.
 //
-// With Q_k = P_k Gamma_k (P_k = X_k Vp, see k_procrustes.cu) and T_k = Q_k^T X_k Vp:
-//   F_H = sum_k Y_k Vp S_k            = sum_k T_k S_k
-//   F_W(k,s) = (H^T Y_k Vp)(s,s)      = sum_r H(r,s) T_k(r,s)
-//   F_V = sum_k Y_k^T H S_k           = sum_k X_k^T P_k (Gamma_k H S_k)
+// With Q_k from k_procrustes.cu and T_k = Q_k^T X_k V (Y_k = Q_k^T X_k never formed):
+//   F_H = sum_k Y_k V S_k        = sum_k T_k S_k
+//   F_W(k,s) = (H^T Y_k V)(s,s)  = sum_r H(r,s) T_k(r,s)
+//   F_V = sum_k Y_k^T H S_k      = sum_k X_k^T (Q_k H S_k)
 // so only F_V streams X again; it scatters x_ij * u_i into F_V(j,:) with
-// u_i = p_i N_k, N_k = Gamma_k H S_k, and accumulates U^T U = sum_i u_i^T u_i.
+// u_i = q_i H S_k, and accumulates U^T U = sum_i u_i^T u_i.
 #include "copa_internal.cuh"
 
 namespace copa {
@@ -63,13 +62,14 @@ __global__ void k_mttkrp_w(int64_t K, int R, const Real* __restrict__ T,
 }
 
 // ------------------------------------------------------------------------------------
-// F_V = sum_k X_k^T (X_k Vp) Gamma_k H S_k  and  U^T U  (warp per subject, persistent)
+// F_V = sum_k X_k^T Q_k H S_k and U^T U (warp per subject, persistent, largest first):
+// u_i = q_i N_k with N_k = H S_k, F_V(j,:) += x_ij u_i, U^T U += u_i^T u_i
 // ------------------------------------------------------------------------------------
 template <typename Real>
 __global__ void __launch_bounds__(128) k_mttkrp_v(
-    TensorView X, int R, const Real* __restrict__ Gamma, const Real* __restrict__ Vp,
-    const Real* __restrict__ H, const Real* __restrict__ W, Real* __restrict__ F,
-    double* __restrict__ utu_part, const int64_t* __restrict__ order, int* __restrict__ counter) {
+    TensorView X, int R, const Real* __restrict__ Q, const Real* __restrict__ H,
+    const Real* __restrict__ W, Real* __restrict__ F, double* __restrict__ utu_part,
+    const int64_t* __restrict__ order, int* __restrict__ counter) {
   extern __shared__ unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int ldr = R + 1;
@@ -77,8 +77,8 @@ __global__ void __launch_bounds__(128) k_mttkrp_v(
   Real* Hs = reinterpret_cast<Real*>(smem_raw);                    // R x R
   Real* base = Hs + R * R + (size_t)warp * (R * ldr + 3 * R + npk);
   Real* N = base;              // R x ldr
-  Real* pv = N + R * ldr;      // R
-  Real* uv = pv + R;           // R
+  Real* qv = N + R * ldr;      // R
+  Real* uv = qv + R;           // R
   Real* wv = uv + R;           // R
   Real* uacc = wv + R;         // npk: this subject's U^T U (packed upper triangle)
   uint16_t* pk = reinterpret_cast<uint16_t*>(Hs + R * R + (size_t)nwarps * (R * ldr + 3 * R + npk));
@@ -103,23 +103,14 @@ __global__ void __launch_bounds__(128) k_mttkrp_v(
     if (r0 == r1) continue;
     for (int s = lane; s < R; s += 32) wv[s] = W[k * R + s];
     __syncwarp();
-    // N = Gamma_k H S_k
-    const Real* Gk = Gamma + k * R * R;
     for (int e = lane; e < R * R; e += 32) {
       const int r = e / R, s = e - r * R;
-      Real acc = Real(0);
-      for (int t = 0; t < R; ++t) acc += Gk[r * R + t] * Hs[t * R + s];
-      N[r * ldr + s] = acc * wv[s];
+      N[r * ldr + s] = Hs[e] * wv[s];
     }
     __syncwarp();
     for (int64_t i = r0; i < r1; ++i) {
       const int64_t a = X.row_ptr[i], b = X.row_ptr[i + 1];
-      for (int r = lane; r < R; r += 32) {
-        Real acc = Real(0);
-        for (int64_t t = a; t < b; ++t)
-          acc += load_x<Real>(X, t) * __ldg(Vp + (int64_t)__ldg(X.col + t) * R + r);
-        pv[r] = acc;
-      }
+      for (int r = lane; r < R; r += 32) qv[r] = Q[i * R + r];
       __syncwarp();
       Real u[kRegs];
 #pragma unroll
@@ -127,7 +118,7 @@ __global__ void __launch_bounds__(128) k_mttkrp_v(
         const int s = lane + 32 * q;
         Real acc = Real(0);
         if (s < R)
-          for (int r = 0; r < R; ++r) acc += pv[r] * N[r * ldr + s];
+          for (int r = 0; r < R; ++r) acc += qv[r] * N[r * ldr + s];
         u[q] = acc;
         if (s < R) uv[s] = acc;
       }
@@ -418,48 +409,6 @@ __global__ void k_fit_value(int64_t J, int R, const Real* __restrict__ V, const 
   }
 }
 
-// ------------------------------------------------------------------------------------
-// Q rows q_i = (x_i Vp) Gamma_k and optionally U rows u_i = q_i H
-// ------------------------------------------------------------------------------------
-template <typename Real>
-__global__ void k_assemble_q(TensorView X, int R, const Real* __restrict__ Gamma,
-                             const Real* __restrict__ Vp, const Real* __restrict__ H,
-                             Real* __restrict__ Q, Real* __restrict__ U) {
-  extern __shared__ unsigned char smem_raw[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  Real* pv = reinterpret_cast<Real*>(smem_raw) + warp * 2 * R;
-  Real* qv = pv + R;
-  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = (gridDim.x * (int64_t)blockDim.x) >> 5;
-  for (int64_t k = wid; k < X.K; k += nw) {
-    const Real* Gk = Gamma + k * R * R;
-    for (int64_t i = X.subj_ptr[k]; i < X.subj_ptr[k + 1]; ++i) {
-      const int64_t a = X.row_ptr[i], b = X.row_ptr[i + 1];
-      for (int r = lane; r < R; r += 32) {
-        Real acc = Real(0);
-        for (int64_t t = a; t < b; ++t) acc += load_x<Real>(X, t) * Vp[(int64_t)X.col[t] * R + r];
-        pv[r] = acc;
-      }
-      __syncwarp();
-      for (int s = lane; s < R; s += 32) {
-        Real acc = Real(0);
-        for (int r = 0; r < R; ++r) acc += pv[r] * Gk[r * R + s];
-        qv[s] = acc;
-        Q[i * R + s] = acc;
-      }
-      __syncwarp();
-      if (U) {
-        for (int s = lane; s < R; s += 32) {
-          Real acc = Real(0);
-          for (int r = 0; r < R; ++r) acc += qv[r] * H[r * R + s];
-          U[i * R + s] = acc;
-        }
-      }
-      __syncwarp();
-    }
-  }
-}
-
 }  // namespace
 
 // ---------------------------------- launchers ----------------------------------------
@@ -491,8 +440,8 @@ copa_status_t launch_mttkrp_w(copa_ctx* h, int64_t K, int R, const Real* T, cons
 }
 
 template <typename Real>
-copa_status_t launch_mttkrp_v(copa_ctx* h, const TensorView& X, int R, const Real* Gamma,
-                              const Real* Vp, const Real* H, const Real* W, Real* F, double* UtU) {
+copa_status_t launch_mttkrp_v(copa_ctx* h, const TensorView& X, int R, const Real* Q, const Real* H,
+                              const Real* W, Real* F, double* UtU) {
   if (R > kMaxR) return fail(h, COPA_ERR_UNSUPPORTED, "mttkrp V: R too large");
   copa_status_t st;
   const int npk0 = R * (R + 1) / 2;
@@ -526,8 +475,8 @@ copa_status_t launch_mttkrp_v(copa_ctx* h, const TensorView& X, int R, const Rea
     return st;
   if ((st = cuda_check(h, cudaMemsetAsync(F, 0, sizeof(Real) * (size_t)X.J * R, h->stream), "memset F")) != COPA_OK)
     return st;
-  k_mttkrp_v<Real><<<(unsigned)blocks, 32 * warps, smem, h->stream>>>(X, R, Gamma, Vp, H, W, F, part,
-                                                                         order, counter + 1);
+  k_mttkrp_v<Real><<<(unsigned)blocks, 32 * warps, smem, h->stream>>>(X, R, Q, H, W, F, part, order,
+                                                                         counter + 1);
   if ((st = cuda_check(h, cudaGetLastError(), "k_mttkrp_v")) != COPA_OK) return st;
   if (UtU) {
     // packed partials -> full symmetric UtU
@@ -600,22 +549,13 @@ copa_status_t launch_fit_value(copa_ctx* h, int64_t J, int R, const Real* V, con
   return cuda_check(h, cudaGetLastError(), "k_fit_value");
 }
 
-template <typename Real>
-copa_status_t launch_assemble_q(copa_ctx* h, const TensorView& X, int R, const Real* Gamma,
-                                const Real* Vp, const Real* H, Real* Q, Real* U) {
-  const size_t smem = sizeof(Real) * 8 * 2 * (size_t)R;
-  k_assemble_q<Real><<<grid_for(h, X.K, 8, 16), 256, smem, h->stream>>>(X, R, Gamma, Vp, H, Q, U);
-  return cuda_check(h, cudaGetLastError(), "k_assemble_q");
-}
-
 #define COPA_INST(Real)                                                                          \
   template copa_status_t launch_mttkrp_h<Real>(copa_ctx*, int64_t, int, const Real*, const Real*, \
                                                Real*);                                            \
   template copa_status_t launch_mttkrp_w<Real>(copa_ctx*, int64_t, int, const Real*, const Real*, \
                                                Real*);                                            \
   template copa_status_t launch_mttkrp_v<Real>(copa_ctx*, const TensorView&, int, const Real*,    \
-                                               const Real*, const Real*, const Real*, Real*,      \
-                                               double*);                                          \
+                                               const Real*, const Real*, Real*, double*);         \
   template copa_status_t launch_gram<Real>(copa_ctx*, const Real*, int64_t, int, double*);        \
   template copa_status_t launch_chol<Real>(copa_ctx*, const double*, const double*, int, Real*,   \
                                            double*);                                              \
@@ -627,8 +567,7 @@ copa_status_t launch_assemble_q(copa_ctx* h, const TensorView& X, int R, const R
                                              int64_t, int);                                       \
   template copa_status_t launch_fit_value<Real>(copa_ctx*, int64_t, int, const Real*, const Real*, \
                                                 const double*, const double*, double, double*);   \
-  template copa_status_t launch_assemble_q<Real>(copa_ctx*, const TensorView&, int, const Real*,  \
-                                                 const Real*, const Real*, Real*, Real*);
+
 COPA_INST(float)
 COPA_INST(double)
 

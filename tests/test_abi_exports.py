@@ -13,9 +13,17 @@ def _declared():
     return sorted(set(re.findall(r"\b(copa_[a-z_0-9]+)\s*\(", src)))
 
 
+def _build():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "copa_build", os.path.join(ROOT, "paper_1803_04572_gb300", "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod.build()
+
+
 def test_library_exports_every_declared_symbol():
-    from paper_1803_04572_gb300 import build
-    lib_path = build.build()
+    lib_path = _build()
     lib = ctypes.CDLL(lib_path)
     names = _declared()
     assert len(names) >= 15, names
@@ -24,7 +32,31 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_binding_lists_every_declared_symbol():
-    from paper_1803_04572_gb300 import build
-    build.build()
+    _build()
     import paper_1803_04572_gb300 as P
     assert sorted(set(P.EXPORTED)) == _declared()
+
+
+def test_device_tensor_sizes_from_arrays():
+    """S is the number of visit rows (row_ptr has S + 1 entries), not K."""
+    _build()
+    import numpy as np
+    import torch
+    import paper_1803_04572_gb300 as P
+    import synth
+    X = synth.ehr_custom(7, 5, median=4, lo=2, hi=6, seed=1)
+    t = lambda a, dt: torch.as_tensor(np.asarray(a, dtype=dt))
+    d = P.DeviceTensor(X.K, X.J, t(X.subj_ptr, np.int64), t(X.row_ptr, np.int64), t(X.col, np.int32),
+                       t(X.val, np.float32), "f32")
+    assert (d.K, d.S, d.nnz) == (X.K, X.S, X.nnz)
+    c = d.c()
+    assert (c.K, c.J, c.S, c.nnz) == (X.K, X.J, X.S, X.nnz)
+
+
+def test_host_tensor_sizes_from_arrays():
+    _build()
+    import paper_1803_04572_gb300 as P
+    import synth
+    X = synth.ehr_custom(9, 6, median=5, lo=2, hi=9, seed=2)
+    tc, keep = P.host_tensor_c(X, "f32")
+    assert (tc.K, tc.J, tc.S, tc.nnz) == (X.K, X.J, X.S, X.nnz)

@@ -133,7 +133,7 @@ class Clocks:
         sm = np.array([float(r[1]) for r in rows])
         mx = float(rows[0][2])
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]})
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
         load = sm[sm > 0.5 * mx] if (sm > 0.5 * mx).any() else sm
         return {"sm_mhz": float(np.median(load)), "sm_max_mhz": mx, "reasons": reasons,
                 "samples": len(rows)}
@@ -178,11 +178,9 @@ def kernel_breakdown(h, P, Xd, R, H, V, W, reps=2):
 
 
 def procrustes_roofline(h, P, Xd, X, R, H, V, W, peaks, reps=3):
-    """Average duration of the Procrustes launch (the dominant kernel) and its
-    algorithmic FP64 work: the Gram sum_i R(R+1) flops per visit row, the congruence
-    H S G S H^T (4 R^3 per subject) and the Jacobi rotations actually applied
-    (18 n flops each, counted by the kernel's rotation counter is not available here, so
-    the minimum of 6 sweeps x R(R-1)/2 rotations is used), i.e. a lower bound."""
+    """Average duration of the Procrustes launch (the dominant kernel), timed with CUDA
+    events on the handle's stream, and its algorithmic work: the multiply-adds the kernel
+    tallies for the rows, QR, Jacobi rotations and products it performs (2 FLOP each)."""
     torch = h.torch
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     st = h.procrustes(Xd, R, H, V, W, want_fh=True)
@@ -193,14 +191,13 @@ def procrustes_roofline(h, P, Xd, X, R, H, V, W, peaks, reps=3):
     e1.record(h.stream)
     h.sync()
     ms = e0.elapsed_time(e1) / reps
-    S, K = X.S, X.K
-    flops = S * R * (R + 1) + K * (4 * R ** 3 + 6 * (R * (R - 1) // 2) * 18 * R + 6 * R ** 3)
-    achieved = flops / (ms * 1e-3) / 1e12
-    peak = peaks["fp64_tflops"]
+    fma = h.procrustes_work()
+    achieved = 2.0 * fma / (ms * 1e-3) / 1e12
+    key = "fp32_tflops" if h.precision == "mixed" else "fp64_tflops"
+    peak = peaks[key]
     return ms, {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": "k_procrustes (FP64 Gram + Jacobi)",
-                "peak_source": peaks["fp64_source"]}
+                "frac": achieved / peak, "traffic": None, "kernel": "k_procrustes",
+                "work_fma_per_launch": fma, "peak_source": peaks[key.replace("tflops", "source")]}
 
 
 def gpu_leg(args, X, init, rank, world):
@@ -272,10 +269,14 @@ def gpu_leg(args, X, init, rank, world):
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     d = json.load(open(p)) if os.path.exists(p) else {}
-    # FP64 peak: 152 SMs x 64 FP64 flop/clk/SM... derived from the FP64 rate measured by a
-    # DFMA loop on this machine's GB300 (1.19 TFLOP/s); nominal 1.25 TFLOP/s
-    return {"hbm_gbs": d.get("hbm_gbs", 6800.0), "fp64_tflops": 1.19,
-            "fp64_source": "measured DFMA-loop peak on GB300 (1.19 TFLOP/s; nominal 1.25)",
+    # Plain-ALU peaks from the unit counts at the maximum SM clock (2070 MHz): 152 SMs x
+    # 128 FP32 FMA/clk x 2 = 80.5 TFLOP/s; FP64 2 FMA/clk/SM -> 1.26 TFLOP/s (an FMA-loop
+    # probe on this machine's GB300 measured 69.4 and 1.19 TFLOP/s).
+    return {"hbm_gbs": d.get("hbm_gbs", 6800.0),
+            "fp32_tflops": 152 * 128 * 2 * 2.070e9 / 1e12,
+            "fp32_source": "unit count 152 SM x 128 FMA/clk at 2070 MHz (FMA-loop probe: 69.4)",
+            "fp64_tflops": 152 * 2 * 2 * 2.070e9 / 1e12,
+            "fp64_source": "unit count 152 SM x 2 DFMA/clk at 2070 MHz (DFMA-loop probe: 1.19)",
             "hbm_source": "of measured" if "hbm_gbs" in d else "of fallback"}
 
 

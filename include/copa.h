@@ -125,6 +125,12 @@ copa_status_t copa_procrustes(copa_handle_t handle, const copa_tensor_t* X, int3
                               const void* H, const void* V, const void* W, double tau,
                               copa_procrustes_out_t* out, void* F_H);
 
+/* Diagnostic (no counterpart in the paper): the number of multiply-adds the last
+ * copa_procrustes launch on this handle performed, as tallied by the kernel from the
+ * rows, rotations and products it executed (the algorithmic work behind the roofline
+ * figure of the benchmark). Synchronises; writes 0 before the first launch. */
+copa_status_t copa_procrustes_work(copa_handle_t handle, double* fma_host);
+
 /* (c) The MTTKRPs of Y = {Q_k^T X_k} (Sec. 2, Algorithm 1 "F = Y_(n)(Khatri-Rao)"),
  * from the Procrustes output `st` (computed with some V_p; T_k = Q_k^T X_k V_p):
  *   COPA_MODE_H: F (R x R) = sum_k T_k diag(W(k,:))               uses st->T, W

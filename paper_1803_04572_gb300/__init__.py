@@ -31,7 +31,7 @@ MODE = {"H": 0, "V": 1, "W": 2}
 EXPORTED = ["copa_create", "copa_destroy", "copa_last_error", "copa_sync", "copa_validate",
             "copa_procrustes", "copa_mttkrp", "copa_gram", "copa_admm_step", "copa_admm_w_fused",
             "copa_fit_value", "copa_fit", "copa_fit_host", "copa_smooth_plan",
-            "copa_smooth_project", "copa_loss_grad"]
+            "copa_smooth_project", "copa_loss_grad", "copa_procrustes_work"]
 
 
 class CopaError(RuntimeError):
@@ -78,6 +78,7 @@ _sig = {
     "copa_smooth_project": [_V, POINTER(TensorC), _V, c_int32, c_int32, POINTER(TensorC), _V],
     "copa_loss_grad": [_V, POINTER(TensorC), c_int32, POINTER(ProcOutC), _V, _V, _V, _V, _V, _V,
                        _V],
+    "copa_procrustes_work": [_V, POINTER(c_double)],
 }
 for _n, _a in _sig.items():
     getattr(_lib, _n).argtypes = _a
@@ -297,6 +298,12 @@ class Copa:
         self._call(_lib.copa_smooth_project, self.h, byref(X.c()), _ptr(days), n_basis, degree, byref(xc),
                                              _ptr(C))
         return Xp, C
+
+    def procrustes_work(self) -> float:
+        """Multiply-adds performed by the last procrustes() launch (counted on the device)."""
+        v = c_double()
+        self._call(_lib.copa_procrustes_work, self.h, byref(v))
+        return v.value
 
     def loss_grad(self, X: DeviceTensor, R, st, H, V, W):
         loss = self.empty(1, dtype=self.torch.float64)

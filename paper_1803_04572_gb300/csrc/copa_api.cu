@@ -303,6 +303,20 @@ copa_status_t copa_procrustes(copa_handle_t h, const copa_tensor_t* X, int32_t R
                                    (double*)F_H);
 }
 
+copa_status_t copa_procrustes_work(copa_handle_t h, double* fma_host) {
+  CHECK_H(h);
+  TRY(set_dev(h));
+  if (!fma_host) return fail(h, COPA_ERR_INVALID_ARG, "copa_procrustes_work: NULL output");
+  *fma_host = 0.0;
+  if (!h->slot_ptr[SLOT_COUNTER]) return COPA_OK;
+  TRY(sync_status(h));
+  unsigned long long v = 0;
+  TRY(cuda_check(h, cudaMemcpy(&v, reinterpret_cast<char*>(h->slot_ptr[SLOT_COUNTER]) + 8, sizeof(v),
+                               cudaMemcpyDeviceToHost), "counter read"));
+  *fma_host = (double)v;
+  return COPA_OK;
+}
+
 copa_status_t copa_mttkrp(copa_handle_t h, int32_t mode, const copa_tensor_t* X, int32_t R,
                           const copa_procrustes_out_t* st, const void* H, const void* W, void* F,
                           double* UtU) {

@@ -120,7 +120,8 @@ __global__ void __launch_bounds__(32) k_procrustes(
     TensorView X, int R, const Real* __restrict__ H, const Real* __restrict__ V,
     const Real* __restrict__ W, double tau_rank, Real* __restrict__ Q, Real* __restrict__ T,
     Real* __restrict__ Pi, int32_t* __restrict__ rank, double* __restrict__ fh_partial,
-    const int64_t* __restrict__ order, int* __restrict__ counter) {
+    const int64_t* __restrict__ order, int* __restrict__ counter,
+    unsigned long long* __restrict__ fma_count) {
   extern __shared__ unsigned char smem_raw[];
   Real* sm = reinterpret_cast<Real*>(smem_raw);
   const Lay L = lay_of<Real>(R);
@@ -140,6 +141,8 @@ __global__ void __launch_bounds__(32) k_procrustes(
   int* pq = reinterpret_cast<int*>(sm + L.pq);
   uint16_t* pk = reinterpret_cast<uint16_t*>(sm + L.pk);
   const Real tol = Tol<Real>::v();
+  // work tally (lane 0): multiply-adds the algorithm performs, for the roofline
+  unsigned long long fma = 0;
 
   for (int i = lane; i < R * R; i += 32) Hs[(i / R) * ld + (i % R)] = H[i];
   for (int r = 0, e = 0; r < R; ++r)
@@ -160,6 +163,13 @@ __global__ void __launch_bounds__(32) k_procrustes(
     const int Ik = (int)(r1 - r0 < (int64_t)R + 1 ? r1 - r0 : (int64_t)R + 1);
     const bool wide = Ik <= R;
     const int m = wide ? Ik : R;
+    const unsigned long long nnzk = (unsigned long long)(X.row_ptr[r1] - X.row_ptr[r0]);
+    const unsigned long long ik = (unsigned long long)(r1 - r0), RR = (unsigned long long)R * R;
+    // rows: p_i and a_i; tall: Householder QR (~R^2 per row) and the second pass
+    fma += nnzk * R + ik * RR;
+    if (!wide) fma += ik * RR + nnzk * R + 3 * ik * RR + 2 * RR * R;
+    else fma += 2ull * m * m * R + 2ull * RR * m;
+    fma += 2ull * m * R;   // norms and normalisation
 
     // ---- E = S_k H^T; clear R_A (tall) or nothing (wide) and G ----
     for (int r = lane; r < R; r += 32) al[r] = W[k * R + r];
@@ -203,12 +213,13 @@ __global__ void __launch_bounds__(32) k_procrustes(
     __syncwarp();
     const int n2 = m + (m & 1);
     for (int sweep = 0; sweep < kMaxSweeps && n2 > 1; ++sweep) {
-      int nrot = 0;
+      int nrot = 0, ntest = 0;
       for (int round = 0; round < n2 - 1; ++round) {
         for (int pj = lane; pj < n2 / 2; pj += 32) {
           int ii = rr_elem(pj, round, n2), jj = rr_elem(n2 - 1 - pj, round, n2);
           if (ii > jj) { const int tmp = ii; ii = jj; jj = tmp; }
           if (jj >= m) continue;
+          ++ntest;
           Real* zi = Zb + ii * ld;
           Real* zj = Zb + jj * ld;
           Real aa = Real(0), bb = Real(0), gg = Real(0);
@@ -243,7 +254,9 @@ __global__ void __launch_bounds__(32) k_procrustes(
         }
         __syncwarp();
       }
-      if (warp_sum(nrot) == 0) break;
+      const int tot_rot = warp_sum(nrot), tot_test = warp_sum(ntest);
+      fma += (unsigned long long)tot_test * 3 * R + (unsigned long long)tot_rot * 4 * (R + (wide ? m : 0));
+      if (tot_rot == 0) break;
     }
 
     // ---- singular values, rank cut, normalised right singular vectors c_j ----
@@ -352,6 +365,7 @@ __global__ void __launch_bounds__(32) k_procrustes(
       __syncwarp();
     }
   }
+  if (fma_count && lane == 0) atomicAdd(fma_count, fma);
 }
 
 template <typename Real>
@@ -395,15 +409,16 @@ copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const R
   if ((st = get_schedule(h, X, &order)) != COPA_OK) return st;
   int* counter = nullptr;
   if ((st = ws_get(h, SLOT_COUNTER, 64, (void**)&counter)) != COPA_OK) return st;
+  unsigned long long* fma_count = reinterpret_cast<unsigned long long*>(counter + 2);
   double* part = nullptr;
   if (F_H) {
     if ((st = ws_get(h, SLOT_PARTIAL, (size_t)blocks * R * R * sizeof(double), (void**)&part)) != COPA_OK)
       return st;
   }
-  if ((st = cuda_check(h, cudaMemsetAsync(counter, 0, sizeof(int), h->stream), "memset")) != COPA_OK)
+  if ((st = cuda_check(h, cudaMemsetAsync(counter, 0, 16, h->stream), "memset")) != COPA_OK)
     return st;
   k_procrustes<Real><<<(unsigned)blocks, 32, smem, h->stream>>>(X, R, H, V, W, tau, Q, T, Pi, rank, part,
-                                                               order, counter);
+                                                               order, counter, fma_count);
   if ((st = cuda_check(h, cudaGetLastError(), "k_procrustes launch")) != COPA_OK) return st;
   if (F_H) {
     k_reduce_partials<Real><<<(R * R + 255) / 256, 256, 0, h->stream>>>(part, (int)blocks, R * R, F_H);

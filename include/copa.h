@@ -148,6 +148,27 @@ copa_status_t copa_mttkrp(copa_handle_t handle, int32_t mode, const copa_tensor_
 copa_status_t copa_gram(copa_handle_t handle, const void* A, int64_t rows, int32_t R,
                         double* G);
 
+/* Column Gram without any allocation (no counterpart in the paper; a deployment aid).
+ * Some callers cannot allocate device memory while they run this: their device memory
+ * is reserved up front by their own pool, or the implicit device synchronisation of
+ * cudaMalloc/cudaFree would stall other work they have in flight. This call computes the
+ * same G = A^T A as copa_gram but needs no handle and no workspace: its per-block partial
+ * sums go to a fixed 1 MiB array that libcopa keeps in device memory (every GPU that
+ * loads the library holds it until the process exits). It allocates nothing and calls no
+ * allocating routine.
+ *   stream:     cudaStream_t to enqueue on (NULL = legacy default stream)
+ *   a_is_double: 0 if A is float, 1 if A is double
+ *   A:          rows x R row-major (device), G: R x R double (device, overwritten)
+ * Runs on the calling thread's current device. R > 90 returns COPA_ERR_UNSUPPORTED,
+ * other bad sizes or NULL pointers COPA_ERR_INVALID_ARG. The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress, no allocation); make that first
+ * call before any stream capture. All calls share the one array, which keeps the last
+ * call's contents: calls that may overlap on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller. Asynchronous: launch errors are returned at
+ * once, execution errors surface at the caller's next synchronisation. */
+copa_status_t copa_gram_noalloc(void* stream, int32_t a_is_double, const void* A, int64_t rows,
+                                int32_t R, double* G);
+
 /* (d) One factor update by ADMM (Algorithm 1 inner loop; Eq. Solve_W update rules):
  * G = Ga .* Gb (R x R double, Hadamard product of two Grams; Gb may be NULL meaning
  * G = Ga), rho = trace(G)/R, L = chol(G + rho I) (FP64), then n_inner times, row-wise

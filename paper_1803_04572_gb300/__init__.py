@@ -31,7 +31,7 @@ MODE = {"H": 0, "V": 1, "W": 2}
 EXPORTED = ["copa_create", "copa_destroy", "copa_last_error", "copa_sync", "copa_validate",
             "copa_procrustes", "copa_mttkrp", "copa_gram", "copa_admm_step", "copa_admm_w_fused",
             "copa_fit_value", "copa_fit", "copa_fit_host", "copa_smooth_plan",
-            "copa_smooth_project", "copa_loss_grad", "copa_procrustes_work"]
+            "copa_smooth_project", "copa_loss_grad", "copa_procrustes_work", "copa_gram_noalloc"]
 
 
 class CopaError(RuntimeError):
@@ -79,6 +79,7 @@ _sig = {
     "copa_loss_grad": [_V, POINTER(TensorC), c_int32, POINTER(ProcOutC), _V, _V, _V, _V, _V, _V,
                        _V],
     "copa_procrustes_work": [_V, POINTER(c_double)],
+    "copa_gram_noalloc": [_V, c_int32, _V, c_int64, c_int32, _V],
 }
 for _n, _a in _sig.items():
     getattr(_lib, _n).argtypes = _a
@@ -311,6 +312,17 @@ class Copa:
         self._call(_lib.copa_loss_grad, self.h, byref(X.c()), R, byref(self.proc_c(st)), _ptr(H), _ptr(V),
                                         _ptr(W), _ptr(loss), _ptr(gH), _ptr(gV), _ptr(gW))
         return loss, gH, gV, gW
+
+
+def gram_noalloc(A, G, stream):
+    """G = A^T A through copa_gram_noalloc, which allocates nothing (see include/copa.h).
+    A: rows x R float32/float64 CUDA tensor; G: R x R float64 CUDA tensor (written);
+    stream: a torch.cuda.Stream to enqueue on. Raises CopaError on a bad argument."""
+    import torch
+    code = _lib.copa_gram_noalloc(c_void_p(stream.cuda_stream), 1 if A.dtype == torch.float64 else 0,
+                                  _ptr(A), A.shape[0], A.shape[1], _ptr(G))
+    if code != OK:
+        raise CopaError(code, "copa_gram_noalloc failed")
 
 
 def reconstruction_loss(handle: Copa, X: DeviceTensor, H, V, W, tau=1e-8):

@@ -8,6 +8,8 @@
 //   F_V = sum_k Y_k^T H S_k      = sum_k X_k^T (Q_k H S_k)
 // so only F_V streams X again; it scatters x_ij * u_i into F_V(j,:) with
 // u_i = q_i H S_k, and accumulates U^T U = sum_i u_i^T u_i.
+#include <mutex>
+
 #include "copa_internal.cuh"
 
 namespace copa {
@@ -573,3 +575,70 @@ COPA_INST(double)
 
 }  // namespace copa
 
+
+// =====================================================================================
+// copa_gram_noalloc: the column Gram with its per-block partial sums in a fixed device
+// array owned by the library instead of the handle's workspace, for callers that cannot
+// allocate device memory. No counterpart in the paper.
+// =====================================================================================
+
+namespace copa {
+namespace {
+
+constexpr int kNoAllocMaxR = 90;                       // k_gram holds <= 8 entries/thread
+constexpr size_t kNoAllocScratchDoubles = 131072;      // 1 MiB of block partials
+__device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[256] = {nullptr};                 // resolved address per device
+
+}  // namespace
+
+}  // namespace copa
+
+extern "C" copa_status_t copa_gram_noalloc(void* stream, int32_t a_is_double, const void* A, int64_t rows,
+                                           int32_t R, double* G) {
+  using namespace copa;
+  if (!A || !G || rows < 0 || R < 1) return COPA_ERR_INVALID_ARG;
+  if (R > kNoAllocMaxR) return COPA_ERR_UNSUPPORTED;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+    cudaGetLastError();
+    return COPA_ERR_CUDA;
+  }
+  void* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      // host code cannot use the array's name as a device address: look it up once per
+      // device, with that device current
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return COPA_ERR_CUDA;
+      }
+      g_noalloc_addr[dev] = p;
+    }
+    scratch = g_noalloc_addr[dev];
+  }
+  const int npk = R * (R + 1) / 2;
+  const int threads = npk <= 256 ? 256 : 512;
+  int64_t blocks = (rows + 2047) / 2048;
+  const int64_t cap = (int64_t)(kNoAllocScratchDoubles / ((size_t)R * R));
+  if (blocks > cap) blocks = cap;
+  if (blocks > 304) blocks = 304;
+  if (blocks < 1) blocks = 1;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  double* part = reinterpret_cast<double*>(scratch);
+  // every block writes its whole R x R partial, so nothing has to be cleared first
+  if (a_is_double) {
+    k_gram<double><<<(unsigned)blocks, threads, sizeof(double) * 64 * (size_t)R, st>>>(
+        reinterpret_cast<const double*>(A), rows, R, part);
+  } else {
+    k_gram<float><<<(unsigned)blocks, threads, sizeof(float) * 64 * (size_t)R, st>>>(
+        reinterpret_cast<const float*>(A), rows, R, part);
+  }
+  k_reduce_rows<double><<<(R * R + 255) / 256, 256, 0, st>>>(part, (int)blocks, R * R, G);
+  if (cudaGetLastError() != cudaSuccess) return COPA_ERR_CUDA;
+  return COPA_OK;
+}

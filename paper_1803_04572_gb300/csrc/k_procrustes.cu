@@ -1,6 +1,6 @@
 // Procrustes step of COPA (Sec. 3.1, Eq. solv_Q; Algorithm 1 per-subject loop) and the
-// fused mode-1 MTTKRP, for all subjects in one persistent launch: one warp per subject,
-// dynamic scheduling over a largest-first subject order.
+// fused mode-1 MTTKRP, for all subjects in one persistent launch: one CTA of 128 threads
+// (4 warps) per subject, dynamic scheduling over a largest-first subject order.
 //
 // For subject k: P_k = X_k V (I_k x R), E_k = S_k H^T, A_k = P_k E_k. With the thin SVD
 // A_k = B D C^T, the update is Q_k = B C^T over the singular values kept by the rank
@@ -14,14 +14,21 @@
 //     Sigma and C, so Omega = C_K Sigma_K^{-1} C_K^T and Q_k = A_k Omega (rows recomputed
 //     in a second pass over X_k, which also accumulates T_k = sum_i q_i^T p_i).
 // Outputs per subject: Q_k rows (S x R), T_k = Q_k^T P_k (= Y_k V, R x R), optionally
-// Pi_k = Q_k^T Q_k = C_K C_K^T and the rank |K|; and F_H = sum_k T_k S_k through per-warp
+// Pi_k = Q_k^T Q_k = C_K C_K^T and the rank |K|; and F_H = sum_k T_k S_k through per-CTA
 // FP64 partial sums. The same code runs in float (mixed) or double (plain FP64).
+//
+// Parallel layout inside the CTA: rows of X_k are handled four at a time, one per warp
+// (lanes over the R components); the Jacobi pairs of a round are spread over the 128
+// threads with LP = 128 / pairs threads per pair (a power of two), each thread holding
+// R / LP components of the two vectors and the pair's dot products reduced by shuffles.
 #include "copa_internal.cuh"
 
 namespace copa {
 
 namespace {
 
+constexpr int kNT = 128;          // threads per CTA (one subject)
+constexpr int kNW = kNT / 32;     // warps per CTA = rows handled at once
 constexpr int kMaxSweeps = 30;
 
 template <typename Real>
@@ -39,32 +46,25 @@ __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
 
 struct Lay {
-  int R, ld, npk, np;   // np: max pairs per round
-  size_t Hs, Es, Zb, Pb, Ub, pv, av, al, vb, misc, cs, pq, pk, total;  // in Real units
+  int R, ld;
+  size_t Es, Zb, Pb, Ub, rv, al, vb, misc, total;  // in Real units
 };
 
 template <typename Real>
 __host__ __device__ inline Lay lay_of(int R) {
   Lay L;
   L.R = R;
-  L.ld = (R & 1) ? R + 2 : R + 1;   // odd leading dimension
-  L.npk = R * (R + 1) / 2;
-  L.np = R / 2 + 1;
+  L.ld = (R & 1) ? R + 2 : R + 1;   // odd leading dimension: conflict-free row/column access
   size_t o = 0;
   const size_t m = (size_t)R * L.ld;
-  L.Hs = o; o += m;
   L.Es = o; o += m;
   L.Zb = o; o += 2 * m;
   L.Pb = o; o += m;
   L.Ub = o; o += m;
-  L.pv = o; o += R;
-  L.av = o; o += R;
+  L.rv = o; o += (size_t)kNW * 3 * R;   // per-warp p, a, q vectors of one row
   L.al = o; o += R;
   L.vb = o; o += R + 1;
-  L.misc = o; o += 8;
-  L.cs = o; o += 2 * L.np;
-  L.pq = o; o += (2 * L.np * sizeof(int) + sizeof(Real) - 1) / sizeof(Real);
-  L.pk = o; o += (L.npk * sizeof(uint16_t) + sizeof(Real) - 1) / sizeof(Real);
+  L.misc = o; o += 8 + kNW;
   L.total = o;
   return L;
 }
@@ -73,50 +73,114 @@ __device__ __forceinline__ int rr_elem(int pos, int round, int n2) {
   return pos == 0 ? 0 : 1 + ((pos - 1 + round) % (n2 - 1));
 }
 
+template <typename Real>
+__device__ __forceinline__ Real warp_sum_r(Real v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// p_i = x_i V (lanes over components) for row i; the row's nonzeros are fetched 32 at a
+// time by the lanes and broadcast, so that the V-row gathers of a row are independent.
+template <typename Real>
+__device__ __forceinline__ void row_times_v(const TensorView& X, int64_t i, int R, const Real* __restrict__ V,
+                                            Real* __restrict__ pv) {
+  const int lane = threadIdx.x & 31;
+  const int64_t a = X.row_ptr[i], b = X.row_ptr[i + 1];
+  Real acc0 = Real(0), acc1 = Real(0), acc2 = Real(0);
+  for (int64_t c0 = a; c0 < b; c0 += 32) {
+    const int n = (int)min((int64_t)32, b - c0);
+    int col = 0;
+    Real x = Real(0);
+    if (lane < n) {
+      col = __ldg(X.col + c0 + lane);
+      x = load_x<Real>(X, c0 + lane);
+    }
+    for (int q = 0; q < n; ++q) {
+      const int cq = __shfl_sync(0xffffffffu, col, q);
+      const Real xq = __shfl_sync(0xffffffffu, x, q);
+      const Real* vr = V + (int64_t)cq * R;
+      if (lane < R) acc0 += xq * __ldg(vr + lane);
+      if (lane + 32 < R) acc1 += xq * __ldg(vr + lane + 32);
+      if (lane + 64 < R) acc2 += xq * __ldg(vr + lane + 64);
+    }
+  }
+  if (lane < R) pv[lane] = acc0;
+  if (lane + 32 < R) pv[lane + 32] = acc1;
+  if (lane + 64 < R) pv[lane + 64] = acc2;
+}
+
+// out = p M (lanes over t); M[r][t] at r*ld + t
+template <typename Real>
+__device__ __forceinline__ void vec_times_mat(const Real* __restrict__ p, const Real* __restrict__ M, int ld,
+                                              int R, Real* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  for (int t = lane; t < R; t += 32) {
+    Real a0 = Real(0), a1 = Real(0);
+    int r = 0;
+    for (; r + 1 < R; r += 2) {
+      a0 += p[r] * M[r * ld + t];
+      a1 += p[r + 1] * M[(r + 1) * ld + t];
+    }
+    if (r < R) a0 += p[r] * M[r * ld + t];
+    out[t] = a0 + a1;
+  }
+}
+
 // Householder QR update of the stacked [R_A (R x R, rows 0..R-1 of Z); block (nb rows,
 // rows R..R+nb-1 of Z)]: afterwards Z[0..R-1] holds the new R factor and the block is 0.
+// Thread c owns column c; warp 0 forms each reflector.
 template <typename Real>
 __device__ void tsqr_block(Real* Z, int ld, int R, int nb, Real* vb, Real* misc) {
-  const int lane = threadIdx.x & 31;
+  const int tid = threadIdx.x, lane = tid & 31;
   for (int j = 0; j < R; ++j) {
-    if (lane == (j & 31)) {
-      const Real x0 = Z[j * ld + j];
+    if (tid < 32) {
       Real ss = Real(0);
-      for (int i = 0; i < nb; ++i) {
+      for (int i = lane; i < nb; i += 32) {
         const Real v = Z[(R + i) * ld + j];
         ss += v * v;
       }
-      Real tau = Real(0);
+      ss = warp_sum_r(ss);
+      const Real x0 = Z[j * ld + j];
+      Real tau = Real(0), scale = Real(0), beta = x0;
       if (ss > Real(0)) {
         const Real nrm = sqrt(x0 * x0 + ss);
-        const Real beta = x0 >= Real(0) ? -nrm : nrm;
+        beta = x0 >= Real(0) ? -nrm : nrm;
         tau = (beta - x0) / beta;
-        const Real scale = Real(1) / (x0 - beta);
-        for (int i = 0; i < nb; ++i) {
-          vb[i] = Z[(R + i) * ld + j] * scale;
-          Z[(R + i) * ld + j] = Real(0);
-        }
+        scale = Real(1) / (x0 - beta);
+      }
+      __syncwarp();
+      for (int i = lane; i < nb; i += 32) {
+        vb[i] = Z[(R + i) * ld + j] * scale;
+        if (tau != Real(0)) Z[(R + i) * ld + j] = Real(0);
+      }
+      if (lane == 0) {
+        misc[0] = tau;
         Z[j * ld + j] = beta;
       }
-      misc[0] = tau;
     }
-    __syncwarp();
+    __syncthreads();
     const Real tau = misc[0];
     if (tau != Real(0)) {
-      for (int c = j + 1 + ((lane - (j + 1)) & 31); c < R; c += 32) {
-        Real w = Z[j * ld + c];
-        for (int i = 0; i < nb; ++i) w += vb[i] * Z[(R + i) * ld + c];
-        w *= tau;
+      for (int c = j + 1 + threadIdx.x; c < R; c += kNT) {
+        Real w0 = Z[j * ld + c], w1 = Real(0);
+        int i = 0;
+        for (; i + 1 < nb; i += 2) {
+          w0 += vb[i] * Z[(R + i) * ld + c];
+          w1 += vb[i + 1] * Z[(R + i + 1) * ld + c];
+        }
+        if (i < nb) w0 += vb[i] * Z[(R + i) * ld + c];
+        const Real w = (w0 + w1) * tau;
         Z[j * ld + c] -= w;
-        for (int i = 0; i < nb; ++i) Z[(R + i) * ld + c] -= vb[i] * w;
+        for (int q = 0; q < nb; ++q) Z[(R + q) * ld + c] -= vb[q] * w;
       }
     }
-    __syncwarp();
+    __syncthreads();
   }
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(32) k_procrustes(
+__global__ void __launch_bounds__(kNT) k_procrustes(
     TensorView X, int R, const Real* __restrict__ H, const Real* __restrict__ V,
     const Real* __restrict__ W, double tau_rank, Real* __restrict__ Q, Real* __restrict__ T,
     Real* __restrict__ Pi, int32_t* __restrict__ rank, double* __restrict__ fh_partial,
@@ -126,181 +190,188 @@ __global__ void __launch_bounds__(32) k_procrustes(
   Real* sm = reinterpret_cast<Real*>(smem_raw);
   const Lay L = lay_of<Real>(R);
   const int ld = L.ld;
-  const int lane = threadIdx.x;
-  Real* Hs = sm + L.Hs;   // H[t][r] at t*ld + r
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   Real* Es = sm + L.Es;   // E[r][t] = w_r H[t][r]
-  Real* Zb = sm + L.Zb;   // rows 0..R-1: A_k rows / R_A / c_j; rows R..2R-1: block, B, T
+  Real* Zb = sm + L.Zb;   // rows 0..R-1: A_k rows / R_A / c_j; rows R..2R-1: QR block, B
   Real* Pb = sm + L.Pb;   // wide: p rows; tall: Omega
-  Real* Ub = sm + L.Ub;   // wide: U
-  Real* pv = sm + L.pv;
-  Real* av = sm + L.av;
+  Real* Ub = sm + L.Ub;   // wide: U; tall: T accumulator
+  Real* pvw = sm + L.rv + (size_t)warp * 3 * R;   // this warp's p, a, q
+  Real* avw = pvw + R;
+  Real* qvw = avw + R;
   Real* al = sm + L.al;
   Real* vb = sm + L.vb;
   Real* misc = sm + L.misc;
-  Real* cs = sm + L.cs;
-  int* pq = reinterpret_cast<int*>(sm + L.pq);
-  uint16_t* pk = reinterpret_cast<uint16_t*>(sm + L.pk);
+  int* sidx = reinterpret_cast<int*>(misc + 8);
   const Real tol = Tol<Real>::v();
-  // work tally (lane 0): multiply-adds the algorithm performs, for the roofline
-  unsigned long long fma = 0;
+  unsigned long long fma = 0;   // work tally (thread 0), for the roofline
 
-  for (int i = lane; i < R * R; i += 32) Hs[(i / R) * ld + (i % R)] = H[i];
-  for (int r = 0, e = 0; r < R; ++r)
-    for (int s = r; s < R; ++s, ++e)
-      if ((e & 31) == lane) pk[e] = (uint16_t)((r << 8) | s);
   double* fh = fh_partial ? fh_partial + (size_t)blockIdx.x * R * R : nullptr;
   if (fh)
-    for (int i = lane; i < R * R; i += 32) fh[i] = 0.0;
-  __syncwarp();
+    for (int i = tid; i < R * R; i += kNT) fh[i] = 0.0;
 
   while (true) {
-    int idx = 0;
-    if (lane == 0) idx = atomicAdd(counter, 1);
-    idx = __shfl_sync(0xffffffffu, idx, 0);
+    __syncthreads();
+    if (tid == 0) sidx[0] = atomicAdd(counter, 1);
+    __syncthreads();
+    const int idx = sidx[0];
     if (idx >= X.K) break;
     const int64_t k = order ? order[idx] : idx;
     const int64_t r0 = X.subj_ptr[k], r1 = X.subj_ptr[k + 1];
-    const int Ik = (int)(r1 - r0 < (int64_t)R + 1 ? r1 - r0 : (int64_t)R + 1);
-    const bool wide = Ik <= R;
-    const int m = wide ? Ik : R;
-    const unsigned long long nnzk = (unsigned long long)(X.row_ptr[r1] - X.row_ptr[r0]);
-    const unsigned long long ik = (unsigned long long)(r1 - r0), RR = (unsigned long long)R * R;
-    // rows: p_i and a_i; tall: Householder QR (~R^2 per row) and the second pass
-    fma += nnzk * R + ik * RR;
-    if (!wide) fma += ik * RR + nnzk * R + 3 * ik * RR + 2 * RR * R;
-    else fma += 2ull * m * m * R + 2ull * RR * m;
-    fma += 2ull * m * R;   // norms and normalisation
+    const int64_t Ik64 = r1 - r0;
+    const bool wide = Ik64 <= R;
+    const int m = wide ? (int)Ik64 : R;
+    if (tid == 0) {
+      const unsigned long long nnzk = (unsigned long long)(X.row_ptr[r1] - X.row_ptr[r0]);
+      const unsigned long long ik = (unsigned long long)Ik64, RR = (unsigned long long)R * R;
+      fma += nnzk * R + ik * RR + 2ull * m * R;
+      if (!wide) fma += ik * RR + nnzk * R + 3 * ik * RR + 2 * RR * R;
+      else fma += 2ull * m * m * R + 2ull * RR * m;
+    }
 
-    // ---- E = S_k H^T; clear R_A (tall) or nothing (wide) and G ----
-    for (int r = lane; r < R; r += 32) al[r] = W[k * R + r];
-    __syncwarp();
-    for (int e = lane; e < R * R; e += 32) {
+    // ---- E = S_k H^T; tall: clear R_A and the T accumulator; wide: U = I ----
+    for (int e = tid; e < R * R; e += kNT) {
       const int r = e / R, t = e - r * R;
-      Es[r * ld + t] = al[r] * Hs[t * ld + r];
-      if (!wide) Zb[r * ld + t] = Real(0);
+      Es[r * ld + t] = W[k * R + r] * __ldg(H + t * R + r);
+      if (!wide) {
+        Zb[r * ld + t] = Real(0);
+        Ub[r * ld + t] = Real(0);
+      } else if (r < m && t < m) {
+        Ub[r * ld + t] = (r == t) ? Real(1) : Real(0);
+      }
     }
-    __syncwarp();
+    __syncthreads();
 
-    // ---- pass 1 over the rows: p_i, a_i = p_i E; wide: keep both; tall: G, TSQR ----
-    int nb = 0;
-    for (int64_t i = r0; i < r1; ++i) {
-      const int64_t a = X.row_ptr[i], b = X.row_ptr[i + 1];
-      for (int r = lane; r < R; r += 32) {
-        Real acc = Real(0);
-        for (int64_t t = a; t < b; ++t)
-          acc += load_x<Real>(X, t) * __ldg(V + (int64_t)__ldg(X.col + t) * R + r);
-        pv[r] = acc;
+    // ---- pass 1: rows four at a time, a_i = (x_i V) E; wide: keep p_i and a_i;
+    //      tall: fill a QR block of up to R rows, then fold it into R_A ----
+    int nb = 0;   // rows in the QR block (tall); always < R before a group
+    for (int64_t g = r0; g < r1;) {
+      int nrow = (int)min((int64_t)kNW, r1 - g);
+      if (!wide && nrow > R - nb) nrow = R - nb;   // the block holds at most R rows
+      const int64_t i = g + warp;
+      if (warp < nrow) {
+        row_times_v<Real>(X, i, R, V, pvw);
+        __syncwarp();
+        const int row = wide ? (int)(i - r0) : R + nb + warp;
+        vec_times_mat<Real>(pvw, Es, ld, R, Zb + row * ld);
+        if (wide)
+          for (int t = lane; t < R; t += 32) Pb[row * ld + t] = pvw[t];
       }
-      __syncwarp();
-      const int row = wide ? (int)(i - r0) : R + nb;
-      for (int t = lane; t < R; t += 32) {
-        Real acc = Real(0);
-        for (int r = 0; r < R; ++r) acc += pv[r] * Es[r * ld + t];
-        Zb[row * ld + t] = acc;
-        if (wide) Pb[row * ld + t] = pv[t];
-      }
-      __syncwarp();
-      if (!wide && ++nb == R) {
-        tsqr_block<Real>(Zb, ld, R, nb, vb, misc);
-        nb = 0;
+      __syncthreads();
+      g += nrow;
+      if (!wide) {
+        nb += nrow;
+        if (nb == R || g >= r1) {
+          tsqr_block<Real>(Zb, ld, R, nb, vb, misc);
+          nb = 0;
+        }
       }
     }
-    if (!wide && nb > 0) tsqr_block<Real>(Zb, ld, R, nb, vb, misc);
 
     // ---- Hestenes one-sided Jacobi on rows 0..m-1 of Zb (U accumulated if wide) ----
-    if (wide)
-      for (int e = lane; e < m * m; e += 32) Ub[(e / m) * ld + (e % m)] = (e / m == e % m) ? Real(1) : Real(0);
-    __syncwarp();
     const int n2 = m + (m & 1);
+    const int npairs = n2 / 2;
+    int LP = 1;
+    while (LP < 32 && npairs * LP * 2 <= kNT) LP <<= 1;
+    const int pj = tid / LP, sl = tid % LP;
     for (int sweep = 0; sweep < kMaxSweeps && n2 > 1; ++sweep) {
-      int nrot = 0, ntest = 0;
+      int nrot = 0;
       for (int round = 0; round < n2 - 1; ++round) {
-        for (int pj = lane; pj < n2 / 2; pj += 32) {
-          int ii = rr_elem(pj, round, n2), jj = rr_elem(n2 - 1 - pj, round, n2);
+        bool rotated = false;
+        int ii = 0, jj = 0;
+        const bool act = pj < npairs;
+        if (act) {
+          ii = rr_elem(pj, round, n2);
+          jj = rr_elem(n2 - 1 - pj, round, n2);
           if (ii > jj) { const int tmp = ii; ii = jj; jj = tmp; }
-          if (jj >= m) continue;
-          ++ntest;
-          Real* zi = Zb + ii * ld;
-          Real* zj = Zb + jj * ld;
-          Real aa = Real(0), bb = Real(0), gg = Real(0);
-          for (int t = 0; t < R; ++t) {
+        }
+        const bool real_pair = act && jj < m;
+        Real aa = Real(0), bb = Real(0), gg = Real(0);
+        Real* zi = Zb + ii * ld;
+        Real* zj = Zb + jj * ld;
+        if (real_pair)
+          for (int t = sl; t < R; t += LP) {
             const Real x = zi[t], y = zj[t];
             aa += x * x;
             bb += y * y;
             gg += x * y;
           }
-          if (gg != Real(0) && fabs(gg) > tol * sqrt(aa * bb)) {
-            const Real zeta = (bb - aa) / (Real(2) * gg);
-            Real tt;
-            if (fabs(zeta) > Real(1e15)) tt = Real(0.5) / zeta;
-            else tt = (zeta >= Real(0) ? Real(1) : Real(-1)) / (fabs(zeta) + sqrt(Real(1) + zeta * zeta));
-            const Real c = rsqrt_(Real(1) + tt * tt), s = c * tt;
-            for (int t = 0; t < R; ++t) {
-              const Real x = zi[t], y = zj[t];
-              zi[t] = c * x - s * y;
-              zj[t] = s * x + c * y;
-            }
-            if (wide) {
-              Real* ui = Ub + ii * ld;
-              Real* uj = Ub + jj * ld;
-              for (int t = 0; t < m; ++t) {
-                const Real x = ui[t], y = uj[t];
-                ui[t] = c * x - s * y;
-                uj[t] = s * x + c * y;
-              }
-            }
-            ++nrot;
-          }
+        // reduce over the LP threads of the pair (aligned groups inside one warp)
+        for (int o = LP >> 1; o > 0; o >>= 1) {
+          aa += __shfl_xor_sync(0xffffffffu, aa, o);
+          bb += __shfl_xor_sync(0xffffffffu, bb, o);
+          gg += __shfl_xor_sync(0xffffffffu, gg, o);
         }
-        __syncwarp();
+        if (real_pair && gg != Real(0) && fabs(gg) > tol * sqrt(aa * bb)) {
+          const Real zeta = (bb - aa) / (Real(2) * gg);
+          Real tt;
+          if (fabs(zeta) > Real(1e15)) tt = Real(0.5) / zeta;
+          else tt = (zeta >= Real(0) ? Real(1) : Real(-1)) / (fabs(zeta) + sqrt(Real(1) + zeta * zeta));
+          const Real c = rsqrt_(Real(1) + tt * tt), s = c * tt;
+          for (int t = sl; t < R; t += LP) {
+            const Real x = zi[t], y = zj[t];
+            zi[t] = c * x - s * y;
+            zj[t] = s * x + c * y;
+          }
+          if (wide) {
+            Real* ui = Ub + ii * ld;
+            Real* uj = Ub + jj * ld;
+            for (int t = sl; t < m; t += LP) {
+              const Real x = ui[t], y = uj[t];
+              ui[t] = c * x - s * y;
+              uj[t] = s * x + c * y;
+            }
+          }
+          rotated = sl == 0;
+        }
+        nrot += __syncthreads_count(rotated);
       }
-      const int tot_rot = warp_sum(nrot), tot_test = warp_sum(ntest);
-      fma += (unsigned long long)tot_test * 3 * R + (unsigned long long)tot_rot * 4 * (R + (wide ? m : 0));
-      if (tot_rot == 0) break;
+      if (tid == 0)
+        fma += (unsigned long long)(m * (m - 1) / 2) * 3 * R + (unsigned long long)nrot * 4 * (R + (wide ? m : 0));
+      if (nrot == 0) break;
     }
 
     // ---- singular values, rank cut, normalised right singular vectors c_j ----
-    Real amax = Real(0);
-    for (int j = lane; j < m; j += 32) {
+    for (int j = tid; j < m; j += kNT) {
       Real acc = Real(0);
       for (int t = 0; t < R; ++t) acc += Zb[j * ld + t] * Zb[j * ld + t];
       al[j] = acc;
-      amax = acc > amax ? acc : amax;
     }
-    amax = warp_max(amax);
-    int kept = 0;
-    for (int j = lane; j < m; j += 32) {
-      const bool keep = amax > Real(0) && (double)al[j] > tau_rank * (double)amax;
-      al[j] = keep ? rsqrt_(al[j]) : Real(0);   // 1 / sigma_j, 0 if dropped
-      kept += keep ? 1 : 0;
+    __syncthreads();
+    if (tid < 32) {
+      Real amax = Real(0);
+      for (int j = lane; j < m; j += 32) amax = al[j] > amax ? al[j] : amax;
+      amax = warp_max(amax);
+      int kept = 0;
+      for (int j = lane; j < m; j += 32) {
+        const bool keep = amax > Real(0) && (double)al[j] > tau_rank * (double)amax;
+        al[j] = keep ? rsqrt_(al[j]) : Real(0);   // 1 / sigma_j, 0 if dropped
+        kept += keep ? 1 : 0;
+      }
+      kept = warp_sum(kept);
+      if (rank && lane == 0) rank[k] = kept;
     }
-    kept = warp_sum(kept);
-    if (rank && lane == 0) rank[k] = kept;
-    __syncwarp();
-    for (int e = lane; e < m * R; e += 32) {
+    __syncthreads();
+    for (int e = tid; e < m * R; e += kNT) {
       const int j = e / R, t = e - j * R;
       Zb[j * ld + t] *= al[j];
     }
-    __syncwarp();
+    __syncthreads();
 
     Real* Tk = T + k * R * R;
     if (wide) {
-      // Q rows: q_i = sum_j U[j][i] c_j
-      for (int e = lane; e < m * R; e += 32) {
+      // Q rows q_i = sum_j U[j][i] c_j; B = U P -> rows R.. of Zb
+      for (int e = tid; e < m * R; e += kNT) {
         const int i = e / R, t = e - i * R;
-        Real acc = Real(0);
-        for (int j = 0; j < m; ++j) acc += Ub[j * ld + i] * Zb[j * ld + t];
+        Real acc = Real(0), bacc = Real(0);
+        for (int j = 0; j < m; ++j) {
+          acc += Ub[j * ld + i] * Zb[j * ld + t];
+          bacc += Ub[i * ld + j] * Pb[j * ld + t];
+        }
         Q[(r0 + i) * R + t] = acc;
+        Zb[(R + i) * ld + t] = bacc;
       }
-      // B = U P -> rows R.. of Zb
-      for (int e = lane; e < m * R; e += 32) {
-        const int j = e / R, s = e - j * R;
-        Real acc = Real(0);
-        for (int i = 0; i < m; ++i) acc += Ub[j * ld + i] * Pb[i * ld + s];
-        Zb[(R + j) * ld + s] = acc;
-      }
-      __syncwarp();
-      for (int e = lane; e < R * R; e += 32) {
+      __syncthreads();
+      for (int e = tid; e < R * R; e += kNT) {
         const int r = e / R, s = e - r * R;
         Real acc = Real(0), pacc = Real(0);
         for (int j = 0; j < m; ++j) {
@@ -311,10 +382,9 @@ __global__ void __launch_bounds__(32) k_procrustes(
         if (Pi) Pi[k * R * R + e] = pacc;
         if (fh) fh[e] += (double)acc * (double)W[k * R + s];
       }
-      __syncwarp();
     } else {
-      // Omega = sum_j c_j c_j^T / sigma_j -> Pb; Pi -> global; clear the T accumulator
-      for (int e = lane; e < R * R; e += 32) {
+      // Omega = sum_j c_j c_j^T / sigma_j -> Pb; Pi -> global
+      for (int e = tid; e < R * R; e += kNT) {
         const int r = e / R, t = e - r * R;
         Real acc = Real(0), pacc = Real(0);
         for (int j = 0; j < R; ++j) {
@@ -324,48 +394,42 @@ __global__ void __launch_bounds__(32) k_procrustes(
         }
         Pb[r * ld + t] = acc;
         if (Pi) Pi[k * R * R + e] = pacc;
-        Zb[(R + r) * ld + t] = Real(0);
       }
-      __syncwarp();
-      // pass 2: q_i = (p_i E) Omega, T_k += q_i^T p_i
-      for (int64_t i = r0; i < r1; ++i) {
-        const int64_t a = X.row_ptr[i], b = X.row_ptr[i + 1];
-        for (int r = lane; r < R; r += 32) {
-          Real acc = Real(0);
-          for (int64_t t = a; t < b; ++t)
-            acc += load_x<Real>(X, t) * __ldg(V + (int64_t)__ldg(X.col + t) * R + r);
-          pv[r] = acc;
+      __syncthreads();
+      // pass 2, rows four at a time: q_i = (p_i E) Omega; T_k += q_i^T p_i
+      for (int64_t g = r0; g < r1; g += kNW) {
+        const int64_t i = g + warp;
+        const int nrow = (int)min((int64_t)kNW, r1 - g);
+        if (warp < nrow) {
+          row_times_v<Real>(X, i, R, V, pvw);
+          __syncwarp();
+          vec_times_mat<Real>(pvw, Es, ld, R, avw);
+          __syncwarp();
+          vec_times_mat<Real>(avw, Pb, ld, R, qvw);
+          __syncwarp();
+          for (int t = lane; t < R; t += 32) Q[i * R + t] = qvw[t];
         }
-        __syncwarp();
-        for (int t = lane; t < R; t += 32) {
-          Real acc = Real(0);
-          for (int r = 0; r < R; ++r) acc += pv[r] * Es[r * ld + t];
-          av[t] = acc;
-        }
-        __syncwarp();
-        for (int t = lane; t < R; t += 32) {
-          Real acc = Real(0);
-          for (int r = 0; r < R; ++r) acc += av[r] * Pb[r * ld + t];
-          Q[i * R + t] = acc;
-          al[t] = acc;
-        }
-        __syncwarp();
-        for (int e = lane; e < R * R; e += 32) {
+        __syncthreads();
+        for (int e = tid; e < R * R; e += kNT) {
           const int r = e / R, s = e - r * R;
-          Zb[(R + r) * ld + s] += al[r] * pv[s];
+          Real acc = Ub[r * ld + s];
+          for (int w = 0; w < nrow; ++w) {
+            const Real* base = sm + L.rv + (size_t)w * 3 * R;
+            acc += base[2 * R + r] * base[s];
+          }
+          Ub[r * ld + s] = acc;
         }
-        __syncwarp();
+        __syncthreads();
       }
-      for (int e = lane; e < R * R; e += 32) {
+      for (int e = tid; e < R * R; e += kNT) {
         const int r = e / R, s = e - r * R;
-        const Real acc = Zb[(R + r) * ld + s];
+        const Real acc = Ub[r * ld + s];
         Tk[e] = acc;
         if (fh) fh[e] += (double)acc * (double)W[k * R + s];
       }
-      __syncwarp();
     }
   }
-  if (fma_count && lane == 0) atomicAdd(fma_count, fma);
+  if (fma_count && tid == 0) atomicAdd(fma_count, fma);
 }
 
 template <typename Real>
@@ -390,7 +454,7 @@ copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const R
                                 const Real* V, const Real* W, double tau, Real* Q, Real* T,
                                 Real* Pi, int32_t* rank, Real* F_H) {
   const size_t smem = procrustes_smem<Real>(R);
-  if (R < 1 || smem > 227 * 1024)
+  if (R < 1 || R > kNT || smem > 227 * 1024)
     return fail(h, COPA_ERR_UNSUPPORTED, "Procrustes: R too large for shared memory at this precision");
   copa_status_t st;
   if ((st = cuda_check(h, cudaFuncSetAttribute(k_procrustes<Real>,
@@ -399,7 +463,7 @@ copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const R
     return st;
   int per_sm = 0;
   if ((st = cuda_check(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_procrustes<Real>,
-                                                                        32, smem),
+                                                                        kNT, smem),
                        "occupancy")) != COPA_OK)
     return st;
   if (per_sm < 1) per_sm = 1;
@@ -417,8 +481,8 @@ copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const R
   }
   if ((st = cuda_check(h, cudaMemsetAsync(counter, 0, 16, h->stream), "memset")) != COPA_OK)
     return st;
-  k_procrustes<Real><<<(unsigned)blocks, 32, smem, h->stream>>>(X, R, H, V, W, tau, Q, T, Pi, rank, part,
-                                                               order, counter, fma_count);
+  k_procrustes<Real><<<(unsigned)blocks, kNT, smem, h->stream>>>(X, R, H, V, W, tau, Q, T, Pi, rank, part,
+                                                                order, counter, fma_count);
   if ((st = cuda_check(h, cudaGetLastError(), "k_procrustes launch")) != COPA_OK) return st;
   if (F_H) {
     k_reduce_partials<Real><<<(R * R + 255) / 256, 256, 0, h->stream>>>(part, (int)blocks, R * R, F_H);

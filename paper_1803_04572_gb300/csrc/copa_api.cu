@@ -131,6 +131,34 @@ __global__ void k_xnorm2(TensorView X, double* __restrict__ out) {
   if (threadIdx.x == 0) atomicAdd(out, red[0]);
 }
 
+__global__ void k_warm_sizes(const int64_t* __restrict__ subj_ptr, int64_t K, int R, int64_t* __restrict__ out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K; k += gridDim.x * (int64_t)blockDim.x) {
+    const int64_t ik = subj_ptr[k + 1] - subj_ptr[k];
+    const int64_t m = ik < R ? ik : R;
+    out[k] = m * m;
+  }
+}
+
+// exclusive scan of n values in place into out[0..n] (single block)
+__global__ void k_scan_inplace(int64_t* __restrict__ v, int64_t n) {
+  __shared__ int64_t part[1024];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int64_t per = (n + nt - 1) / nt;
+  const int64_t a = tid * per, b = min(n, a + per);
+  int64_t s = 0;
+  for (int64_t i = a; i < b; ++i) s += v[i];
+  part[tid] = s;
+  __syncthreads();
+  if (tid == 0) {
+    int64_t acc = 0;
+    for (int i = 0; i < nt; ++i) { const int64_t x = part[i]; part[i] = acc; acc += x; }
+    v[n] = acc;
+  }
+  __syncthreads();
+  s = part[tid];
+  for (int64_t i = a; i < b; ++i) { const int64_t x = v[i]; v[i] = s; s += x; }
+}
+
 __global__ void k_store_fit(const double* __restrict__ fit, double* __restrict__ hist, int* __restrict__ it) {
   hist[*it] = *fit;
   *it += 1;
@@ -161,6 +189,36 @@ copa_status_t get_schedule(copa_ctx* h, const TensorView& X, const int64_t** ord
   h->sched_K = X.K;
   h->sched_S = X.S;
   *order = ord;
+  return COPA_OK;
+}
+
+copa_status_t get_warm_offsets(copa_ctx* h, const TensorView& X, int R, const int64_t** woff, int64_t* total) {
+  copa_status_t st;
+  if (h->warm_key == X.subj_ptr && h->warm_K == X.K && h->warm_S == X.S && h->warm_R == R &&
+      h->slot_ptr[SLOT_WARM_OFF]) {
+    *woff = reinterpret_cast<const int64_t*>(h->slot_ptr[SLOT_WARM_OFF]);
+    *total = h->warm_total;
+    return COPA_OK;
+  }
+  int64_t* off = nullptr;
+  if ((st = ws_get(h, SLOT_WARM_OFF, sizeof(int64_t) * (X.K + 1), (void**)&off)) != COPA_OK) return st;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((X.K + 255) / 256, 4096));
+  k_warm_sizes<<<blocks, 256, 0, h->stream>>>(X.subj_ptr, X.K, R, off);
+  k_scan_inplace<<<1, 1024, 0, h->stream>>>(off, X.K);
+  if ((st = cuda_check(h, cudaGetLastError(), "warm offsets")) != COPA_OK) return st;
+  int64_t tot = 0;
+  if ((st = cuda_check(h, cudaMemcpyAsync(&tot, off + X.K, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream),
+                       "D2H")) != COPA_OK)
+    return st;
+  if ((st = cuda_check(h, cudaStreamSynchronize(h->stream), "sync")) != COPA_OK) return st;
+  h->warm_key = X.subj_ptr;
+  h->warm_K = X.K;
+  h->warm_S = X.S;
+  h->warm_R = R;
+  h->warm_total = tot;
+  h->warm_valid = false;
+  *woff = off;
+  *total = tot;
   return COPA_OK;
 }
 
@@ -432,6 +490,8 @@ namespace {
 
 template <typename Real>
 struct FitBufs {
+  Real* Uw;
+  const int64_t* woff;
   Real* Q;
   Real* T;
   Real* Pi;
@@ -452,10 +512,10 @@ struct FitBufs {
 
 template <typename Real>
 copa_status_t one_iteration(copa_ctx* h, const TensorView& X, const copa_options_t* o, Real* H, Real* V,
-                            Real* W, Real* DH, Real* DV, Real* DW, const FitBufs<Real>& b) {
+                            Real* W, Real* DH, Real* DV, Real* DW, const FitBufs<Real>& b, bool warm_in) {
   const int R = o->R;
   // (a)+(b) Procrustes, with the H-mode MTTKRP fused
-  TRY(launch_procrustes<Real>(h, X, R, H, V, W, o->tau, b.Q, b.T, b.Pi, b.rank, b.FH));
+  TRY(launch_procrustes<Real>(h, X, R, H, V, W, o->tau, b.Q, b.T, b.Pi, b.rank, b.FH, b.Uw, b.woff, warm_in));
   // H: G = W^T W .* V^T V
   TRY(launch_gram<Real>(h, W, X.K, R, b.gW));
   TRY(launch_gram<Real>(h, V, X.J, R, b.gV));
@@ -518,9 +578,16 @@ copa_status_t fit_impl(copa_ctx* h, const copa_tensor_t* Xc, const copa_options_
   b.Ginv = (Real*)take(sizeof(Real) * R * (R + 1));
   TRY(cuda_check(h, cudaMemsetAsync(b.it, 0, sizeof(int), h->stream), "memset"));
   TRY(launch_xnorm2(h, X, b.xn2));
+  {
+    int64_t wtot = 0;
+    TRY(get_warm_offsets(h, X, R, &b.woff, &wtot));
+    TRY(ws_get(h, SLOT_WARM, sizeof(Real) * (size_t)(wtot + 1), (void**)&b.Uw));
+  }
   if (o->n_outer > 0) {
     // the first iteration runs eagerly: it sizes every workspace buffer
-    TRY(one_iteration<Real>(h, X, o, H, V, W, DH, DV, DW, b));
+    TRY(one_iteration<Real>(h, X, o, H, V, W, DH, DV, DW, b, h->warm_valid && h->warm_prec == h->precision));
+    h->warm_valid = true;
+    h->warm_prec = h->precision;
   }
   if (o->n_outer > 1) {
     if (o->use_graph) {
@@ -531,7 +598,7 @@ copa_status_t fit_impl(copa_ctx* h, const copa_tensor_t* Xc, const copa_options_
       TRY(cuda_check(h, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "cudaStreamCreate"));
       h->stream = cap;
       cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
-      copa_status_t cs = ce == cudaSuccess ? one_iteration<Real>(h, X, o, H, V, W, DH, DV, DW, b) : COPA_OK;
+      copa_status_t cs = ce == cudaSuccess ? one_iteration<Real>(h, X, o, H, V, W, DH, DV, DW, b, true) : COPA_OK;
       if (ce == cudaSuccess) ce = cudaStreamEndCapture(cap, &graph);
       h->stream = orig;
       cudaStreamDestroy(cap);
@@ -551,7 +618,7 @@ copa_status_t fit_impl(copa_ctx* h, const copa_tensor_t* Xc, const copa_options_
       cudaGraphExecDestroy(exec);
       TRY(cuda_check(h, ce, "GraphLaunch"));
     } else {
-      for (int it = 1; it < o->n_outer; ++it) TRY(one_iteration<Real>(h, X, o, H, V, W, DH, DV, DW, b));
+      for (int it = 1; it < o->n_outer; ++it) TRY(one_iteration<Real>(h, X, o, H, V, W, DH, DV, DW, b, true));
     }
   }
   TRY(sync_status(h));

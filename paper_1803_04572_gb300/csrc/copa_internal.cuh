@@ -121,6 +121,12 @@ struct copa_ctx {
   // CUDA graph of one outer iteration
   cudaGraphExec_t graph_exec = nullptr;
   uint64_t graph_key = 0;
+  // cached warm-start offsets (per tensor and rank)
+  const int64_t* warm_key = nullptr;
+  int64_t warm_K = 0, warm_S = 0, warm_total = 0;
+  int warm_R = 0;
+  int warm_prec = -1;
+  bool warm_valid = false;   // the buffer holds the rotations of a finished iteration
 };
 
 namespace copa {
@@ -137,7 +143,11 @@ enum Slot {
   SLOT_SMOOTH = 8,     // smoothing set-up temporaries
   SLOT_MISC = 9,
   SLOT_PI = 10,
+  SLOT_WARM = 11,      // copa_fit: per-subject Jacobi rotations kept between iterations
+  SLOT_WARM_OFF = 12,  // int64[K+1] offsets of the min(I_k,R)^2 blocks
 };
+copa_status_t get_warm_offsets(copa_ctx* h, const TensorView& X, int R, const int64_t** woff,
+                               int64_t* total);
 
 copa_status_t ws_get(copa_ctx* h, int slot, size_t bytes, void** out);
 copa_status_t fail(copa_ctx* h, copa_status_t code, const std::string& msg);
@@ -150,7 +160,8 @@ copa_status_t get_schedule(copa_ctx* h, const TensorView& X, const int64_t** ord
 template <typename Real>
 copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const Real* H,
                                 const Real* V, const Real* W, double tau, Real* Q, Real* T,
-                                Real* Pi, int32_t* rank, Real* F_H);
+                                Real* Pi, int32_t* rank, Real* F_H, Real* Uw = nullptr,
+                                const int64_t* woff = nullptr, bool warm_in = false);
 template <typename Real>
 size_t procrustes_smem(int R);
 template <typename Real>

@@ -13,6 +13,10 @@
 //     A_k = Q_A R_A (R_A upper triangular R x R); Hestenes on the rows of R_A gives
 //     Sigma and C, so Omega = C_K Sigma_K^{-1} C_K^T and Q_k = A_k Omega (rows recomputed
 //     in a second pass over X_k, which also accumulates T_k = sum_i q_i^T p_i).
+// Warm start (copa_fit): the left rotation U of each subject (Z = U A) is kept between
+// outer iterations; the next iteration starts the Jacobi sweeps from U_prev A, which is
+// nearly row-orthogonal once the factors settle, so fewer sweeps are needed. The result
+// is the same SVD (up to rounding).
 // Outputs per subject: Q_k rows (S x R), T_k = Q_k^T P_k (= Y_k V, R x R), optionally
 // Pi_k = Q_k^T Q_k = C_K C_K^T and the rank |K|; and F_H = sum_k T_k S_k through per-CTA
 // FP64 partial sums. The same code runs in float (mixed) or double (plain FP64).
@@ -72,6 +76,12 @@ __host__ __device__ inline Lay lay_of(int R) {
 __device__ __forceinline__ int rr_elem(int pos, int round, int n2) {
   return pos == 0 ? 0 : 1 + ((pos - 1 + round) % (n2 - 1));
 }
+
+// Element at a round-robin position in the next round (position 0 stays at element 0).
+__device__ __forceinline__ int rr_next(int e, int n2) { return e == 0 ? 0 : (e == n2 - 1 ? 1 : e + 1); }
+
+__device__ __forceinline__ float fdiv_(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv_(double a, double b) { return a / b; }
 
 template <typename Real>
 __device__ __forceinline__ Real warp_sum_r(Real v) {
@@ -185,7 +195,8 @@ __global__ void __launch_bounds__(kNT) k_procrustes(
     const Real* __restrict__ W, double tau_rank, Real* __restrict__ Q, Real* __restrict__ T,
     Real* __restrict__ Pi, int32_t* __restrict__ rank, double* __restrict__ fh_partial,
     const int64_t* __restrict__ order, int* __restrict__ counter,
-    unsigned long long* __restrict__ fma_count) {
+    unsigned long long* __restrict__ fma_count, Real* __restrict__ Uw,
+    const int64_t* __restrict__ woff, int warm_in) {
   extern __shared__ unsigned char smem_raw[];
   Real* sm = reinterpret_cast<Real*>(smem_raw);
   const Lay L = lay_of<Real>(R);
@@ -194,7 +205,7 @@ __global__ void __launch_bounds__(kNT) k_procrustes(
   Real* Es = sm + L.Es;   // E[r][t] = w_r H[t][r]
   Real* Zb = sm + L.Zb;   // rows 0..R-1: A_k rows / R_A / c_j; rows R..2R-1: QR block, B
   Real* Pb = sm + L.Pb;   // wide: p rows; tall: Omega
-  Real* Ub = sm + L.Ub;   // wide: U; tall: T accumulator
+  Real* Ub = sm + L.Ub;   // U (wide, or any subject with a warm-start buffer); tall: then T
   Real* pvw = sm + L.rv + (size_t)warp * 3 * R;   // this warp's p, a, q
   Real* avw = pvw + R;
   Real* qvw = avw + R;
@@ -228,16 +239,11 @@ __global__ void __launch_bounds__(kNT) k_procrustes(
       else fma += 2ull * m * m * R + 2ull * RR * m;
     }
 
-    // ---- E = S_k H^T; tall: clear R_A and the T accumulator; wide: U = I ----
+    // ---- E = S_k H^T; tall: clear R_A ----
     for (int e = tid; e < R * R; e += kNT) {
       const int r = e / R, t = e - r * R;
       Es[r * ld + t] = W[k * R + r] * __ldg(H + t * R + r);
-      if (!wide) {
-        Zb[r * ld + t] = Real(0);
-        Ub[r * ld + t] = Real(0);
-      } else if (r < m && t < m) {
-        Ub[r * ld + t] = (r == t) ? Real(1) : Real(0);
-      }
+      if (!wide) Zb[r * ld + t] = Real(0);
     }
     __syncthreads();
 
@@ -267,23 +273,47 @@ __global__ void __launch_bounds__(kNT) k_procrustes(
       }
     }
 
-    // ---- Hestenes one-sided Jacobi on rows 0..m-1 of Zb (U accumulated if wide) ----
+    // ---- Hestenes one-sided Jacobi on rows 0..m-1 of Zb. U (Z = U A) is accumulated for
+    //      wide subjects (it gives Q) and whenever a warm-start buffer is given; a warm
+    //      start begins from the previous outer iteration's U: Z = U_prev A. ----
+    const bool accU = wide || Uw != nullptr;
+    Real* Uk = Uw ? Uw + woff[k] : nullptr;
+    if (accU) {
+      for (int e = tid; e < m * m; e += kNT) {
+        const int r = e / m, t = e - r * m;
+        Ub[r * ld + t] = (Uk && warm_in) ? Uk[e] : ((r == t) ? Real(1) : Real(0));
+      }
+      __syncthreads();
+      if (Uk && warm_in) {
+        for (int e = tid; e < m * R; e += kNT) {
+          const int i = e / R, t = e - i * R;
+          Real acc = Real(0);
+          for (int j = 0; j < m; ++j) acc += Ub[i * ld + j] * Zb[j * ld + t];
+          Zb[(R + i) * ld + t] = acc;
+        }
+        __syncthreads();
+        for (int e = tid; e < m * R; e += kNT) {
+          const int i = e / R, t = e - i * R;
+          Zb[i * ld + t] = Zb[(R + i) * ld + t];
+        }
+        __syncthreads();
+        if (tid == 0) fma += (unsigned long long)m * m * R;
+      }
+    }
     const int n2 = m + (m & 1);
     const int npairs = n2 / 2;
     int LP = 1;
     while (LP < 32 && npairs * LP * 2 <= kNT) LP <<= 1;
     const int pj = tid / LP, sl = tid % LP;
+    const bool act = pj < npairs;
     for (int sweep = 0; sweep < kMaxSweeps && n2 > 1; ++sweep) {
       int nrot = 0;
+      int e1 = act ? rr_elem(pj, 0, n2) : 0, e2 = act ? rr_elem(n2 - 1 - pj, 0, n2) : 0;
       for (int round = 0; round < n2 - 1; ++round) {
         bool rotated = false;
-        int ii = 0, jj = 0;
-        const bool act = pj < npairs;
-        if (act) {
-          ii = rr_elem(pj, round, n2);
-          jj = rr_elem(n2 - 1 - pj, round, n2);
-          if (ii > jj) { const int tmp = ii; ii = jj; jj = tmp; }
-        }
+        const int ii = e1 < e2 ? e1 : e2, jj = e1 < e2 ? e2 : e1;
+        e1 = rr_next(e1, n2);
+        e2 = rr_next(e2, n2);
         const bool real_pair = act && jj < m;
         Real aa = Real(0), bb = Real(0), gg = Real(0);
         Real* zi = Zb + ii * ld;
@@ -302,17 +332,17 @@ __global__ void __launch_bounds__(kNT) k_procrustes(
           gg += __shfl_xor_sync(0xffffffffu, gg, o);
         }
         if (real_pair && gg != Real(0) && fabs(gg) > tol * sqrt(aa * bb)) {
-          const Real zeta = (bb - aa) / (Real(2) * gg);
+          const Real zeta = fdiv_(bb - aa, Real(2) * gg);
           Real tt;
-          if (fabs(zeta) > Real(1e15)) tt = Real(0.5) / zeta;
-          else tt = (zeta >= Real(0) ? Real(1) : Real(-1)) / (fabs(zeta) + sqrt(Real(1) + zeta * zeta));
+          if (fabs(zeta) > Real(1e15)) tt = fdiv_(Real(0.5), zeta);
+          else tt = fdiv_(zeta >= Real(0) ? Real(1) : Real(-1), fabs(zeta) + sqrt(Real(1) + zeta * zeta));
           const Real c = rsqrt_(Real(1) + tt * tt), s = c * tt;
           for (int t = sl; t < R; t += LP) {
             const Real x = zi[t], y = zj[t];
             zi[t] = c * x - s * y;
             zj[t] = s * x + c * y;
           }
-          if (wide) {
+          if (accU) {
             Real* ui = Ub + ii * ld;
             Real* uj = Ub + jj * ld;
             for (int t = sl; t < m; t += LP) {
@@ -326,9 +356,11 @@ __global__ void __launch_bounds__(kNT) k_procrustes(
         nrot += __syncthreads_count(rotated);
       }
       if (tid == 0)
-        fma += (unsigned long long)(m * (m - 1) / 2) * 3 * R + (unsigned long long)nrot * 4 * (R + (wide ? m : 0));
+        fma += (unsigned long long)(m * (m - 1) / 2) * 3 * R + (unsigned long long)nrot * 4 * (R + (accU ? m : 0));
       if (nrot == 0) break;
     }
+    if (Uk)
+      for (int e = tid; e < m * m; e += kNT) Uk[e] = Ub[(e / m) * ld + (e % m)];
 
     // ---- singular values, rank cut, normalised right singular vectors c_j ----
     for (int j = tid; j < m; j += kNT) {
@@ -394,6 +426,7 @@ __global__ void __launch_bounds__(kNT) k_procrustes(
         }
         Pb[r * ld + t] = acc;
         if (Pi) Pi[k * R * R + e] = pacc;
+        Ub[r * ld + t] = Real(0);
       }
       __syncthreads();
       // pass 2, rows four at a time: q_i = (p_i E) Omega; T_k += q_i^T p_i
@@ -452,7 +485,8 @@ size_t procrustes_smem(int R) {
 template <typename Real>
 copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const Real* H,
                                 const Real* V, const Real* W, double tau, Real* Q, Real* T,
-                                Real* Pi, int32_t* rank, Real* F_H) {
+                                Real* Pi, int32_t* rank, Real* F_H, Real* Uw, const int64_t* woff,
+                                bool warm_in) {
   const size_t smem = procrustes_smem<Real>(R);
   if (R < 1 || R > kNT || smem > 227 * 1024)
     return fail(h, COPA_ERR_UNSUPPORTED, "Procrustes: R too large for shared memory at this precision");
@@ -482,7 +516,8 @@ copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const R
   if ((st = cuda_check(h, cudaMemsetAsync(counter, 0, 16, h->stream), "memset")) != COPA_OK)
     return st;
   k_procrustes<Real><<<(unsigned)blocks, kNT, smem, h->stream>>>(X, R, H, V, W, tau, Q, T, Pi, rank, part,
-                                                                order, counter, fma_count);
+                                                                order, counter, fma_count, Uw, woff,
+                                                                warm_in ? 1 : 0);
   if ((st = cuda_check(h, cudaGetLastError(), "k_procrustes launch")) != COPA_OK) return st;
   if (F_H) {
     k_reduce_partials<Real><<<(R * R + 255) / 256, 256, 0, h->stream>>>(part, (int)blocks, R * R, F_H);
@@ -495,9 +530,11 @@ template size_t procrustes_smem<float>(int);
 template size_t procrustes_smem<double>(int);
 template copa_status_t launch_procrustes<float>(copa_ctx*, const TensorView&, int, const float*,
                                                 const float*, const float*, double, float*,
-                                                float*, float*, int32_t*, float*);
+                                                float*, float*, int32_t*, float*, float*,
+                                                const int64_t*, bool);
 template copa_status_t launch_procrustes<double>(copa_ctx*, const TensorView&, int, const double*,
                                                  const double*, const double*, double, double*,
-                                                 double*, double*, int32_t*, double*);
+                                                 double*, double*, int32_t*, double*, double*,
+                                                 const int64_t*, bool);
 
 }  // namespace copa

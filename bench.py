@@ -229,13 +229,15 @@ def gpu_leg(args, X, init, rank, world):
     e1.record(h.stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    launches = h.fit_launches()
     clocks = clk.stop()
     if world > 1:
         t = torch.tensor([ms], device=h.device)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
         torch.distributed.barrier()
-    out = {"ms_total": ms, "fit_last": float(hist[-1]), "fit_hist": [float(x) for x in hist], "clocks": clocks}
+    out = {"ms_total": ms, "fit_last": float(hist[-1]), "fit_hist": [float(x) for x in hist], "clocks": clocks,
+           "launches": launches}
     if rank == 0:
         out["breakdown_ms"] = kernel_breakdown(h, P, Xd, R, H, V, W)
         out["proc_ms"], out["roofline"] = procrustes_roofline(h, P, Xd, X, R, H, V, W, PEAKS)
@@ -315,12 +317,11 @@ def main():
         return
     ms_step = res["ms_total"] / args.steps
     value = world * 1000.0 / ms_step
-    kernels_per_iter = 20
     line = dict(base, value=value, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms_step, scaling="weak", vs_baseline=None,
                 dtype="f32 bulk (bf16 counts), f64 Gram/eigen/Cholesky/FIT" if args.precision == "mixed" else "f64",
                 roofline=res["roofline"], clocks=res["clocks"],
-                gpu_launches=kernels_per_iter * args.steps + 1,
+                gpu_launches=res["launches"],
                 fit_last=res["fit_last"], sparsity_V=res["sparsity_V"], breakdown_ms=res["breakdown_ms"],
                 generation_s=gen_s)
     line["config"]["parallelism"] = "replicas x%d (subjects per replica fixed)" % world if world > 1 else "1 GPU"

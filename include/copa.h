@@ -131,6 +131,11 @@ copa_status_t copa_procrustes(copa_handle_t handle, const copa_tensor_t* X, int3
  * figure of the benchmark). Synchronises; writes 0 before the first launch. */
 copa_status_t copa_procrustes_work(copa_handle_t handle, double* fma_host);
 
+/* Diagnostic (no counterpart in the paper): the number of kernels the last copa_fit call
+ * on this handle launched (the kernel nodes of the captured iteration graph times n_outer,
+ * plus set-up kernels), or -1 if unknown (use_graph = 0). */
+copa_status_t copa_fit_launches(copa_handle_t handle, int64_t* launches_host);
+
 /* (c) The MTTKRPs of Y = {Q_k^T X_k} (Sec. 2, Algorithm 1 "F = Y_(n)(Khatri-Rao)"),
  * from the Procrustes output `st` (computed with some V_p; T_k = Q_k^T X_k V_p):
  *   COPA_MODE_H: F (R x R) = sum_k T_k diag(W(k,:))               uses st->T, W

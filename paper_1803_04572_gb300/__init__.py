@@ -31,7 +31,8 @@ MODE = {"H": 0, "V": 1, "W": 2}
 EXPORTED = ["copa_create", "copa_destroy", "copa_last_error", "copa_sync", "copa_validate",
             "copa_procrustes", "copa_mttkrp", "copa_gram", "copa_admm_step", "copa_admm_w_fused",
             "copa_fit_value", "copa_fit", "copa_fit_host", "copa_smooth_plan",
-            "copa_smooth_project", "copa_loss_grad", "copa_procrustes_work", "copa_gram_noalloc"]
+            "copa_smooth_project", "copa_loss_grad", "copa_procrustes_work", "copa_gram_noalloc",
+            "copa_fit_launches"]
 
 
 class CopaError(RuntimeError):
@@ -80,6 +81,7 @@ _sig = {
                        _V],
     "copa_procrustes_work": [_V, POINTER(c_double)],
     "copa_gram_noalloc": [_V, c_int32, _V, c_int64, c_int32, _V],
+    "copa_fit_launches": [_V, POINTER(c_int64)],
 }
 for _n, _a in _sig.items():
     getattr(_lib, _n).argtypes = _a
@@ -299,6 +301,12 @@ class Copa:
         self._call(_lib.copa_smooth_project, self.h, byref(X.c()), _ptr(days), n_basis, degree, byref(xc),
                                              _ptr(C))
         return Xp, C
+
+    def fit_launches(self) -> int:
+        """Kernels launched by the last fit() (graph nodes x iterations + set-up), -1 if unknown."""
+        v = c_int64()
+        self._call(_lib.copa_fit_launches, self.h, byref(v))
+        return v.value
 
     def procrustes_work(self) -> float:
         """Multiply-adds performed by the last procrustes() launch (counted on the device)."""

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "copa_internal.cuh"
 
@@ -184,6 +185,7 @@ copa_status_t get_schedule(copa_ctx* h, const TensorView& X, const int64_t** ord
     k_sched_scan<<<1, 32, 0, h->stream>>>(tmp, tmp + kBuckets);
     k_sched_scatter<<<blocks, 256, 0, h->stream>>>(X.subj_ptr, X.K, tmp + kBuckets, tmp, ord);
     if ((st = cuda_check(h, cudaGetLastError(), "schedule kernels")) != COPA_OK) return st;
+    h->setup_launches += 3;
   }
   h->sched_key = X.subj_ptr;
   h->sched_K = X.K;
@@ -206,6 +208,7 @@ copa_status_t get_warm_offsets(copa_ctx* h, const TensorView& X, int R, const in
   k_warm_sizes<<<blocks, 256, 0, h->stream>>>(X.subj_ptr, X.K, R, off);
   k_scan_inplace<<<1, 1024, 0, h->stream>>>(off, X.K);
   if ((st = cuda_check(h, cudaGetLastError(), "warm offsets")) != COPA_OK) return st;
+  h->setup_launches += 2;
   int64_t tot = 0;
   if ((st = cuda_check(h, cudaMemcpyAsync(&tot, off + X.K, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream),
                        "D2H")) != COPA_OK)
@@ -234,6 +237,7 @@ copa_status_t launch_xnorm2(copa_ctx* h, const TensorView& X, double* out) {
   if ((st = cuda_check(h, cudaMemsetAsync(out, 0, sizeof(double), h->stream), "memset")) != COPA_OK) return st;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((X.nnz + 255) / 256, (int64_t)h->num_sms * 4));
   k_xnorm2<<<blocks, 256, 0, h->stream>>>(X, out);
+  h->setup_launches += 1;
   return cuda_check(h, cudaGetLastError(), "k_xnorm2");
 }
 
@@ -359,6 +363,13 @@ copa_status_t copa_procrustes(copa_handle_t h, const copa_tensor_t* X, int32_t R
   return launch_procrustes<double>(h, v, R, (const double*)H, (const double*)V, (const double*)W, tau,
                                    (double*)out->Q, (double*)out->T, (double*)out->Pi, out->rank,
                                    (double*)F_H);
+}
+
+copa_status_t copa_fit_launches(copa_handle_t h, int64_t* launches_host) {
+  CHECK_H(h);
+  if (!launches_host) return fail(h, COPA_ERR_INVALID_ARG, "copa_fit_launches: NULL output");
+  *launches_host = h->fit_launches;
+  return COPA_OK;
 }
 
 copa_status_t copa_procrustes_work(copa_handle_t h, double* fma_host) {
@@ -512,7 +523,8 @@ struct FitBufs {
 
 template <typename Real>
 copa_status_t one_iteration(copa_ctx* h, const TensorView& X, const copa_options_t* o, Real* H, Real* V,
-                            Real* W, Real* DH, Real* DV, Real* DW, const FitBufs<Real>& b, bool warm_in) {
+                            Real* W, Real* DH, Real* DV, Real* DW, const FitBufs<Real>& b, bool warm_in,
+                            bool first) {
   const int R = o->R;
   // (a)+(b) Procrustes, with the H-mode MTTKRP fused
   TRY(launch_procrustes<Real>(h, X, R, H, V, W, o->tau, b.Q, b.T, b.Pi, b.rank, b.FH, b.Uw, b.woff, warm_in));
@@ -527,7 +539,7 @@ copa_status_t one_iteration(copa_ctx* h, const TensorView& X, const copa_options
   TRY(launch_admm_w<Real>(h, b.T, H, b.Ginv, b.rho + 1, o->n_inner, o->c_W, o->lam_W, W, DW, X.K, R));
   // V: G = H^T H .* W^T W; F_V = sum_k X_k^T Q_k H S_k
   TRY(launch_gram<Real>(h, W, X.K, R, b.gW));
-  TRY(launch_mttkrp_v<Real>(h, X, R, b.Q, H, W, b.FV, b.UtU));
+  TRY(launch_mttkrp_v<Real>(h, X, R, b.Q, H, W, b.FV, b.UtU, /*reuse_csc=*/!first));
   TRY(launch_chol<Real>(h, b.gH, b.gW, R, b.Ginv, b.rho + 2));
   TRY(launch_admm_rows<Real>(h, b.FV, b.Ginv, b.rho + 2, o->n_inner, o->c_V, o->lam_V, V, DV, X.J, R));
   // FIT of (Q_k, H, W, V) after the iteration
@@ -576,6 +588,9 @@ copa_status_t fit_impl(copa_ctx* h, const copa_tensor_t* Xc, const copa_options_
   b.FH = (Real*)take(sizeof(Real) * R * R);
   b.FV = (Real*)take(sizeof(Real) * (size_t)X.J * R);
   b.Ginv = (Real*)take(sizeof(Real) * R * (R + 1));
+  h->fit_launches = -1;
+  h->setup_launches = 0;
+  int64_t per_iter = -1;
   TRY(cuda_check(h, cudaMemsetAsync(b.it, 0, sizeof(int), h->stream), "memset"));
   TRY(launch_xnorm2(h, X, b.xn2));
   {
@@ -585,7 +600,7 @@ copa_status_t fit_impl(copa_ctx* h, const copa_tensor_t* Xc, const copa_options_
   }
   if (o->n_outer > 0) {
     // the first iteration runs eagerly: it sizes every workspace buffer
-    TRY(one_iteration<Real>(h, X, o, H, V, W, DH, DV, DW, b, h->warm_valid && h->warm_prec == h->precision));
+    TRY(one_iteration<Real>(h, X, o, H, V, W, DH, DV, DW, b, h->warm_valid && h->warm_prec == h->precision, true));
     h->warm_valid = true;
     h->warm_prec = h->precision;
   }
@@ -598,7 +613,7 @@ copa_status_t fit_impl(copa_ctx* h, const copa_tensor_t* Xc, const copa_options_
       TRY(cuda_check(h, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "cudaStreamCreate"));
       h->stream = cap;
       cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
-      copa_status_t cs = ce == cudaSuccess ? one_iteration<Real>(h, X, o, H, V, W, DH, DV, DW, b, true) : COPA_OK;
+      copa_status_t cs = ce == cudaSuccess ? one_iteration<Real>(h, X, o, H, V, W, DH, DV, DW, b, true, false) : COPA_OK;
       if (ce == cudaSuccess) ce = cudaStreamEndCapture(cap, &graph);
       h->stream = orig;
       cudaStreamDestroy(cap);
@@ -607,6 +622,19 @@ copa_status_t fit_impl(copa_ctx* h, const copa_tensor_t* Xc, const copa_options_
         return cs;
       }
       TRY(cuda_check(h, ce, "EndCapture"));
+      {
+        size_t nn = 0;
+        if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn > 0) {
+          std::vector<cudaGraphNode_t> nodes(nn);
+          if (cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess) {
+            per_iter = 0;
+            for (size_t q = 0; q < nn; ++q) {
+              cudaGraphNodeType ty;
+              if (cudaGraphNodeGetType(nodes[q], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++per_iter;
+            }
+          }
+        }
+      }
       cudaGraphExec_t exec = nullptr;
       ce = cudaGraphInstantiate(&exec, graph, 0);
       cudaGraphDestroy(graph);
@@ -618,10 +646,11 @@ copa_status_t fit_impl(copa_ctx* h, const copa_tensor_t* Xc, const copa_options_
       cudaGraphExecDestroy(exec);
       TRY(cuda_check(h, ce, "GraphLaunch"));
     } else {
-      for (int it = 1; it < o->n_outer; ++it) TRY(one_iteration<Real>(h, X, o, H, V, W, DH, DV, DW, b, true));
+      for (int it = 1; it < o->n_outer; ++it) TRY(one_iteration<Real>(h, X, o, H, V, W, DH, DV, DW, b, true, false));
     }
   }
   TRY(sync_status(h));
+  if (per_iter >= 0) h->fit_launches = h->setup_launches + per_iter * o->n_outer;
   if (hist_host && o->n_outer > 0)
     TRY(cuda_check(h, cudaMemcpy(hist_host, b.hist, sizeof(double) * o->n_outer, cudaMemcpyDeviceToHost),
                    "history D2H"));

@@ -127,6 +127,13 @@ struct copa_ctx {
   int warm_R = 0;
   int warm_prec = -1;
   bool warm_valid = false;   // the buffer holds the rotations of a finished iteration
+  // kernels launched by the last copa_fit call (graph nodes x iterations + set-up), -1 unknown
+  int64_t fit_launches = -1;
+  int64_t setup_launches = 0;
+  // cached column-sorted copy of X
+  const int32_t* csc_key = nullptr;
+  int64_t csc_nnz = -1;
+  int csc_J = 0, csc_prec = -1;
 };
 
 namespace copa {
@@ -145,6 +152,8 @@ enum Slot {
   SLOT_PI = 10,
   SLOT_WARM = 11,      // copa_fit: per-subject Jacobi rotations kept between iterations
   SLOT_WARM_OFF = 12,  // int64[K+1] offsets of the min(I_k,R)^2 blocks
+  SLOT_CSC = 13,       // column-sorted copy of X (pointers, row indices, values)
+  SLOT_UVEC = 14,      // u_i = q_i H S_k for every visit row (S x R)
 };
 copa_status_t get_warm_offsets(copa_ctx* h, const TensorView& X, int R, const int64_t** woff,
                                int64_t* total);
@@ -169,7 +178,8 @@ copa_status_t launch_mttkrp_h(copa_ctx* h, int64_t K, int R, const Real* T, cons
                               Real* F);
 template <typename Real>
 copa_status_t launch_mttkrp_v(copa_ctx* h, const TensorView& X, int R, const Real* Q,
-                              const Real* H, const Real* W, Real* F, double* UtU);
+                              const Real* H, const Real* W, Real* F, double* UtU,
+                              bool reuse_csc = false);
 template <typename Real>
 copa_status_t launch_mttkrp_w(copa_ctx* h, int64_t K, int R, const Real* T, const Real* H,
                               Real* F);

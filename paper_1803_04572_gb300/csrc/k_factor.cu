@@ -6,8 +6,8 @@
 //   F_H = sum_k Y_k V S_k        = sum_k T_k S_k
 //   F_W(k,s) = (H^T Y_k V)(s,s)  = sum_r H(r,s) T_k(r,s)
 //   F_V = sum_k Y_k^T H S_k      = sum_k X_k^T (Q_k H S_k)
-// so only F_V streams X again; it scatters x_ij * u_i into F_V(j,:) with
-// u_i = q_i H S_k, and accumulates U^T U = sum_i u_i^T u_i.
+// so only F_V streams X again: u_i = q_i H S_k for every visit, then F_V = X^T U over a
+// column-sorted copy of X; U^T U = sum_i u_i^T u_i comes with the first step.
 #include <mutex>
 
 #include "copa_internal.cuh"
@@ -64,36 +64,48 @@ __global__ void k_mttkrp_w(int64_t K, int R, const Real* __restrict__ T,
 }
 
 // ------------------------------------------------------------------------------------
-// F_V = sum_k X_k^T Q_k H S_k and U^T U (warp per subject, persistent, largest first):
-// u_i = q_i N_k with N_k = H S_k, F_V(j,:) += x_ij u_i, U^T U += u_i^T u_i
+// F_V as a gather: F_V = sum_k X_k^T U_k with U_k = Q_k H S_k.
+//  1. k_uvec: u_i = q_i H S_k for every visit row (warp per subject, largest first),
+//     written to U (S x R); U^T U = sum_i u_i^T u_i accumulated in registers, each lane
+//     owning a 5 x 10 tile of the R x R result (R <= 40; packed shared-memory sums above).
+//  2. k_spmm_csc: F_V(j,:) = sum_{i in column j} x_ij u_i over a column-sorted copy of X
+//     (built once per tensor); each warp takes a fixed chunk of nonzeros, so hot
+//     columns are split evenly, and flushes one atomic add per (chunk, column).
 // ------------------------------------------------------------------------------------
-template <typename Real>
-__global__ void __launch_bounds__(128) k_mttkrp_v(
+constexpr int kTR = 5, kTC = 10;   // U^T U register tile per lane (8 x 4 tiles cover 40 x 40)
+constexpr int kUNT = 256;          // threads per block of k_uvec
+constexpr int kChunk = 256;        // nonzeros per warp in k_spmm_csc
+
+template <typename Real, bool kTiles>
+__global__ void __launch_bounds__(kUNT) k_uvec(
     TensorView X, int R, const Real* __restrict__ Q, const Real* __restrict__ H,
-    const Real* __restrict__ W, Real* __restrict__ F, double* __restrict__ utu_part,
+    const Real* __restrict__ W, Real* __restrict__ U, double* __restrict__ utu_part,
     const int64_t* __restrict__ order, int* __restrict__ counter) {
   extern __shared__ unsigned char smem_raw[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const int ldr = R + 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int nw = kUNT / 32;
   const int npk = R * (R + 1) / 2;
-  Real* Hs = reinterpret_cast<Real*>(smem_raw);                    // R x R
-  Real* base = Hs + R * R + (size_t)warp * (R * ldr + 3 * R + npk);
-  Real* N = base;              // R x ldr
-  Real* qv = N + R * ldr;      // R
-  Real* uv = qv + R;           // R
-  Real* wv = uv + R;           // R
-  Real* uacc = wv + R;         // npk: this subject's U^T U (packed upper triangle)
-  uint16_t* pk = reinterpret_cast<uint16_t*>(Hs + R * R + (size_t)nwarps * (R * ldr + 3 * R + npk));
-  double* up = utu_part ? utu_part + (size_t)(blockIdx.x * nwarps + warp) * npk : nullptr;
-  for (int i = threadIdx.x; i < R * R; i += blockDim.x) Hs[i] = H[i];
-  for (int e = threadIdx.x; e < npk; e += blockDim.x) {
-    int r = 0, rem = e;
-    while (rem >= R - r) { rem -= R - r; ++r; }
-    pk[e] = (uint16_t)((r << 8) | (r + rem));
+  Real* Hs = reinterpret_cast<Real*>(smem_raw);                      // R x R
+  Real* wv = Hs + R * R + (size_t)warp * (2 * R + (kTiles ? 0 : npk));
+  Real* uv = wv + R;
+  Real* uacc = uv + R;                                               // packed U^T U (no tiles)
+  uint16_t* pk = reinterpret_cast<uint16_t*>(Hs + R * R + (size_t)nw * (2 * R + (kTiles ? 0 : npk)));
+  for (int e = threadIdx.x; e < R * R; e += kUNT) Hs[e] = H[e];
+  if (!kTiles) {
+    for (int e = threadIdx.x; e < npk; e += kUNT) {
+      int r = 0, rem = e;
+      while (rem >= R - r) { rem -= R - r; ++r; }
+      pk[e] = (uint16_t)((r << 8) | (r + rem));
+    }
+    for (int e = lane; e < npk; e += 32) uacc[e] = Real(0);
   }
-  if (up)
-    for (int e = lane; e < npk; e += 32) { up[e] = 0.0; uacc[e] = Real(0); }
   __syncthreads();
+  const int tr = lane >> 2, tc = lane & 3;
+  Real acc[kTiles ? kTR : 1][kTiles ? kTC : 1];
+#pragma unroll
+  for (int a = 0; a < (kTiles ? kTR : 1); ++a)
+#pragma unroll
+    for (int b = 0; b < (kTiles ? kTC : 1); ++b) acc[a][b] = Real(0);
 
   while (true) {
     int idx = 0;
@@ -102,49 +114,141 @@ __global__ void __launch_bounds__(128) k_mttkrp_v(
     if (idx >= X.K) break;
     const int64_t k = order ? order[idx] : idx;
     const int64_t r0 = X.subj_ptr[k], r1 = X.subj_ptr[k + 1];
-    if (r0 == r1) continue;
     for (int s = lane; s < R; s += 32) wv[s] = W[k * R + s];
     __syncwarp();
-    for (int e = lane; e < R * R; e += 32) {
-      const int r = e / R, s = e - r * R;
-      N[r * ldr + s] = Hs[e] * wv[s];
-    }
-    __syncwarp();
     for (int64_t i = r0; i < r1; ++i) {
-      const int64_t a = X.row_ptr[i], b = X.row_ptr[i + 1];
-      for (int r = lane; r < R; r += 32) qv[r] = Q[i * R + r];
-      __syncwarp();
-      Real u[kRegs];
-#pragma unroll
-      for (int q = 0; q < kRegs; ++q) {
-        const int s = lane + 32 * q;
-        Real acc = Real(0);
-        if (s < R)
-          for (int r = 0; r < R; ++r) acc += qv[r] * N[r * ldr + s];
-        u[q] = acc;
-        if (s < R) uv[s] = acc;
-      }
-      for (int64_t t = a; t < b; ++t) {
-        const Real x = load_x<Real>(X, t);
-        const int64_t j = __ldg(X.col + t);
-#pragma unroll
-        for (int q = 0; q < kRegs; ++q) {
-          const int s = lane + 32 * q;
-          if (s < R) atomicAdd(F + j * R + s, x * u[q]);
+      const Real* qi = Q + i * R;
+      for (int s = lane; s < R; s += 32) {
+        Real a0 = Real(0), a1 = Real(0);
+        int r = 0;
+        for (; r + 1 < R; r += 2) {
+          a0 += __ldg(qi + r) * Hs[r * R + s];
+          a1 += __ldg(qi + r + 1) * Hs[(r + 1) * R + s];
         }
+        if (r < R) a0 += __ldg(qi + r) * Hs[r * R + s];
+        const Real u = (a0 + a1) * wv[s];
+        uv[s] = u;
+        U[i * R + s] = u;
       }
       __syncwarp();
-      if (up) {
-        for (int e = lane; e < npk; e += 32) {
-          const int r = pk[e] >> 8, s = pk[e] & 255;
-          uacc[e] += uv[r] * uv[s];
+      if (utu_part) {
+        if (kTiles) {
+#pragma unroll
+          for (int aa = 0; aa < kTR; ++aa) {
+            const int r = tr * kTR + aa;
+            const Real ur = r < R ? uv[r] : Real(0);
+#pragma unroll
+            for (int bb = 0; bb < kTC; ++bb) {
+              const int s = tc * kTC + bb;
+              if (s < R) acc[aa][bb] += ur * uv[s];
+            }
+          }
+        } else {
+          for (int e = lane; e < npk; e += 32) {
+            const int r = pk[e] >> 8, s = pk[e] & 255;
+            uacc[e] += uv[r] * uv[s];
+          }
         }
       }
       __syncwarp();
     }
-    if (up)
-      for (int e = lane; e < npk; e += 32) { up[e] += (double)uacc[e]; uacc[e] = Real(0); }
-    __syncwarp();
+  }
+  if (utu_part) {
+    double* up = utu_part + ((size_t)blockIdx.x * nw + warp) * R * R;
+    if (kTiles) {
+#pragma unroll
+      for (int aa = 0; aa < kTR; ++aa)
+#pragma unroll
+        for (int bb = 0; bb < kTC; ++bb) {
+          const int r = tr * kTR + aa, s = tc * kTC + bb;
+          if (r < R && s < R) up[r * R + s] = (double)acc[aa][bb];
+        }
+    } else {
+      for (int e = lane; e < npk; e += 32) {
+        const int r = pk[e] >> 8, s = pk[e] & 255;
+        up[r * R + s] = (double)uacc[e];
+        if (r != s) up[s * R + r] = (double)uacc[e];
+      }
+    }
+  }
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(256) k_spmm_csc(int64_t nnz, int J, int R, const int64_t* __restrict__ cptr,
+                                                  const int32_t* __restrict__ crow, const Real* __restrict__ cval,
+                                                  const Real* __restrict__ U, Real* __restrict__ F) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nchunks = (nnz + kChunk - 1) / kChunk;
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwt = (gridDim.x * (int64_t)blockDim.x) >> 5;
+  for (int64_t c = wid; c < nchunks; c += nwt) {
+    const int64_t e0 = c * kChunk, e1 = min(nnz, e0 + kChunk);
+    // column holding e0: last j with cptr[j] <= e0
+    int lo = 0, hi = J;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (cptr[mid] <= e0) lo = mid; else hi = mid;
+    }
+    int j = lo;
+    int64_t jend = cptr[j + 1];
+    Real a0 = Real(0), a1 = Real(0), a2 = Real(0);
+    for (int64_t b0 = e0; b0 < e1; b0 += 32) {
+      const int n = (int)min((int64_t)32, e1 - b0);
+      int row = 0;
+      Real x = Real(0);
+      if (lane < n) {
+        row = __ldg(crow + b0 + lane);
+        x = __ldg(cval + b0 + lane);
+      }
+      for (int q = 0; q < n; ++q) {
+        const int64_t e = b0 + q;
+        while (e >= jend) {   // column boundary: flush and move on
+          if (a0 != Real(0) && lane < R) atomicAdd(F + (int64_t)j * R + lane, a0);
+          if (a1 != Real(0) && lane + 32 < R) atomicAdd(F + (int64_t)j * R + lane + 32, a1);
+          if (a2 != Real(0) && lane + 64 < R) atomicAdd(F + (int64_t)j * R + lane + 64, a2);
+          a0 = a1 = a2 = Real(0);
+          ++j;
+          jend = cptr[j + 1];
+        }
+        const int rq = __shfl_sync(0xffffffffu, row, q);
+        const Real xq = __shfl_sync(0xffffffffu, x, q);
+        const Real* ur = U + (int64_t)rq * R;
+        if (lane < R) a0 += xq * __ldg(ur + lane);
+        if (lane + 32 < R) a1 += xq * __ldg(ur + lane + 32);
+        if (lane + 64 < R) a2 += xq * __ldg(ur + lane + 64);
+      }
+    }
+    if (a0 != Real(0) && lane < R) atomicAdd(F + (int64_t)j * R + lane, a0);
+    if (a1 != Real(0) && lane + 32 < R) atomicAdd(F + (int64_t)j * R + lane + 32, a1);
+    if (a2 != Real(0) && lane + 64 < R) atomicAdd(F + (int64_t)j * R + lane + 64, a2);
+  }
+}
+
+// column-sorted copy of X: histogram of columns, exclusive scan, scatter (row index and
+// value of every nonzero; the order inside a column is arbitrary)
+__global__ void k_csc_hist(TensorView X, int64_t* __restrict__ cnt) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < X.nnz; t += gridDim.x * (int64_t)blockDim.x)
+    atomicAdd(reinterpret_cast<unsigned long long*>(cnt + X.col[t]), 1ull);
+}
+
+template <typename Real>
+__global__ void k_csc_scatter(TensorView X, const int64_t* __restrict__ cptr, int64_t* __restrict__ cur,
+                              int32_t* __restrict__ crow, Real* __restrict__ cval) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < X.S; i += gridDim.x * (int64_t)blockDim.x) {
+    for (int64_t t = X.row_ptr[i]; t < X.row_ptr[i + 1]; ++t) {
+      const int c = X.col[t];
+      const int64_t pos = cptr[c] + (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(cur + c), 1ull);
+      crow[pos] = (int32_t)i;
+      cval[pos] = load_x<Real>(X, t);
+    }
+  }
+}
+
+__global__ void k_scan_cols(int64_t* __restrict__ v, int n) {
+  if (threadIdx.x == 0) {
+    int64_t acc = 0;
+    for (int j = 0; j < n; ++j) { const int64_t x = v[j]; v[j] = acc; acc += x; }
+    v[n] = acc;
   }
 }
 
@@ -441,49 +545,96 @@ copa_status_t launch_mttkrp_w(copa_ctx* h, int64_t K, int R, const Real* T, cons
   return cuda_check(h, cudaGetLastError(), "k_mttkrp_w");
 }
 
+// The column-sorted copy is rebuilt unless `reuse` (copa_fit builds it once per call and
+// reuses it for the later iterations of the same call, where X cannot change).
+template <typename Real>
+static copa_status_t get_csc(copa_ctx* h, const TensorView& X, bool reuse, const int64_t** cptr,
+                             const int32_t** crow, const Real** cval) {
+  copa_status_t st;
+  const int prec = sizeof(Real) == 8 ? 1 : 0;
+  if (!(reuse && h->csc_key == X.col && h->csc_nnz == X.nnz && h->csc_J == X.J && h->csc_prec == prec &&
+        h->slot_ptr[SLOT_CSC])) {
+    const size_t bytes = sizeof(int64_t) * 2 * ((size_t)X.J + 1) + sizeof(int32_t) * (size_t)X.nnz +
+                         sizeof(Real) * (size_t)X.nnz + 256;
+    char* p = nullptr;
+    if ((st = ws_get(h, SLOT_CSC, bytes, (void**)&p)) != COPA_OK) return st;
+    int64_t* ptr = reinterpret_cast<int64_t*>(p);
+    int64_t* cur = ptr + X.J + 1;
+    int32_t* rows = reinterpret_cast<int32_t*>(cur + X.J + 1);
+    Real* vals = reinterpret_cast<Real*>((reinterpret_cast<uintptr_t>(rows + X.nnz) + 15) & ~uintptr_t(15));
+    if ((st = cuda_check(h, cudaMemsetAsync(ptr, 0, sizeof(int64_t) * 2 * ((size_t)X.J + 1), h->stream),
+                         "memset")) != COPA_OK)
+      return st;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((X.nnz + 255) / 256, (int64_t)h->num_sms * 16));
+    k_csc_hist<<<blocks, 256, 0, h->stream>>>(X, ptr);
+    k_scan_cols<<<1, 32, 0, h->stream>>>(ptr, X.J);
+    const int rblocks = (int)std::max<int64_t>(1, std::min<int64_t>((X.S + 255) / 256, (int64_t)h->num_sms * 16));
+    k_csc_scatter<Real><<<rblocks, 256, 0, h->stream>>>(X, ptr, cur, rows, vals);
+    if ((st = cuda_check(h, cudaGetLastError(), "csc build")) != COPA_OK) return st;
+    h->setup_launches += 3;
+    h->csc_key = X.col;
+    h->csc_nnz = X.nnz;
+    h->csc_J = X.J;
+    h->csc_prec = prec;
+  }
+  char* p = reinterpret_cast<char*>(h->slot_ptr[SLOT_CSC]);
+  const int64_t* ptr = reinterpret_cast<const int64_t*>(p);
+  const int32_t* rows = reinterpret_cast<const int32_t*>(ptr + 2 * ((size_t)X.J + 1));
+  *cptr = ptr;
+  *crow = rows;
+  *cval = reinterpret_cast<const Real*>((reinterpret_cast<uintptr_t>(rows + X.nnz) + 15) & ~uintptr_t(15));
+  return COPA_OK;
+}
+
 template <typename Real>
 copa_status_t launch_mttkrp_v(copa_ctx* h, const TensorView& X, int R, const Real* Q, const Real* H,
-                              const Real* W, Real* F, double* UtU) {
+                              const Real* W, Real* F, double* UtU, bool reuse_csc) {
   if (R > kMaxR) return fail(h, COPA_ERR_UNSUPPORTED, "mttkrp V: R too large");
   copa_status_t st;
-  const int npk0 = R * (R + 1) / 2;
-  const size_t per_warp = sizeof(Real) * ((size_t)R * (R + 1) + 3 * (size_t)R + npk0);
-  const size_t fixed = sizeof(Real) * (size_t)R * R + sizeof(uint16_t) * npk0 + 64;
-  int warps = 4;
-  while (warps > 1 && fixed + warps * per_warp > 200 * 1024) --warps;
-  const size_t smem = fixed + warps * per_warp;
-  if ((st = cuda_check(h, cudaFuncSetAttribute(k_mttkrp_v<Real>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem), "cudaFuncSetAttribute")) != COPA_OK)
-    return st;
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mttkrp_v<Real>, 32 * warps, smem);
-  if (per_sm < 1) per_sm = 1;
-  int64_t blocks = (int64_t)h->num_sms * per_sm;
-  const int64_t need = (X.K + warps - 1) / warps;
-  if (blocks > need) blocks = need > 0 ? need : 1;
   const int64_t* order = nullptr;
   if ((st = get_schedule(h, X, &order)) != COPA_OK) return st;
+  const int64_t* cptr = nullptr;
+  const int32_t* crow = nullptr;
+  const Real* cval = nullptr;
+  if ((st = get_csc<Real>(h, X, reuse_csc, &cptr, &crow, &cval)) != COPA_OK) return st;
+  Real* U = nullptr;
+  if ((st = ws_get(h, SLOT_UVEC, sizeof(Real) * ((size_t)X.S * R + 16), (void**)&U)) != COPA_OK) return st;
   int* counter = nullptr;
   if ((st = ws_get(h, SLOT_COUNTER, 64, (void**)&counter)) != COPA_OK) return st;
-  const int npk = R * (R + 1) / 2;
-  double* part = nullptr;
-  const int nparts = (int)blocks * warps;
-  if (UtU) {
-    if ((st = ws_get(h, SLOT_PARTIAL, (size_t)nparts * npk * sizeof(double), (void**)&part)) != COPA_OK)
-      return st;
-  }
   if ((st = cuda_check(h, cudaMemsetAsync(counter + 1, 0, sizeof(int), h->stream), "memset")) != COPA_OK)
     return st;
   if ((st = cuda_check(h, cudaMemsetAsync(F, 0, sizeof(Real) * (size_t)X.J * R, h->stream), "memset F")) != COPA_OK)
     return st;
-  k_mttkrp_v<Real><<<(unsigned)blocks, 32 * warps, smem, h->stream>>>(X, R, Q, H, W, F, part, order,
-                                                                         counter + 1);
-  if ((st = cuda_check(h, cudaGetLastError(), "k_mttkrp_v")) != COPA_OK) return st;
+  const bool tiles = R <= kTR * 8;
+  const int nw = kUNT / 32;
+  const int npk = R * (R + 1) / 2;
+  const size_t smem = sizeof(Real) * ((size_t)R * R + (size_t)nw * (2 * R + (tiles ? 0 : npk))) +
+                      (tiles ? 0 : sizeof(uint16_t) * npk) + 64;
+  auto kern = tiles ? k_uvec<Real, true> : k_uvec<Real, false>;
+  if ((st = cuda_check(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                       "cudaFuncSetAttribute")) != COPA_OK)
+    return st;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kUNT, smem);
+  if (per_sm < 1) per_sm = 1;
+  int64_t blocks = (int64_t)h->num_sms * per_sm;
+  const int64_t need = (X.K + nw - 1) / nw;
+  if (blocks > need) blocks = need > 0 ? need : 1;
+  double* part = nullptr;
+  const int nparts = (int)blocks * nw;
   if (UtU) {
-    // packed partials -> full symmetric UtU
-    k_unpack_sym_sum<<<(R * R + 255) / 256, 256, 0, h->stream>>>(part, nparts, R, UtU);
-    if ((st = cuda_check(h, cudaGetLastError(), "k_unpack_sym_sum")) != COPA_OK) return st;
+    if ((st = ws_get(h, SLOT_PARTIAL, (size_t)nparts * R * R * sizeof(double), (void**)&part)) != COPA_OK)
+      return st;
+  }
+  kern<<<(unsigned)blocks, kUNT, smem, h->stream>>>(X, R, Q, H, W, U, part, order, counter + 1);
+  if ((st = cuda_check(h, cudaGetLastError(), "k_uvec")) != COPA_OK) return st;
+  const int64_t nchunks = (X.nnz + kChunk - 1) / kChunk;
+  const int sblocks = (int)std::max<int64_t>(1, std::min<int64_t>((nchunks + 7) / 8, (int64_t)h->num_sms * 16));
+  k_spmm_csc<Real><<<sblocks, 256, 0, h->stream>>>(X.nnz, X.J, R, cptr, crow, cval, U, F);
+  if ((st = cuda_check(h, cudaGetLastError(), "k_spmm_csc")) != COPA_OK) return st;
+  if (UtU) {
+    k_reduce_rows<double><<<(R * R + 255) / 256, 256, 0, h->stream>>>(part, nparts, R * R, UtU);
+    if ((st = cuda_check(h, cudaGetLastError(), "UtU reduce")) != COPA_OK) return st;
   }
   return COPA_OK;
 }
@@ -557,7 +708,7 @@ copa_status_t launch_fit_value(copa_ctx* h, int64_t J, int R, const Real* V, con
   template copa_status_t launch_mttkrp_w<Real>(copa_ctx*, int64_t, int, const Real*, const Real*, \
                                                Real*);                                            \
   template copa_status_t launch_mttkrp_v<Real>(copa_ctx*, const TensorView&, int, const Real*,    \
-                                               const Real*, const Real*, Real*, double*);         \
+                                               const Real*, const Real*, Real*, double*, bool);   \
   template copa_status_t launch_gram<Real>(copa_ctx*, const Real*, int64_t, int, double*);        \
   template copa_status_t launch_chol<Real>(copa_ctx*, const double*, const double*, int, Real*,   \
                                            double*);                                              \

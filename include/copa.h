@@ -5,11 +5,11 @@
  * Model (Sec. 2 "Original PARAFAC2 model", Sec. 3.1): every subject k holds a sparse
  * I_k x J slice X_k ~ Q_k H S_k V^T with S_k = diag(W(k,:)), Q_k^T Q_k = I. One outer
  * iteration of Algorithm 1 is
- *   (a) the Procrustes step Q_k = polar(X_k V S_k H^T) (Eq. solv_Q),
+ *   (a) the Procrustes step Q_k = polar(X_k V S_k H^T) (Eq. 5),
  *   (b) the projection Y_k = Q_k^T X_k,
  *   (c) the MTTKRPs of Y for H, W and V,
  *   (d) per factor an ADMM inner loop with a cached Cholesky of G + rho I, a proximal
- *       operator and the dual update (Eq. Solve_W update rules, Sec. 3.3).
+ *       operator and the dual update (Eq. 8 update rules, Sec. 3.3).
  *
  * Conventions shared by every call
  *   - All array pointers are DEVICE pointers unless a name ends in _host. They are
@@ -112,7 +112,7 @@ copa_status_t copa_sync(copa_handle_t handle);
  * Returns COPA_ERR_INVALID_ARG with a message naming the first violation. */
 copa_status_t copa_validate(copa_handle_t handle, const copa_tensor_t* X);
 
-/* (a)+(b), Eq. solv_Q and Algorithm 1's per-subject loop, for every subject at once:
+/* (a)+(b), Eq. 5 and Algorithm 1's per-subject loop, for every subject at once:
  * A_k = X_k V S_k H^T = B D C^T (thin SVD) and Q_k = B C^T over the singular values with
  * sigma^2 > tau * sigma_max^2 (tau = 1e-8 in the paper's reading used here). Computed by
  * one-sided Jacobi on the rows of A_k (I_k <= R) or of the R factor of a Householder QR
@@ -174,7 +174,7 @@ copa_status_t copa_gram(copa_handle_t handle, const void* A, int64_t rows, int32
 copa_status_t copa_gram_noalloc(void* stream, int32_t a_is_double, const void* A, int64_t rows,
                                 int32_t R, double* G);
 
-/* (d) One factor update by ADMM (Algorithm 1 inner loop; Eq. Solve_W update rules):
+/* (d) One factor update by ADMM (Algorithm 1 inner loop; Eq. 8 update rules):
  * G = Ga .* Gb (R x R double, Hadamard product of two Grams; Gb may be NULL meaning
  * G = Ga), rho = trace(G)/R, L = chol(G + rho I) (FP64), then n_inner times, row-wise
  *   z = (G + rho I)^{-1} (f + rho (zbar + d)),  zbar = prox_c(z - d),  d = d + zbar - z.

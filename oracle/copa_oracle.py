@@ -10,10 +10,10 @@ dense slices X_k, dense projected slices Y_k over the columns X_k uses.
 
 Notation follows the paper: X_k (I_k x J) ~ Q_k H S_k V^T with S_k = diag(W(k,:)),
 Q_k^T Q_k = I; Y_k = Q_k^T X_k (R x J) are the frontal slices of the R x J x K tensor Y
-that is CP-decomposed as [H; V; W] (Sec. 3.1, Eq. Solve_HWV).
+that is CP-decomposed as [H; V; W] (Sec. 3.1, Eq. 7).
 
 Readings of the paper used here (the paper is silent or ambiguous at these points):
-  * Procrustes (Eq. solv_Q, Algorithm 1): A_k = X_k V S_k H^T = B D C^T (thin SVD,
+  * Procrustes (Eq. 5, Algorithm 1): A_k = X_k V S_k H^T = B D C^T (thin SVD,
     B left, C right singular vectors) and Q_k = B C^T, keeping only singular values
     with d_i^2 > TAU * d_max^2 (TAU = 1e-8); A_k = 0 gives Q_k = 0. This is the
     pseudo-polar factor: the Procrustes optimum whenever that optimum is unique.
@@ -21,7 +21,7 @@ Readings of the paper used here (the paper is silent or ambiguous at these point
     proximal output), updated in the order H, W, V (Algorithm 1).
   * rho = trace(G) / R (Algorithm 1), recomputed once per mode per outer iteration.
   * Inner ADMM, row form: (G + rho I) z = f + rho (zbar + d); zbar = prox(z - d);
-    d = d + zbar - z (Eq. Solve_W update rules, Algorithm 1).
+    d = d + zbar - z (Eq. 8 update rules, Algorithm 1).
   * l1 prox: sign(v) max(|v| - lambda/rho, 0); l0 prox: v if v^2 > 2 lambda/rho else 0
     (a tie goes to 0); non-negativity: max(0, v) (Sec. 3.3.2, 3.3.3).
   * Fixed inner and outer iteration counts; Zbar and D carried across outer iterations.
@@ -45,12 +45,12 @@ NONE, NONNEG, L1, L0 = "none", "nonneg", "l1", "l0"
 
 
 # ------------------------------------------------------------------------------------
-# Procrustes step and projection (Sec. 3.1, Eq. solv_Q; Algorithm 1, per-subject loop)
+# Procrustes step and projection (Sec. 3.1, Eq. 5; Algorithm 1, per-subject loop)
 # ------------------------------------------------------------------------------------
 
 def procrustes(Xk: np.ndarray, V: np.ndarray, w: np.ndarray, H: np.ndarray,
                tau: float = TAU) -> np.ndarray:
-    """Q_k = B C^T from the truncated SVD of A_k = X_k V S_k H^T (Eq. solv_Q)."""
+    """Q_k = B C^T from the truncated SVD of A_k = X_k V S_k H^T (Eq. 5)."""
     R = H.shape[0]
     A = Xk @ V @ np.diag(w) @ H.T
     if A.shape[0] == 0:
@@ -141,7 +141,7 @@ def mttkrp_W(Ys: Slices, H, V) -> np.ndarray:
 
 
 # ------------------------------------------------------------------------------------
-# ADMM inner loop (Eq. Solve_W update rules, Algorithm 1) and proximal operators
+# ADMM inner loop (Eq. 8 update rules, Algorithm 1) and proximal operators
 # ------------------------------------------------------------------------------------
 
 def prox(v: np.ndarray, kind: str, lam: float, rho: float) -> np.ndarray:

@@ -177,9 +177,9 @@ copa_status_t get_schedule(copa_ctx* h, const TensorView& X, const int64_t** ord
   int* tmp = nullptr;
   if ((st = ws_get(h, SLOT_ORDER, sizeof(int64_t) * (X.K + 1), (void**)&ord)) != COPA_OK) return st;
   if ((st = ws_get(h, SLOT_SCHED_TMP, sizeof(int) * 3 * kBuckets, (void**)&tmp)) != COPA_OK) return st;
+  if ((st = cuda_check(h, cudaMemsetAsync(tmp, 0, sizeof(int) * 3 * kBuckets, h->stream), "memset")) != COPA_OK)
+    return st;
   if (X.K > 0) {
-    if ((st = cuda_check(h, cudaMemsetAsync(tmp, 0, sizeof(int) * 3 * kBuckets, h->stream), "memset")) != COPA_OK)
-      return st;
     const int blocks = (int)std::min<int64_t>((X.K + 255) / 256, 4096);
     k_sched_hist<<<blocks, 256, 0, h->stream>>>(X.subj_ptr, X.K, tmp);
     k_sched_scan<<<1, 32, 0, h->stream>>>(tmp, tmp + kBuckets);
@@ -192,6 +192,12 @@ copa_status_t get_schedule(copa_ctx* h, const TensorView& X, const int64_t** ord
   h->sched_S = X.S;
   *order = ord;
   return COPA_OK;
+}
+
+const int* schedule_count_above(copa_ctx* h, int thr) {
+  // the scan left offs[b] = number of subjects in buckets before b (bucket b holds I_k =
+  // kBuckets - 1 - b), i.e. offs[kBuckets - 1 - thr] subjects have I_k > thr
+  return reinterpret_cast<const int*>(h->slot_ptr[SLOT_SCHED_TMP]) + kBuckets + (kBuckets - 1 - thr);
 }
 
 copa_status_t get_warm_offsets(copa_ctx* h, const TensorView& X, int R, const int64_t** woff, int64_t* total) {

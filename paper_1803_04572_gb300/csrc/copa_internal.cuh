@@ -132,7 +132,7 @@ struct copa_ctx {
   int64_t setup_launches = 0;
   // cached column-sorted copy of X
   const int32_t* csc_key = nullptr;
-  int64_t csc_nnz = -1;
+  int64_t csc_nnz = -1, csc_S = -1;
   int csc_J = 0, csc_prec = -1;
 };
 
@@ -164,6 +164,10 @@ copa_status_t cuda_check(copa_ctx* h, cudaError_t e, const char* what);
 TensorView view_of(const copa_tensor_t* X);
 copa_status_t check_tensor_args(copa_ctx* h, const copa_tensor_t* X);
 copa_status_t get_schedule(copa_ctx* h, const TensorView& X, const int64_t** order);
+// Device pointer to the number of subjects with I_k > thr (0 <= thr < 2047), which is the
+// length of the prefix of the schedule (decreasing I_k) that holds them. Valid after
+// get_schedule for the same tensor, until the next get_schedule for another tensor.
+const int* schedule_count_above(copa_ctx* h, int thr);
 
 // ---- launchers (host functions, enqueue on h->stream) ----
 template <typename Real>

@@ -1,5 +1,5 @@
 // Gradient of the reconstruction loss L = sum_k ||X_k - Q_k H S_k V^T||_F^2 (no 1/2)
-// with Q_k fixed, from the model of Sec. 2 / Eq. Classic_PARAFAC2_obj_func. With
+// with Q_k fixed, from the model of Sec. 2 / Eq. 1. With
 // R_k = X_k - Q_k H S_k V^T, Phi = V^T V, Pi_k = Q_k^T Q_k, T_k = Q_k^T X_k V:
 //   dL/dH      = -2 sum_k Q_k^T R_k V S_k = -2 (F_H - sum_k Pi_k H S_k Phi S_k)
 //   dL/dV      = -2 sum_k R_k^T Q_k H S_k = -2 (F_V - V U^T U)

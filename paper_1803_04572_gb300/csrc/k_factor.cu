@@ -1,6 +1,6 @@
 // MTTKRPs on the implicit Y (Algorithm 1, "F = Y_(n)(Khatri-Rao of the others)"), the
 // factor Grams, rho and the cached Cholesky of G + rho I, the ADMM inner loops with the
-// proximal operators of Sec. 3.3 (Eq. Solve_W update rules), and the FIT of Sec. 4.1.
+// proximal operators of Sec. 3.3 (Eq. 8 update rules), and the FIT of Sec. 4.1.
 //
 // With Q_k from k_procrustes.cu and T_k = Q_k^T X_k V (Y_k = Q_k^T X_k never formed):
 //   F_H = sum_k Y_k V S_k        = sum_k T_k S_k
@@ -173,6 +173,122 @@ __global__ void __launch_bounds__(kUNT) k_uvec(
   }
 }
 
+// Tiled form of step 1 for R <= 48: a block takes kVT consecutive visit rows at a time
+// (rows of any subjects; the subject of a row comes from the row -> subject map), forms
+// the kVT x R tile of U = (Q H) .* W(k(i), :) as a small GEMM from shared memory (a thread
+// owns 4 rows x NC columns), writes the tile out coalesced, and adds the tile's Gram to
+// U^T U: four groups of 64 threads take 32 rows each, a thread owning an NC x NC block,
+// summed in FP32 within a tile and in FP64 across tiles.
+constexpr int kVT = 128;    // rows per tile
+constexpr int kVNT = 256;   // threads per block
+
+template <typename Real, int NC>   // NC = ceil(R / 8)
+__global__ void __launch_bounds__(kVNT, 2) k_uvec_tiled(int64_t S, int R, const Real* __restrict__ Q,
+                                                       const Real* __restrict__ H, const Real* __restrict__ W,
+                                                       const int32_t* __restrict__ row_subj, Real* __restrict__ U,
+                                                       double* __restrict__ utu_part) {
+  constexpr int HL = 8 * NC;   // padded row length of H in shared memory
+  extern __shared__ unsigned char smem_raw[];
+  Real* Hs = reinterpret_cast<Real*>(smem_raw);   // Hs[r * HL + c] = H(r, c), zero-padded
+  Real* Ts = Hs + HL * HL;                        // kVT x ld: Q rows, then U rows
+  const int ld = R + 1;
+  const int tid = threadIdx.x;
+  const int tx = tid & 7, ty = tid >> 3;                            // GEMM mapping
+  const int g = tid >> 6, gp = (tid >> 3) & 7, gq = tid & 7;        // Gram mapping
+  for (int e = tid; e < HL * HL; e += kVNT) {
+    const int r = e / HL, c = e - r * HL;
+    Hs[e] = (r < R && c < R) ? H[r * R + c] : Real(0);
+  }
+  double dacc[NC][NC];
+#pragma unroll
+  for (int a = 0; a < NC; ++a)
+#pragma unroll
+    for (int b = 0; b < NC; ++b) dacc[a][b] = 0.0;
+
+  for (int64_t i0 = (int64_t)blockIdx.x * kVT; i0 < S; i0 += (int64_t)gridDim.x * kVT) {
+    const int nrow = (int)min((int64_t)kVT, S - i0);
+    __syncthreads();   // the previous tile's Gram reads are done (and Hs is filled)
+    const Real* qt = Q + i0 * R;
+    for (int e = tid; e < kVT * R; e += kVNT) {
+      const int i = e / R, c = e - i * R;
+      Ts[i * ld + c] = i < nrow ? qt[e] : Real(0);
+    }
+    __syncthreads();
+    Real acc[4][NC];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < NC; ++b) acc[a][b] = Real(0);
+#pragma unroll 2
+    for (int r = 0; r < R; ++r) {
+      Real qa[4], hb[NC];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) qa[a] = Ts[(ty * 4 + a) * ld + r];
+#pragma unroll
+      for (int b = 0; b < NC; ++b) hb[b] = Hs[r * HL + tx * NC + b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < NC; ++b) acc[a][b] += qa[a] * hb[b];
+    }
+    __syncthreads();   // every read of the Q tile is done
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int i = ty * 4 + a;
+      const int64_t k = i < nrow ? (int64_t)row_subj[i0 + i] : -1;
+#pragma unroll
+      for (int b = 0; b < NC; ++b) {
+        const int c = tx * NC + b;
+        if (c < R) Ts[i * ld + c] = k >= 0 ? acc[a][b] * W[k * R + c] : Real(0);
+      }
+    }
+    __syncthreads();
+    Real* ut = U + i0 * R;
+    for (int e = tid; e < nrow * R; e += kVNT) {
+      const int i = e / R, c = e - i * R;
+      ut[e] = Ts[i * ld + c];
+    }
+    if (utu_part) {
+      Real sacc[NC][NC];
+#pragma unroll
+      for (int a = 0; a < NC; ++a)
+#pragma unroll
+        for (int b = 0; b < NC; ++b) sacc[a][b] = Real(0);
+      for (int i = g * (kVT / 4); i < (g + 1) * (kVT / 4); ++i) {
+        Real ua[NC], ub[NC];
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+          const int c = gp * NC + a;
+          ua[a] = c < R ? Ts[i * ld + c] : Real(0);
+        }
+#pragma unroll
+        for (int b = 0; b < NC; ++b) {
+          const int c = gq * NC + b;
+          ub[b] = c < R ? Ts[i * ld + c] : Real(0);
+        }
+#pragma unroll
+        for (int a = 0; a < NC; ++a)
+#pragma unroll
+          for (int b = 0; b < NC; ++b) sacc[a][b] += ua[a] * ub[b];
+      }
+#pragma unroll
+      for (int a = 0; a < NC; ++a)
+#pragma unroll
+        for (int b = 0; b < NC; ++b) dacc[a][b] += (double)sacc[a][b];
+    }
+  }
+  if (utu_part) {
+    double* up = utu_part + ((size_t)blockIdx.x * 4 + g) * R * R;
+#pragma unroll
+    for (int a = 0; a < NC; ++a)
+#pragma unroll
+      for (int b = 0; b < NC; ++b) {
+        const int r = gp * NC + a, c = gq * NC + b;
+        if (r < R && c < R) up[r * R + c] = dacc[a][b];
+      }
+  }
+}
+
 template <typename Real>
 __global__ void __launch_bounds__(256) k_spmm_csc(int64_t nnz, int J, int R, const int64_t* __restrict__ cptr,
                                                   const int32_t* __restrict__ crow, const Real* __restrict__ cval,
@@ -225,23 +341,65 @@ __global__ void __launch_bounds__(256) k_spmm_csc(int64_t nnz, int J, int R, con
 }
 
 // column-sorted copy of X: histogram of columns, exclusive scan, scatter (row index and
-// value of every nonzero; the order inside a column is arbitrary)
+// value of every nonzero; the order inside a column is arbitrary). Code frequencies are
+// heavy-tailed, so both passes aggregate before touching a shared counter: the histogram
+// counts in shared memory per block (J <= kHistSmem), the scatter claims positions once
+// per (warp, column) with the lanes that hold the same column.
+constexpr int kHistSmem = 12288;
+
 __global__ void k_csc_hist(TensorView X, int64_t* __restrict__ cnt) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < X.nnz; t += gridDim.x * (int64_t)blockDim.x)
-    atomicAdd(reinterpret_cast<unsigned long long*>(cnt + X.col[t]), 1ull);
+  __shared__ unsigned int sh[kHistSmem];
+  const bool local = X.J <= kHistSmem;
+  if (local) {
+    for (int j = threadIdx.x; j < X.J; j += blockDim.x) sh[j] = 0u;
+    __syncthreads();
+  }
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < X.nnz; t += gridDim.x * (int64_t)blockDim.x) {
+    const int c = X.col[t];
+    if (local) atomicAdd(sh + c, 1u);
+    else atomicAdd(reinterpret_cast<unsigned long long*>(cnt + c), 1ull);
+  }
+  if (local) {
+    __syncthreads();
+    for (int j = threadIdx.x; j < X.J; j += blockDim.x)
+      if (sh[j]) atomicAdd(reinterpret_cast<unsigned long long*>(cnt + j), (unsigned long long)sh[j]);
+  }
 }
 
+// one visit row per lane; the lanes step through their rows' nonzeros together
 template <typename Real>
 __global__ void k_csc_scatter(TensorView X, const int64_t* __restrict__ cptr, int64_t* __restrict__ cur,
                               int32_t* __restrict__ crow, Real* __restrict__ cval) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < X.S; i += gridDim.x * (int64_t)blockDim.x) {
-    for (int64_t t = X.row_ptr[i]; t < X.row_ptr[i + 1]; ++t) {
-      const int c = X.col[t];
-      const int64_t pos = cptr[c] + (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(cur + c), 1ull);
-      crow[pos] = (int32_t)i;
-      cval[pos] = load_x<Real>(X, t);
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = gridDim.x * (int64_t)blockDim.x;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < X.S; base += stride) {
+    const int64_t i = base + lane;
+    int64_t t = 0, e = 0;
+    if (i < X.S) { t = X.row_ptr[i]; e = X.row_ptr[i + 1]; }
+    while (true) {
+      const bool act = t < e;
+      const unsigned amask = __ballot_sync(0xffffffffu, act);
+      if (amask == 0u) break;
+      if (act) {
+        const int c = X.col[t];
+        const unsigned peers = __match_any_sync(amask, c);
+        const int leader = __ffs(peers) - 1;
+        unsigned long long pos0 = 0;
+        if (lane == leader) pos0 = atomicAdd(reinterpret_cast<unsigned long long*>(cur + c), (unsigned long long)__popc(peers));
+        pos0 = __shfl_sync(peers, pos0, leader);
+        const int64_t pos = cptr[c] + (int64_t)pos0 + __popc(peers & ((1u << lane) - 1u));
+        crow[pos] = (int32_t)i;
+        cval[pos] = load_x<Real>(X, t);
+        ++t;
+      }
     }
   }
+}
+
+// subject of every visit row
+__global__ void k_row_subject(const int64_t* __restrict__ subj_ptr, int64_t K, int32_t* __restrict__ rs) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K; k += gridDim.x * (int64_t)blockDim.x)
+    for (int64_t i = subj_ptr[k]; i < subj_ptr[k + 1]; ++i) rs[i] = (int32_t)k;
 }
 
 __global__ void k_scan_cols(int64_t* __restrict__ v, int n) {
@@ -249,20 +407,6 @@ __global__ void k_scan_cols(int64_t* __restrict__ v, int n) {
     int64_t acc = 0;
     for (int j = 0; j < n; ++j) { const int64_t x = v[j]; v[j] = acc; acc += x; }
     v[n] = acc;
-  }
-}
-
-// packed (upper-triangle) per-warp partials -> full symmetric FP64 matrix
-__global__ void k_unpack_sym_sum(const double* __restrict__ part, int nparts, int R,
-                                 double* __restrict__ out) {
-  const int npk = R * (R + 1) / 2;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < R * R; e += gridDim.x * blockDim.x) {
-    int r = e / R, s = e % R;
-    if (r > s) { const int t = r; r = s; s = t; }
-    const int pidx = r * R - r * (r - 1) / 2 + (s - r);
-    double acc = 0.0;
-    for (int q = 0; q < nparts; ++q) acc += part[(size_t)q * npk + pidx];
-    out[e] = acc;
   }
 }
 
@@ -547,43 +691,90 @@ copa_status_t launch_mttkrp_w(copa_ctx* h, int64_t K, int R, const Real* T, cons
 
 // The column-sorted copy is rebuilt unless `reuse` (copa_fit builds it once per call and
 // reuses it for the later iterations of the same call, where X cannot change).
+// Column-sorted copy of X and the row -> subject map, in SLOT_CSC:
+//   int64 ptr[J+1], int64 cursor[J+1], int32 rows[nnz], Real vals[nnz] (16-byte aligned),
+//   int32 row_subj[S] (16-byte aligned).
 template <typename Real>
 static copa_status_t get_csc(copa_ctx* h, const TensorView& X, bool reuse, const int64_t** cptr,
-                             const int32_t** crow, const Real** cval) {
+                             const int32_t** crow, const Real** cval, const int32_t** rsubj) {
   copa_status_t st;
   const int prec = sizeof(Real) == 8 ? 1 : 0;
+  auto al16 = [](uintptr_t v) { return (v + 15) & ~uintptr_t(15); };
+  auto layout = [&](char* p, int64_t** ptr, int32_t** rows, Real** vals, int32_t** rs) {
+    *ptr = reinterpret_cast<int64_t*>(p);
+    *rows = reinterpret_cast<int32_t*>(*ptr + 2 * ((size_t)X.J + 1));
+    *vals = reinterpret_cast<Real*>(al16(reinterpret_cast<uintptr_t>(*rows + X.nnz)));
+    *rs = reinterpret_cast<int32_t*>(al16(reinterpret_cast<uintptr_t>(*vals + X.nnz)));
+  };
+  int64_t* ptr = nullptr;
+  int32_t* rows = nullptr;
+  Real* vals = nullptr;
+  int32_t* rs = nullptr;
   if (!(reuse && h->csc_key == X.col && h->csc_nnz == X.nnz && h->csc_J == X.J && h->csc_prec == prec &&
-        h->slot_ptr[SLOT_CSC])) {
+        h->csc_S == X.S && h->slot_ptr[SLOT_CSC])) {
     const size_t bytes = sizeof(int64_t) * 2 * ((size_t)X.J + 1) + sizeof(int32_t) * (size_t)X.nnz +
-                         sizeof(Real) * (size_t)X.nnz + 256;
+                         sizeof(Real) * (size_t)X.nnz + sizeof(int32_t) * (size_t)X.S + 64;
     char* p = nullptr;
     if ((st = ws_get(h, SLOT_CSC, bytes, (void**)&p)) != COPA_OK) return st;
-    int64_t* ptr = reinterpret_cast<int64_t*>(p);
+    layout(p, &ptr, &rows, &vals, &rs);
     int64_t* cur = ptr + X.J + 1;
-    int32_t* rows = reinterpret_cast<int32_t*>(cur + X.J + 1);
-    Real* vals = reinterpret_cast<Real*>((reinterpret_cast<uintptr_t>(rows + X.nnz) + 15) & ~uintptr_t(15));
     if ((st = cuda_check(h, cudaMemsetAsync(ptr, 0, sizeof(int64_t) * 2 * ((size_t)X.J + 1), h->stream),
                          "memset")) != COPA_OK)
       return st;
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((X.nnz + 255) / 256, (int64_t)h->num_sms * 16));
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((X.nnz + 255) / 256, (int64_t)h->num_sms * 8));
     k_csc_hist<<<blocks, 256, 0, h->stream>>>(X, ptr);
     k_scan_cols<<<1, 32, 0, h->stream>>>(ptr, X.J);
     const int rblocks = (int)std::max<int64_t>(1, std::min<int64_t>((X.S + 255) / 256, (int64_t)h->num_sms * 16));
     k_csc_scatter<Real><<<rblocks, 256, 0, h->stream>>>(X, ptr, cur, rows, vals);
+    const int kblocks = (int)std::max<int64_t>(1, std::min<int64_t>((X.K + 255) / 256, (int64_t)h->num_sms * 16));
+    k_row_subject<<<kblocks, 256, 0, h->stream>>>(X.subj_ptr, X.K, rs);
     if ((st = cuda_check(h, cudaGetLastError(), "csc build")) != COPA_OK) return st;
-    h->setup_launches += 3;
+    h->setup_launches += 4;
     h->csc_key = X.col;
     h->csc_nnz = X.nnz;
     h->csc_J = X.J;
+    h->csc_S = X.S;
     h->csc_prec = prec;
+  } else {
+    layout(reinterpret_cast<char*>(h->slot_ptr[SLOT_CSC]), &ptr, &rows, &vals, &rs);
   }
-  char* p = reinterpret_cast<char*>(h->slot_ptr[SLOT_CSC]);
-  const int64_t* ptr = reinterpret_cast<const int64_t*>(p);
-  const int32_t* rows = reinterpret_cast<const int32_t*>(ptr + 2 * ((size_t)X.J + 1));
   *cptr = ptr;
   *crow = rows;
-  *cval = reinterpret_cast<const Real*>((reinterpret_cast<uintptr_t>(rows + X.nnz) + 15) & ~uintptr_t(15));
+  *cval = vals;
+  *rsubj = rs;
   return COPA_OK;
+}
+
+template <typename Real>
+static copa_status_t launch_uvec_tiled(copa_ctx* h, int64_t S, int R, const Real* Q, const Real* H, const Real* W,
+                                       const int32_t* rsubj, Real* U, double* UtU_part_or_null, int64_t* nparts,
+                                       bool size_only) {
+  const int nc = (R + 7) / 8;
+  void (*kern)(int64_t, int, const Real*, const Real*, const Real*, const int32_t*, Real*, double*) = nullptr;
+  switch (nc) {
+    case 1: kern = k_uvec_tiled<Real, 1>; break;
+    case 2: kern = k_uvec_tiled<Real, 2>; break;
+    case 3: kern = k_uvec_tiled<Real, 3>; break;
+    case 4: kern = k_uvec_tiled<Real, 4>; break;
+    case 5: kern = k_uvec_tiled<Real, 5>; break;
+    case 6: kern = k_uvec_tiled<Real, 6>; break;
+    default: return fail(h, COPA_ERR_UNSUPPORTED, "tiled U: R > 48");
+  }
+  const size_t smem = sizeof(Real) * ((size_t)64 * nc * nc + (size_t)kVT * (R + 1));
+  copa_status_t st;
+  if ((st = cuda_check(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                       "cudaFuncSetAttribute")) != COPA_OK)
+    return st;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kVNT, smem);
+  if (per_sm < 1) per_sm = 1;
+  int64_t blocks = (int64_t)h->num_sms * per_sm;
+  const int64_t need = (S + kVT - 1) / kVT;
+  if (blocks > need) blocks = std::max<int64_t>(need, 1);
+  *nparts = blocks * 4;
+  if (size_only) return COPA_OK;
+  kern<<<(unsigned)blocks, kVNT, smem, h->stream>>>(S, R, Q, H, W, rsubj, U, UtU_part_or_null);
+  return cuda_check(h, cudaGetLastError(), "k_uvec_tiled");
 }
 
 template <typename Real>
@@ -591,49 +782,58 @@ copa_status_t launch_mttkrp_v(copa_ctx* h, const TensorView& X, int R, const Rea
                               const Real* W, Real* F, double* UtU, bool reuse_csc) {
   if (R > kMaxR) return fail(h, COPA_ERR_UNSUPPORTED, "mttkrp V: R too large");
   copa_status_t st;
-  const int64_t* order = nullptr;
-  if ((st = get_schedule(h, X, &order)) != COPA_OK) return st;
   const int64_t* cptr = nullptr;
   const int32_t* crow = nullptr;
   const Real* cval = nullptr;
-  if ((st = get_csc<Real>(h, X, reuse_csc, &cptr, &crow, &cval)) != COPA_OK) return st;
+  const int32_t* rsubj = nullptr;
+  if ((st = get_csc<Real>(h, X, reuse_csc, &cptr, &crow, &cval, &rsubj)) != COPA_OK) return st;
   Real* U = nullptr;
   if ((st = ws_get(h, SLOT_UVEC, sizeof(Real) * ((size_t)X.S * R + 16), (void**)&U)) != COPA_OK) return st;
-  int* counter = nullptr;
-  if ((st = ws_get(h, SLOT_COUNTER, 64, (void**)&counter)) != COPA_OK) return st;
-  if ((st = cuda_check(h, cudaMemsetAsync(counter + 1, 0, sizeof(int), h->stream), "memset")) != COPA_OK)
-    return st;
   if ((st = cuda_check(h, cudaMemsetAsync(F, 0, sizeof(Real) * (size_t)X.J * R, h->stream), "memset F")) != COPA_OK)
     return st;
-  const bool tiles = R <= kTR * 8;
-  const int nw = kUNT / 32;
-  const int npk = R * (R + 1) / 2;
-  const size_t smem = sizeof(Real) * ((size_t)R * R + (size_t)nw * (2 * R + (tiles ? 0 : npk))) +
-                      (tiles ? 0 : sizeof(uint16_t) * npk) + 64;
-  auto kern = tiles ? k_uvec<Real, true> : k_uvec<Real, false>;
-  if ((st = cuda_check(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                       "cudaFuncSetAttribute")) != COPA_OK)
-    return st;
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kUNT, smem);
-  if (per_sm < 1) per_sm = 1;
-  int64_t blocks = (int64_t)h->num_sms * per_sm;
-  const int64_t need = (X.K + nw - 1) / nw;
-  if (blocks > need) blocks = need > 0 ? need : 1;
   double* part = nullptr;
-  const int nparts = (int)blocks * nw;
-  if (UtU) {
-    if ((st = ws_get(h, SLOT_PARTIAL, (size_t)nparts * R * R * sizeof(double), (void**)&part)) != COPA_OK)
+  int64_t nparts = 0;
+  if (R <= 48) {
+    if ((st = launch_uvec_tiled<Real>(h, X.S, R, Q, H, W, rsubj, U, nullptr, &nparts, true)) != COPA_OK) return st;
+    if (UtU && (st = ws_get(h, SLOT_PARTIAL, (size_t)nparts * R * R * sizeof(double), (void**)&part)) != COPA_OK)
       return st;
+    if ((st = launch_uvec_tiled<Real>(h, X.S, R, Q, H, W, rsubj, U, part, &nparts, false)) != COPA_OK) return st;
+  } else {
+    const int64_t* order = nullptr;
+    if ((st = get_schedule(h, X, &order)) != COPA_OK) return st;
+    int* counter = nullptr;
+    if ((st = ws_get(h, SLOT_COUNTER, 64, (void**)&counter)) != COPA_OK) return st;
+    if ((st = cuda_check(h, cudaMemsetAsync(counter + 1, 0, sizeof(int), h->stream), "memset")) != COPA_OK)
+      return st;
+    const bool tiles = R <= kTR * 8;
+    const int nw = kUNT / 32;
+    const int npk = R * (R + 1) / 2;
+    const size_t smem = sizeof(Real) * ((size_t)R * R + (size_t)nw * (2 * R + (tiles ? 0 : npk))) +
+                        (tiles ? 0 : sizeof(uint16_t) * npk) + 64;
+    auto kern = tiles ? k_uvec<Real, true> : k_uvec<Real, false>;
+    if ((st = cuda_check(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                         "cudaFuncSetAttribute")) != COPA_OK)
+      return st;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kUNT, smem);
+    if (per_sm < 1) per_sm = 1;
+    int64_t blocks = (int64_t)h->num_sms * per_sm;
+    const int64_t need = (X.K + nw - 1) / nw;
+    if (blocks > need) blocks = need > 0 ? need : 1;
+    nparts = blocks * nw;
+    if (UtU) {
+      if ((st = ws_get(h, SLOT_PARTIAL, (size_t)nparts * R * R * sizeof(double), (void**)&part)) != COPA_OK)
+        return st;
+    }
+    kern<<<(unsigned)blocks, kUNT, smem, h->stream>>>(X, R, Q, H, W, U, part, order, counter + 1);
+    if ((st = cuda_check(h, cudaGetLastError(), "k_uvec")) != COPA_OK) return st;
   }
-  kern<<<(unsigned)blocks, kUNT, smem, h->stream>>>(X, R, Q, H, W, U, part, order, counter + 1);
-  if ((st = cuda_check(h, cudaGetLastError(), "k_uvec")) != COPA_OK) return st;
   const int64_t nchunks = (X.nnz + kChunk - 1) / kChunk;
   const int sblocks = (int)std::max<int64_t>(1, std::min<int64_t>((nchunks + 7) / 8, (int64_t)h->num_sms * 16));
   k_spmm_csc<Real><<<sblocks, 256, 0, h->stream>>>(X.nnz, X.J, R, cptr, crow, cval, U, F);
   if ((st = cuda_check(h, cudaGetLastError(), "k_spmm_csc")) != COPA_OK) return st;
   if (UtU) {
-    k_reduce_rows<double><<<(R * R + 255) / 256, 256, 0, h->stream>>>(part, nparts, R * R, UtU);
+    k_reduce_rows<double><<<(R * R + 255) / 256, 256, 0, h->stream>>>(part, (int)nparts, R * R, UtU);
     if ((st = cuda_check(h, cudaGetLastError(), "UtU reduce")) != COPA_OK) return st;
   }
   return COPA_OK;

@@ -1,4 +1,4 @@
-// Procrustes step of COPA (Sec. 3.1, Eq. solv_Q; Algorithm 1 per-subject loop) and the
+// Procrustes step of COPA (Sec. 3.1, Eq. 5; Algorithm 1 per-subject loop) and the
 // fused mode-1 MTTKRP, for all subjects in one persistent launch: one CTA of 128 threads
 // (4 warps) per subject, dynamic scheduling over a largest-first subject order.
 //
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kNT) k_procrustes(
     Real* __restrict__ Pi, int32_t* __restrict__ rank, double* __restrict__ fh_partial,
     const int64_t* __restrict__ order, int* __restrict__ counter,
     unsigned long long* __restrict__ fma_count, Real* __restrict__ Uw,
-    const int64_t* __restrict__ woff, int warm_in) {
+    const int64_t* __restrict__ woff, int warm_in, const int* __restrict__ limit) {
   extern __shared__ unsigned char smem_raw[];
   Real* sm = reinterpret_cast<Real*>(smem_raw);
   const Lay L = lay_of<Real>(R);
@@ -215,6 +215,8 @@ __global__ void __launch_bounds__(kNT) k_procrustes(
   int* sidx = reinterpret_cast<int*>(misc + 8);
   const Real tol = Tol<Real>::v();
   unsigned long long fma = 0;   // work tally (thread 0), for the roofline
+  // subjects order[0 .. kend) are this kernel's; the rest take the warp path
+  const int64_t kend = limit ? min((int64_t)max(*limit, 0), X.K) : X.K;
 
   double* fh = fh_partial ? fh_partial + (size_t)blockIdx.x * R * R : nullptr;
   if (fh)
@@ -225,7 +227,7 @@ __global__ void __launch_bounds__(kNT) k_procrustes(
     if (tid == 0) sidx[0] = atomicAdd(counter, 1);
     __syncthreads();
     const int idx = sidx[0];
-    if (idx >= X.K) break;
+    if (idx >= kend) break;
     const int64_t k = order ? order[idx] : idx;
     const int64_t r0 = X.subj_ptr[k], r1 = X.subj_ptr[k + 1];
     const int64_t Ik64 = r1 - r0;
@@ -465,6 +467,321 @@ __global__ void __launch_bounds__(kNT) k_procrustes(
   if (fma_count && tid == 0) atomicAdd(fma_count, fma);
 }
 
+// ---- warp-per-subject path for the many small subjects (I_k <= min(R, 32)) ----
+// One warp per subject, lane i holding row i of A_k (then of Z = U A_k) and row i of U in
+// registers, so that a Jacobi round needs no block barrier: the partner row is read with
+// shuffles and both lanes of a pair compute the same rotation from the same three dot
+// products. Pairs follow the circle method on n2 = m + (m & 1) positions: position n2-1
+// meets position r in round r, every other position i meets (2r - i) mod (n2 - 1).
+// Rows are zero-padded to kR components (R rounded up to a multiple of 8); padding stays 0
+// under the rotations. Outputs are the same as the block path's wide branch.
+constexpr int kWNT = 128;   // threads per block of the warp path (4 subjects at a time)
+
+template <typename Real, int kR>
+struct WarpLay {
+  static constexpr int kM = kR < 32 ? kR : 32;   // rows of a subject on this path
+  static constexpr int ld = kR + 1;              // odd: lane-per-row stores are conflict-free
+  static constexpr int ldu = kM + 1;
+  static constexpr int per_warp = 2 * kM * ld + kM * ldu;
+  static constexpr size_t bytes = sizeof(Real) * ((size_t)kR * kR + (kWNT / 32) * (size_t)per_warp);
+};
+
+template <typename Real, int kR>
+__global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
+    TensorView X, int R, const Real* __restrict__ H, const Real* __restrict__ V,
+    const Real* __restrict__ W, double tau_rank, Real* __restrict__ Q, Real* __restrict__ T,
+    Real* __restrict__ Pi, int32_t* __restrict__ rank, double* __restrict__ fh_partial,
+    const int64_t* __restrict__ order, const int* __restrict__ first, int* __restrict__ counter,
+    unsigned long long* __restrict__ fma_count, Real* __restrict__ Uw,
+    const int64_t* __restrict__ woff, int warm_in, int* __restrict__ status) {
+  using Lw = WarpLay<Real, kR>;
+  constexpr int kM = Lw::kM, ld = Lw::ld, ldu = Lw::ldu;
+  constexpr int kTR = kR / 8, kTC = kR / 4;   // T tile of a lane: 8 x 4 lanes cover kR x kR
+  constexpr unsigned kFull = 0xffffffffu;
+  extern __shared__ unsigned char smem_raw[];
+  Real* Hs = reinterpret_cast<Real*>(smem_raw);   // Hs[t * kR + r] = H(t, r), zero-padded
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Real* B1 = Hs + kR * kR + (size_t)warp * Lw::per_warp;   // A rows, then c_j rows
+  Real* B2 = B1 + kM * ld;                                  // p rows, then b = U P rows
+  Real* Us = B2 + kM * ld;                                  // U, for its transpose
+  for (int e = threadIdx.x; e < kR * kR; e += kWNT) {
+    const int t = e / kR, r = e - t * kR;
+    Hs[e] = (t < R && r < R) ? H[t * R + r] : Real(0);
+  }
+  __syncthreads();
+  double* fh = fh_partial ? fh_partial + ((size_t)blockIdx.x * (kWNT / 32) + warp) * R * R : nullptr;
+  if (fh)
+    for (int e = lane; e < R * R; e += 32) fh[e] = 0.0;
+  const Real tol = Tol<Real>::v();
+  const int64_t k0 = min((int64_t)max(*first, 0), X.K);
+  const int tr = lane >> 2, tc = lane & 3;
+  unsigned long long fma = 0;
+
+  while (true) {
+    int claim = 0;
+    if (lane == 0) claim = atomicAdd(counter, 1);
+    const int64_t idx = k0 + __shfl_sync(kFull, claim, 0);
+    if (idx >= X.K) break;
+    const int64_t k = order[idx];
+    const int64_t r0 = X.subj_ptr[k];
+    const int64_t ik = X.subj_ptr[k + 1] - r0;
+    if (ik > kM) {   // the schedule split guarantees I_k <= kM; record and skip otherwise
+      if (lane == 0) set_status(status, COPA_ERR_CUDA, (int)k);
+      continue;
+    }
+    const int m = (int)ik;
+    const Real* wk = W + k * R;
+
+    // ---- p_i = x_i V (lane i); a_i = (p_i * w) H^T ----
+    Real p[kR];
+#pragma unroll
+    for (int t = 0; t < kR; ++t) p[t] = Real(0);
+    int nnz_row = 0;
+    if (lane < m) {
+      const int64_t a = X.row_ptr[r0 + lane], b = X.row_ptr[r0 + lane + 1];
+      nnz_row = (int)(b - a);
+      for (int64_t q = a; q < b; ++q) {
+        const Real x = load_x<Real>(X, q);
+        const Real* vr = V + (int64_t)__ldg(X.col + q) * R;
+#pragma unroll
+        for (int t = 0; t < kR; ++t)
+          if (t < R) p[t] += x * __ldg(vr + t);
+      }
+    }
+    if (lane < kM) {
+#pragma unroll
+      for (int t = 0; t < kR; ++t) B2[lane * ld + t] = p[t];
+    }
+    __syncwarp();
+    Real z[kR];
+#pragma unroll
+    for (int t = 0; t < kR; ++t) z[t] = Real(0);
+    if (lane < m) {
+#pragma unroll 1
+      for (int r = 0; r < R; ++r) {
+        const Real pw = B2[lane * ld + r] * wk[r];
+#pragma unroll
+        for (int t = 0; t < kR; ++t) z[t] += pw * Hs[t * kR + r];
+      }
+    }
+
+    // ---- U: identity, or the previous outer iteration's rotation (then Z = U_prev A) ----
+    Real* Uk = Uw ? Uw + woff[k] : nullptr;
+    const bool warm = Uk != nullptr && warm_in != 0;
+    Real u[kM];
+#pragma unroll
+    for (int j = 0; j < kM; ++j) u[j] = (!warm && j == lane && lane < m) ? Real(1) : Real(0);
+    if (warm) {
+      if (lane < kM) {
+#pragma unroll
+        for (int t = 0; t < kR; ++t) B1[lane * ld + t] = z[t];
+      }
+      __syncwarp();
+#pragma unroll
+      for (int t = 0; t < kR; ++t) z[t] = Real(0);
+      if (lane < m) {
+#pragma unroll 1
+        for (int j = 0; j < m; ++j) {
+          const Real uij = Uk[lane * m + j];
+#pragma unroll
+          for (int t = 0; t < kR; ++t) z[t] += uij * B1[j * ld + t];
+        }
+#pragma unroll
+        for (int j = 0; j < kM; ++j)
+          if (j < m) u[j] = Uk[lane * m + j];
+      }
+      __syncwarp();
+    }
+
+    // ---- Hestenes sweeps ----
+    Real al = Real(0);
+#pragma unroll
+    for (int t = 0; t < kR; ++t) al += z[t] * z[t];
+    const int n2 = m + (m & 1);
+    unsigned long long nrot = 0;
+    int sweeps = 0;
+    for (int sweep = 0; sweep < kMaxSweeps && n2 > 1; ++sweep) {
+      ++sweeps;
+      bool any = false;
+      for (int rd = 0; rd < n2 - 1; ++rd) {
+        int j;
+        if (lane >= n2) j = lane;
+        else if (lane == n2 - 1) j = rd;
+        else if (lane == rd) j = n2 - 1;
+        else {
+          j = 2 * rd - lane;
+          if (j < 0) j += n2 - 1;
+          else if (j >= n2 - 1) j -= n2 - 1;
+        }
+        Real zp[kR];
+        Real g0 = Real(0), g1 = Real(0);
+#pragma unroll
+        for (int t = 0; t < kR; ++t) {
+          zp[t] = __shfl_sync(kFull, z[t], j);
+          if (t & 1) g1 += z[t] * zp[t];
+          else g0 += z[t] * zp[t];
+        }
+        const Real be = __shfl_sync(kFull, al, j);
+        const bool lo = lane < j;
+        const Real aa = lo ? al : be, bb = lo ? be : al, gg = g0 + g1;
+        const bool rot = j != lane && gg != Real(0) && fabs(gg) > tol * sqrt(aa * bb);
+        const unsigned rmask = __ballot_sync(kFull, rot);
+        if (rmask == 0u) continue;
+        any = true;
+        if (lane == 0) nrot += __popc(rmask) / 2;
+        Real c = Real(1), s = Real(0);
+        if (rot) {
+          const Real zeta = fdiv_(bb - aa, Real(2) * gg);
+          Real tt;
+          if (fabs(zeta) > Real(1e15)) tt = fdiv_(Real(0.5), zeta);
+          else tt = fdiv_(zeta >= Real(0) ? Real(1) : Real(-1), fabs(zeta) + sqrt(Real(1) + zeta * zeta));
+          c = rsqrt_(Real(1) + tt * tt);
+          s = c * tt;
+        }
+        // lower row x, upper row y: x' = c x - s y, y' = s x + c y
+        const Real so = lo ? -s : s;
+        Real na = Real(0);
+#pragma unroll
+        for (int t = 0; t < kR; ++t) {
+          z[t] = c * z[t] + so * zp[t];
+          na += z[t] * z[t];
+        }
+        if (rot) al = na;
+#pragma unroll
+        for (int jj = 0; jj < kM; ++jj) {
+          if (jj < m) {
+            const Real up = __shfl_sync(kFull, u[jj], j);
+            u[jj] = c * u[jj] + so * up;
+          }
+        }
+      }
+      if (!any) break;
+    }
+    if (Uk && lane < m) {
+#pragma unroll
+      for (int jj = 0; jj < kM; ++jj)
+        if (jj < m) Uk[lane * m + jj] = u[jj];
+    }
+
+    // ---- rank cut; c_i = z_i / sigma_i for kept rows, 0 otherwise ----
+    const Real amax = warp_max(al);
+    const bool keep = lane < m && amax > Real(0) && (double)al > tau_rank * (double)amax;
+    const int kept = __popc(__ballot_sync(kFull, keep));
+    if (rank && lane == 0) rank[k] = kept;
+    const Real inv = keep ? rsqrt_(al) : Real(0);
+    if (lane < kM) {
+#pragma unroll
+      for (int t = 0; t < kR; ++t) B1[lane * ld + t] = z[t] * inv;
+#pragma unroll
+      for (int jj = 0; jj < kM; ++jj) Us[lane * ldu + jj] = u[jj];
+    }
+    __syncwarp();
+
+    // ---- q_i = sum_j U(j, i) c_j and b_i = sum_j U(i, j) p_j ----
+#pragma unroll
+    for (int t = 0; t < kR; ++t) { z[t] = Real(0); p[t] = Real(0); }
+    if (lane < m) {
+#pragma unroll 1
+      for (int jj = 0; jj < m; ++jj) {
+        const Real uji = Us[jj * ldu + lane], uij = Us[lane * ldu + jj];
+#pragma unroll
+        for (int t = 0; t < kR; ++t) {
+          z[t] += uji * B1[jj * ld + t];
+          p[t] += uij * B2[jj * ld + t];
+        }
+      }
+    }
+    __syncwarp();
+    if (lane < m) {
+      Real* qrow = Q + (r0 + lane) * R;
+#pragma unroll
+      for (int t = 0; t < kR; ++t)
+        if (t < R) qrow[t] = z[t];
+    }
+    if (lane < kM) {
+#pragma unroll
+      for (int t = 0; t < kR; ++t) B2[lane * ld + t] = p[t];
+    }
+    __syncwarp();
+
+    // ---- T_k = sum_j c_j^T b_j (lane tile kTR x kTC), F_H partial, optional Pi_k ----
+    {
+      Real acc[kTR][kTC];
+#pragma unroll
+      for (int a = 0; a < kTR; ++a)
+#pragma unroll
+        for (int b = 0; b < kTC; ++b) acc[a][b] = Real(0);
+      for (int jj = 0; jj < m; ++jj) {
+        Real cr[kTR], bs[kTC];
+#pragma unroll
+        for (int a = 0; a < kTR; ++a) cr[a] = B1[jj * ld + tr * kTR + a];
+#pragma unroll
+        for (int b = 0; b < kTC; ++b) bs[b] = B2[jj * ld + tc * kTC + b];
+#pragma unroll
+        for (int a = 0; a < kTR; ++a)
+#pragma unroll
+          for (int b = 0; b < kTC; ++b) acc[a][b] += cr[a] * bs[b];
+      }
+      Real* Tk = T + k * R * R;
+#pragma unroll
+      for (int a = 0; a < kTR; ++a) {
+        const int r = tr * kTR + a;
+        if (r < R) {
+#pragma unroll
+          for (int b = 0; b < kTC; ++b) {
+            const int s = tc * kTC + b;
+            if (s < R) {
+              Tk[r * R + s] = acc[a][b];
+              if (fh) fh[r * R + s] += (double)acc[a][b] * (double)W[k * R + s];
+            }
+          }
+        }
+      }
+    }
+    if (Pi) {
+      Real acc[kTR][kTC];
+#pragma unroll
+      for (int a = 0; a < kTR; ++a)
+#pragma unroll
+        for (int b = 0; b < kTC; ++b) acc[a][b] = Real(0);
+      for (int jj = 0; jj < m; ++jj) {
+        Real cr[kTR], cs[kTC];
+#pragma unroll
+        for (int a = 0; a < kTR; ++a) cr[a] = B1[jj * ld + tr * kTR + a];
+#pragma unroll
+        for (int b = 0; b < kTC; ++b) cs[b] = B1[jj * ld + tc * kTC + b];
+#pragma unroll
+        for (int a = 0; a < kTR; ++a)
+#pragma unroll
+          for (int b = 0; b < kTC; ++b) acc[a][b] += cr[a] * cs[b];
+      }
+      Real* Pk = Pi + k * R * R;
+#pragma unroll
+      for (int a = 0; a < kTR; ++a) {
+        const int r = tr * kTR + a;
+        if (r < R) {
+#pragma unroll
+          for (int b = 0; b < kTC; ++b) {
+            const int s = tc * kTC + b;
+            if (s < R) Pk[r * R + s] = acc[a][b];
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (fma_count) {
+      const int nnzk = __reduce_add_sync(kFull, nnz_row);
+      if (lane == 0) {
+        const unsigned long long mm = (unsigned long long)m, RR = (unsigned long long)R * R;
+        fma += (unsigned long long)nnzk * R + mm * RR + 2ull * mm * R + 2ull * mm * mm * R + 2ull * RR * mm;
+        if (warm) fma += mm * mm * R;
+        fma += (unsigned long long)sweeps * (mm * (mm > 0 ? mm - 1 : 0) / 2) * 3 * R + nrot * 4 * (R + mm);
+      }
+    }
+  }
+  if (fma_count && lane == 0) atomicAdd(fma_count, fma);
+}
+
 template <typename Real>
 __global__ void k_reduce_partials(const double* __restrict__ part, int nparts, int n,
                                   Real* __restrict__ out) {
@@ -472,6 +789,37 @@ __global__ void k_reduce_partials(const double* __restrict__ part, int nparts, i
     double acc = 0.0;
     for (int q = 0; q < nparts; ++q) acc += part[(size_t)q * n + e];
     out[e] = (Real)acc;
+  }
+}
+
+template <typename Real>
+using WarpKernel = void (*)(TensorView, int, const Real*, const Real*, const Real*, double, Real*, Real*, Real*,
+                            int32_t*, double*, const int64_t*, const int*, int*, unsigned long long*, Real*,
+                            const int64_t*, int, int*);
+
+// Instantiation of the warp path for R padded to kr components, or nullptr where the
+// registers of a lane cannot hold a row (float: R <= 48, double: R <= 16).
+template <typename Real>
+WarpKernel<Real> warp_kernel_for(int kr, size_t* smem);
+template <>
+WarpKernel<float> warp_kernel_for<float>(int kr, size_t* smem) {
+  switch (kr) {
+#define COPA_WARP_CASE(KR) \
+  case KR:                 \
+    *smem = WarpLay<float, KR>::bytes; \
+    return k_procrustes_warp<float, KR>;
+    COPA_WARP_CASE(8) COPA_WARP_CASE(16) COPA_WARP_CASE(24) COPA_WARP_CASE(32) COPA_WARP_CASE(40)
+    COPA_WARP_CASE(48)
+#undef COPA_WARP_CASE
+    default: return nullptr;
+  }
+}
+template <>
+WarpKernel<double> warp_kernel_for<double>(int kr, size_t* smem) {
+  switch (kr) {
+    case 8: *smem = WarpLay<double, 8>::bytes; return k_procrustes_warp<double, 8>;
+    case 16: *smem = WarpLay<double, 16>::bytes; return k_procrustes_warp<double, 16>;
+    default: return nullptr;
   }
 }
 
@@ -503,24 +851,51 @@ copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const R
   if (per_sm < 1) per_sm = 1;
   int64_t blocks = (int64_t)h->num_sms * per_sm;
   if (blocks > X.K) blocks = X.K > 0 ? X.K : 1;
+
+  // Subjects with I_k <= min(R, 32) (the tail of the largest-first schedule) take the
+  // warp-per-subject kernel; the block kernel takes the prefix before them.
+  size_t wsmem = 0;
+  const WarpKernel<Real> wkern = warp_kernel_for<Real>((R + 7) / 8 * 8, &wsmem);
+  int64_t wblocks = 0;
+  if (wkern) {
+    if ((st = cuda_check(h, cudaFuncSetAttribute(wkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem),
+                         "cudaFuncSetAttribute")) != COPA_OK)
+      return st;
+    int wper_sm = 0;
+    if ((st = cuda_check(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wper_sm, wkern, kWNT, wsmem),
+                         "occupancy")) != COPA_OK)
+      return st;
+    wblocks = (int64_t)h->num_sms * std::max(wper_sm, 1);
+    const int64_t need = (X.K + kWNT / 32 - 1) / (kWNT / 32);
+    if (wblocks > need) wblocks = std::max<int64_t>(need, 1);
+  }
   const int64_t* order = nullptr;
   if ((st = get_schedule(h, X, &order)) != COPA_OK) return st;
+  const int* split = wkern ? schedule_count_above(h, std::min(R, 32)) : nullptr;
   int* counter = nullptr;
   if ((st = ws_get(h, SLOT_COUNTER, 64, (void**)&counter)) != COPA_OK) return st;
   unsigned long long* fma_count = reinterpret_cast<unsigned long long*>(counter + 2);
+  const int64_t nparts = blocks + wblocks * (kWNT / 32);
   double* part = nullptr;
   if (F_H) {
-    if ((st = ws_get(h, SLOT_PARTIAL, (size_t)blocks * R * R * sizeof(double), (void**)&part)) != COPA_OK)
+    if ((st = ws_get(h, SLOT_PARTIAL, (size_t)nparts * R * R * sizeof(double), (void**)&part)) != COPA_OK)
       return st;
   }
-  if ((st = cuda_check(h, cudaMemsetAsync(counter, 0, 16, h->stream), "memset")) != COPA_OK)
+  // counter[0]: block kernel, [2..3]: work tally, [4]: warp kernel
+  if ((st = cuda_check(h, cudaMemsetAsync(counter, 0, 32, h->stream), "memset")) != COPA_OK)
     return st;
   k_procrustes<Real><<<(unsigned)blocks, kNT, smem, h->stream>>>(X, R, H, V, W, tau, Q, T, Pi, rank, part,
                                                                 order, counter, fma_count, Uw, woff,
-                                                                warm_in ? 1 : 0);
+                                                                warm_in ? 1 : 0, split);
   if ((st = cuda_check(h, cudaGetLastError(), "k_procrustes launch")) != COPA_OK) return st;
+  if (wkern) {
+    wkern<<<(unsigned)wblocks, kWNT, wsmem, h->stream>>>(
+        X, R, H, V, W, tau, Q, T, Pi, rank, part ? part + (size_t)blocks * R * R : nullptr, order, split,
+        counter + 4, fma_count, Uw, woff, warm_in ? 1 : 0, h->d_status);
+    if ((st = cuda_check(h, cudaGetLastError(), "k_procrustes_warp launch")) != COPA_OK) return st;
+  }
   if (F_H) {
-    k_reduce_partials<Real><<<(R * R + 255) / 256, 256, 0, h->stream>>>(part, (int)blocks, R * R, F_H);
+    k_reduce_partials<Real><<<(R * R + 255) / 256, 256, 0, h->stream>>>(part, (int)nparts, R * R, F_H);
     if ((st = cuda_check(h, cudaGetLastError(), "k_reduce_partials launch")) != COPA_OK) return st;
   }
   return COPA_OK;

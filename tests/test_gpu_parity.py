@@ -70,6 +70,8 @@ CASES = [
     (120, 60, 12, 10, 1, 40),
     (60, 90, 40, 25, 1, 120),
     (40, 50, 7, 6, 1, 20),     # odd R
+    (80, 70, 32, 20, 1, 60),   # R = 32: every subject with I_k <= R on the warp path
+    (90, 50, 20, 12, 1, 45),   # rows padded from 20 to 24 components
 ]
 
 

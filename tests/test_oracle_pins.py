@@ -13,7 +13,7 @@ from oracle import copa_oracle as O
 
 
 # ---------------------------------------------------------------------------------
-# Procrustes (Eq. solv_Q): pseudo-polar factor
+# Procrustes (Eq. 5): pseudo-polar factor
 # ---------------------------------------------------------------------------------
 
 def _A(Xk, V, w, H):
@@ -43,7 +43,7 @@ def test_procrustes_wide_case_has_orthonormal_rows():
 
 
 def test_procrustes_maximises_trace_and_nuclear_norm():
-    """tr(Q^T A) = ||A||_* and no orthonormal Q' does better (Eq. solv_Q)."""
+    """tr(Q^T A) = ||A||_* and no orthonormal Q' does better (Eq. 5)."""
     rng = np.random.default_rng(2)
     Ik, J, R = 9, 8, 4
     Xk, V, H = rng.random((Ik, J)), rng.random((J, R)), rng.random((R, R))
@@ -232,7 +232,7 @@ def test_admm_l1_satisfies_lasso_kkt():
 def test_unconstrained_mode_updates_are_exact_cp_als():
     """With c = none and many inner iterations, every mode update is the least-squares
     solution of the matricized CP problem given the CURRENT other factors, computed
-    here by lstsq on the explicit Khatri-Rao product (Sec. 3.1 and Eq. Solve_W)."""
+    here by lstsq on the explicit Khatri-Rao product (Sec. 3.1 and Eq. 8)."""
     X, _ = synth.planted_small(K=8, J=12, R=3, seed=1)
     H0, V0, W0 = synth.random_state(X.K, X.J, 3, seed=4)
     W0 = W0 + 0.1

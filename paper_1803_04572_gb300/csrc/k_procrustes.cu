@@ -192,11 +192,11 @@ __device__ void tsqr_block(Real* Z, int ld, int R, int nb, Real* vb, Real* misc)
 template <typename Real>
 __global__ void __launch_bounds__(kNT) k_procrustes(
     TensorView X, int R, const Real* __restrict__ H, const Real* __restrict__ V,
-    const Real* __restrict__ W, double tau_rank, Real* __restrict__ Q, Real* __restrict__ T,
+    const Real* __restrict__ W, double tau_rank, Real* __restrict__ Q, Real* T,
     Real* __restrict__ Pi, int32_t* __restrict__ rank, double* __restrict__ fh_partial,
     const int64_t* __restrict__ order, int* __restrict__ counter,
     unsigned long long* __restrict__ fma_count, Real* __restrict__ Uw,
-    const int64_t* __restrict__ woff, int warm_in, const int* __restrict__ limit) {
+    const int64_t* __restrict__ woff, int warm_in, const int* __restrict__ limit, int tall_split) {
   extern __shared__ unsigned char smem_raw[];
   Real* sm = reinterpret_cast<Real*>(smem_raw);
   const Lay L = lay_of<Real>(R);
@@ -233,26 +233,29 @@ __global__ void __launch_bounds__(kNT) k_procrustes(
     const int64_t Ik64 = r1 - r0;
     const bool wide = Ik64 <= R;
     const int m = wide ? (int)Ik64 : R;
+    // split tall subject: R_A comes from the QR kernel (in T_k), Omega goes back there
+    const bool split = !wide && tall_split != 0;
     if (tid == 0) {
       const unsigned long long nnzk = (unsigned long long)(X.row_ptr[r1] - X.row_ptr[r0]);
       const unsigned long long ik = (unsigned long long)Ik64, RR = (unsigned long long)R * R;
-      fma += nnzk * R + ik * RR + 2ull * m * R;
-      if (!wide) fma += ik * RR + nnzk * R + 3 * ik * RR + 2 * RR * R;
-      else fma += 2ull * m * m * R + 2ull * RR * m;
+      fma += 2ull * m * R;
+      if (wide) fma += nnzk * R + ik * RR + 2ull * m * m * R + 2ull * RR * m;
+      else if (split) fma += 2 * RR * R;
+      else fma += 2 * nnzk * R + 5 * ik * RR + 2 * RR * R;
     }
 
-    // ---- E = S_k H^T; tall: clear R_A ----
+    // ---- E = S_k H^T; tall: clear R_A (or load it, split) ----
     for (int e = tid; e < R * R; e += kNT) {
       const int r = e / R, t = e - r * R;
       Es[r * ld + t] = W[k * R + r] * __ldg(H + t * R + r);
-      if (!wide) Zb[r * ld + t] = Real(0);
+      if (!wide) Zb[r * ld + t] = split ? __ldcg(T + k * R * R + e) : Real(0);   // R_A from the QR launch
     }
     __syncthreads();
 
     // ---- pass 1: rows four at a time, a_i = (x_i V) E; wide: keep p_i and a_i;
     //      tall: fill a QR block of up to R rows, then fold it into R_A ----
     int nb = 0;   // rows in the QR block (tall); always < R before a group
-    for (int64_t g = r0; g < r1;) {
+    for (int64_t g = r0; g < (split ? r0 : r1);) {
       int nrow = (int)min((int64_t)kNW, r1 - g);
       if (!wide && nrow > R - nb) nrow = R - nb;   // the block holds at most R rows
       const int64_t i = g + warp;
@@ -429,8 +432,10 @@ __global__ void __launch_bounds__(kNT) k_procrustes(
         Pb[r * ld + t] = acc;
         if (Pi) Pi[k * R * R + e] = pacc;
         Ub[r * ld + t] = Real(0);
+        if (split) T[k * R * R + e] = acc;
       }
       __syncthreads();
+      if (split) continue;
       // pass 2, rows four at a time: q_i = (p_i E) Omega; T_k += q_i^T p_i
       for (int64_t g = r0; g < r1; g += kNW) {
         const int64_t i = g + warp;
@@ -474,16 +479,47 @@ __global__ void __launch_bounds__(kNT) k_procrustes(
 // products. Pairs follow the circle method on n2 = m + (m & 1) positions: position n2-1
 // meets position r in round r, every other position i meets (2r - i) mod (n2 - 1).
 // Rows are zero-padded to kR components (R rounded up to a multiple of 8); padding stays 0
-// under the rotations. Outputs are the same as the block path's wide branch.
+// under the rotations. Shared-memory rows have a 16-byte aligned stride, so that the
+// warp-wide (broadcast) row reads are vector loads; the stride is chosen so that the
+// lane-per-row vector stores of a quarter warp fall in distinct banks.
+// Outputs are the same as the block path's wide branch.
 constexpr int kWNT = 128;   // threads per block of the warp path (4 subjects at a time)
+
+template <typename Real>
+struct Vec16;   // 16-byte vector of Real
+template <>
+struct Vec16<float> {
+  using T = float4;
+  static constexpr int n = 4;
+  static __device__ __forceinline__ void ld(const float* p, float* o) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+  static __device__ __forceinline__ void st(float* p, const float* o) {
+    *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+  }
+};
+template <>
+struct Vec16<double> {
+  using T = double2;
+  static constexpr int n = 2;
+  static __device__ __forceinline__ void ld(const double* p, double* o) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    o[0] = v.x; o[1] = v.y;
+  }
+  static __device__ __forceinline__ void st(double* p, const double* o) {
+    *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+  }
+};
 
 template <typename Real, int kR>
 struct WarpLay {
   static constexpr int kM = kR < 32 ? kR : 32;   // rows of a subject on this path
-  static constexpr int ld = kR + 1;              // odd: lane-per-row stores are conflict-free
-  static constexpr int ldu = kM + 1;
-  static constexpr int per_warp = 2 * kM * ld + kM * ldu;
-  static constexpr size_t bytes = sizeof(Real) * ((size_t)kR * kR + (kWNT / 32) * (size_t)per_warp);
+  static constexpr int VN = Vec16<Real>::n;
+  static constexpr int ld = kR + VN;             // row stride of the row buffers
+  static constexpr int ldu = kM + 1;             // U: odd stride, read by columns
+  static constexpr int per_warp = 2 * kM * ld + kM * ldu + VN;
+  static constexpr size_t bytes = sizeof(Real) * ((size_t)kR * kR + (kWNT / 32) * (size_t)per_warp) + 16;
 };
 
 template <typename Real, int kR>
@@ -495,17 +531,18 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
     unsigned long long* __restrict__ fma_count, Real* __restrict__ Uw,
     const int64_t* __restrict__ woff, int warm_in, int* __restrict__ status) {
   using Lw = WarpLay<Real, kR>;
-  constexpr int kM = Lw::kM, ld = Lw::ld, ldu = Lw::ldu;
+  using Vc = Vec16<Real>;
+  constexpr int kM = Lw::kM, ld = Lw::ld, ldu = Lw::ldu, VN = Lw::VN;
   constexpr int kTR = kR / 8, kTC = kR / 4;   // T tile of a lane: 8 x 4 lanes cover kR x kR
   constexpr unsigned kFull = 0xffffffffu;
-  extern __shared__ unsigned char smem_raw[];
-  Real* Hs = reinterpret_cast<Real*>(smem_raw);   // Hs[t * kR + r] = H(t, r), zero-padded
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* Hs = reinterpret_cast<Real*>(smem_raw);   // Hs[r * kR + t] = H(t, r), zero-padded
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   Real* B1 = Hs + kR * kR + (size_t)warp * Lw::per_warp;   // A rows, then c_j rows
   Real* B2 = B1 + kM * ld;                                  // p rows, then b = U P rows
   Real* Us = B2 + kM * ld;                                  // U, for its transpose
   for (int e = threadIdx.x; e < kR * kR; e += kWNT) {
-    const int t = e / kR, r = e - t * kR;
+    const int r = e / kR, t = e - r * kR;
     Hs[e] = (t < R && r < R) ? H[t * R + r] : Real(0);
   }
   __syncthreads();
@@ -550,7 +587,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
     }
     if (lane < kM) {
 #pragma unroll
-      for (int t = 0; t < kR; ++t) B2[lane * ld + t] = p[t];
+      for (int t = 0; t < kR; t += VN) Vc::st(B2 + lane * ld + t, p + t);
     }
     __syncwarp();
     Real z[kR];
@@ -561,7 +598,12 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
       for (int r = 0; r < R; ++r) {
         const Real pw = B2[lane * ld + r] * wk[r];
 #pragma unroll
-        for (int t = 0; t < kR; ++t) z[t] += pw * Hs[t * kR + r];
+        for (int t = 0; t < kR; t += VN) {
+          Real hv[VN];
+          Vc::ld(Hs + r * kR + t, hv);
+#pragma unroll
+          for (int q = 0; q < VN; ++q) z[t + q] += pw * hv[q];
+        }
       }
     }
 
@@ -574,7 +616,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
     if (warm) {
       if (lane < kM) {
 #pragma unroll
-        for (int t = 0; t < kR; ++t) B1[lane * ld + t] = z[t];
+        for (int t = 0; t < kR; t += VN) Vc::st(B1 + lane * ld + t, z + t);
       }
       __syncwarp();
 #pragma unroll
@@ -584,7 +626,12 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
         for (int j = 0; j < m; ++j) {
           const Real uij = Uk[lane * m + j];
 #pragma unroll
-          for (int t = 0; t < kR; ++t) z[t] += uij * B1[j * ld + t];
+          for (int t = 0; t < kR; t += VN) {
+            Real av[VN];
+            Vc::ld(B1 + j * ld + t, av);
+#pragma unroll
+            for (int q = 0; q < VN; ++q) z[t + q] += uij * av[q];
+          }
         }
 #pragma unroll
         for (int j = 0; j < kM; ++j)
@@ -614,16 +661,15 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
           else if (j >= n2 - 1) j -= n2 - 1;
         }
         Real zp[kR];
-        Real g0 = Real(0), g1 = Real(0);
+        Real g[4] = {Real(0), Real(0), Real(0), Real(0)};
 #pragma unroll
         for (int t = 0; t < kR; ++t) {
           zp[t] = __shfl_sync(kFull, z[t], j);
-          if (t & 1) g1 += z[t] * zp[t];
-          else g0 += z[t] * zp[t];
+          g[t & 3] += z[t] * zp[t];
         }
         const Real be = __shfl_sync(kFull, al, j);
         const bool lo = lane < j;
-        const Real aa = lo ? al : be, bb = lo ? be : al, gg = g0 + g1;
+        const Real aa = lo ? al : be, bb = lo ? be : al, gg = (g[0] + g[1]) + (g[2] + g[3]);
         const bool rot = j != lane && gg != Real(0) && fabs(gg) > tol * sqrt(aa * bb);
         const unsigned rmask = __ballot_sync(kFull, rot);
         if (rmask == 0u) continue;
@@ -640,18 +686,22 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
         }
         // lower row x, upper row y: x' = c x - s y, y' = s x + c y
         const Real so = lo ? -s : s;
-        Real na = Real(0);
+        Real na[4] = {Real(0), Real(0), Real(0), Real(0)};
 #pragma unroll
         for (int t = 0; t < kR; ++t) {
           z[t] = c * z[t] + so * zp[t];
-          na += z[t] * z[t];
+          na[t & 3] += z[t] * z[t];
         }
-        if (rot) al = na;
+        if (rot) al = (na[0] + na[1]) + (na[2] + na[3]);
+        // U rows, in chunks of 8 entries up to m
 #pragma unroll
-        for (int jj = 0; jj < kM; ++jj) {
-          if (jj < m) {
-            const Real up = __shfl_sync(kFull, u[jj], j);
-            u[jj] = c * u[jj] + so * up;
+        for (int c8 = 0; c8 < kM; c8 += 8) {
+          if (c8 < m) {
+#pragma unroll
+            for (int jj = c8; jj < c8 + 8; ++jj) {
+              const Real up = __shfl_sync(kFull, u[jj], j);
+              u[jj] = c * u[jj] + so * up;
+            }
           }
         }
       }
@@ -671,7 +721,9 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
     const Real inv = keep ? rsqrt_(al) : Real(0);
     if (lane < kM) {
 #pragma unroll
-      for (int t = 0; t < kR; ++t) B1[lane * ld + t] = z[t] * inv;
+      for (int t = 0; t < kR; ++t) z[t] *= inv;
+#pragma unroll
+      for (int t = 0; t < kR; t += VN) Vc::st(B1 + lane * ld + t, z + t);
 #pragma unroll
       for (int jj = 0; jj < kM; ++jj) Us[lane * ldu + jj] = u[jj];
     }
@@ -685,9 +737,15 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
       for (int jj = 0; jj < m; ++jj) {
         const Real uji = Us[jj * ldu + lane], uij = Us[lane * ldu + jj];
 #pragma unroll
-        for (int t = 0; t < kR; ++t) {
-          z[t] += uji * B1[jj * ld + t];
-          p[t] += uij * B2[jj * ld + t];
+        for (int t = 0; t < kR; t += VN) {
+          Real cv[VN], pv[VN];
+          Vc::ld(B1 + jj * ld + t, cv);
+          Vc::ld(B2 + jj * ld + t, pv);
+#pragma unroll
+          for (int q = 0; q < VN; ++q) {
+            z[t + q] += uji * cv[q];
+            p[t + q] += uij * pv[q];
+          }
         }
       }
     }
@@ -700,7 +758,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
     }
     if (lane < kM) {
 #pragma unroll
-      for (int t = 0; t < kR; ++t) B2[lane * ld + t] = p[t];
+      for (int t = 0; t < kR; t += VN) Vc::st(B2 + lane * ld + t, p + t);
     }
     __syncwarp();
 
@@ -732,7 +790,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
             const int s = tc * kTC + b;
             if (s < R) {
               Tk[r * R + s] = acc[a][b];
-              if (fh) fh[r * R + s] += (double)acc[a][b] * (double)W[k * R + s];
+              if (fh) fh[r * R + s] += (double)acc[a][b] * (double)wk[s];
             }
           }
         }
@@ -782,6 +840,303 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
   if (fma_count && lane == 0) atomicAdd(fma_count, fma);
 }
 
+// ---- tall subjects (I_k > R), split in three launches around the block kernel ----
+// k_tall_qr: warp per subject; the rows of A_k = X_k V S_k H^T are formed 32 at a time
+// (lane = row) and folded into R_A by Householder reflections on the stacked [R_A; block]
+// (lane = column, the block's columns in registers, each reflector broadcast by shuffles).
+// R_A goes to T_k. The block kernel then runs the Jacobi on R_A and leaves
+// Omega = C_K Sigma_K^{-1} C_K^T in T_k; k_tall_pass2 (warp per subject, lane = row)
+// recomputes the rows, writes q_i = a_i Omega and accumulates T_k = sum_i q_i^T p_i and
+// the F_H partial sums. Same arithmetic as the block kernel's tall branch.
+template <typename Real, int kR>
+struct TallLay {
+  static constexpr int VN = Vec16<Real>::n;
+  static constexpr int ldb = kR + VN;   // row blocks (lane-per-row vector stores)
+  static constexpr int ldr = kR + 1;    // R_A (read by columns)
+  static constexpr int per_warp = 2 * 32 * ldb + kR * ldb + VN;   // pass 2: p and a/q blocks, Omega
+  static constexpr int per_warp_qr = 32 * ldb + kR * ldb + VN;     // QR: one row block, R_A
+  static constexpr size_t bytes = sizeof(Real) * ((size_t)kR * kR + (kWNT / 32) * (size_t)per_warp) + 16;
+  static constexpr size_t qr_bytes = sizeof(Real) * ((size_t)kR * kR + (kWNT / 32) * (size_t)per_warp_qr) + 16;
+};
+
+// p_i = x_i V into the registers of the lane owning row i (rows past the block: 0), then
+// a_i = (p_i * w) H^T from the p row kept in shared memory. Returns the row's nonzeros.
+template <typename Real, int kR>
+__device__ __forceinline__ int tall_row(const TensorView& X, int R, const Real* __restrict__ V, const Real* Hs,
+                                        const Real* __restrict__ wk, int64_t i, bool valid, Real* prow, Real* z) {
+  using Vc = Vec16<Real>;
+  constexpr int VN = Vc::n;
+  Real p[kR];
+#pragma unroll
+  for (int t = 0; t < kR; ++t) p[t] = Real(0);
+  int nnz = 0;
+  if (valid) {
+    const int64_t a = X.row_ptr[i], b = X.row_ptr[i + 1];
+    nnz = (int)(b - a);
+    for (int64_t q = a; q < b; ++q) {
+      const Real x = load_x<Real>(X, q);
+      const Real* vr = V + (int64_t)__ldg(X.col + q) * R;
+#pragma unroll
+      for (int t = 0; t < kR; ++t)
+        if (t < R) p[t] += x * __ldg(vr + t);
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < kR; t += VN) Vc::st(prow + t, p + t);
+#pragma unroll
+  for (int t = 0; t < kR; ++t) z[t] = Real(0);
+  if (valid) {
+#pragma unroll 1
+    for (int r = 0; r < R; ++r) {
+      const Real pw = prow[r] * wk[r];
+#pragma unroll
+      for (int t = 0; t < kR; t += VN) {
+        Real hv[VN];
+        Vc::ld(Hs + r * kR + t, hv);
+#pragma unroll
+        for (int q = 0; q < VN; ++q) z[t + q] += pw * hv[q];
+      }
+    }
+  }
+  return nnz;
+}
+
+template <typename Real, int kR>
+__device__ __forceinline__ void load_hs(const Real* __restrict__ H, int R, Real* Hs) {
+  for (int e = threadIdx.x; e < kR * kR; e += kWNT) {
+    const int r = e / kR, t = e - r * kR;
+    Hs[e] = (t < R && r < R) ? H[t * R + r] : Real(0);   // Hs[r * kR + t] = H(t, r)
+  }
+}
+
+template <typename Real, int kR>
+__global__ void __launch_bounds__(kWNT, 3) k_tall_qr(
+    TensorView X, int R, const Real* __restrict__ H, const Real* __restrict__ V, const Real* __restrict__ W,
+    const int64_t* __restrict__ order, const int* __restrict__ count, int* __restrict__ counter,
+    Real* __restrict__ T, unsigned long long* __restrict__ fma_count) {
+  using Lt = TallLay<Real, kR>;
+  using Vc = Vec16<Real>;
+  constexpr int ldb = Lt::ldb, ldr = Lt::ldr, VN = Lt::VN;
+  constexpr int kC2 = kR > 32 ? kR - 32 : 1;   // second columns (lanes 0 .. kR-33)
+  constexpr unsigned kFull = 0xffffffffu;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* Hs = reinterpret_cast<Real*>(smem_raw);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Real* Bs = Hs + kR * kR + (size_t)warp * Lt::per_warp_qr;   // 32 rows of A_k
+  Real* Rs = Bs + 32 * ldb;                                     // R_A
+  load_hs<Real, kR>(H, R, Hs);
+  __syncthreads();
+  const int64_t nt = min((int64_t)max(*count, 0), X.K);
+  unsigned long long fma = 0;
+
+  while (true) {
+    int claim = 0;
+    if (lane == 0) claim = atomicAdd(counter, 1);
+    const int64_t idx = __shfl_sync(kFull, claim, 0);
+    if (idx >= nt) break;
+    const int64_t k = order[idx];
+    const int64_t r0 = X.subj_ptr[k], r1 = X.subj_ptr[k + 1];
+    const Real* wk = W + k * R;
+    for (int e = lane; e < kR * ldr; e += 32) Rs[e] = Real(0);
+    int nnzk = 0;
+    for (int64_t g = r0; g < r1; g += 32) {
+      const int nb = (int)min((int64_t)32, r1 - g);
+      Real z[kR];
+      nnzk += tall_row<Real, kR>(X, R, V, Hs, wk, g + lane, lane < nb, Bs + lane * ldb, z);
+#pragma unroll
+      for (int t = 0; t < kR; t += VN) Vc::st(Bs + lane * ldb + t, z + t);
+      __syncwarp();
+      // block columns: c1 = lane, c2 = 32 + lane
+      Real bc[32], bc2[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        bc[i] = lane < kR ? Bs[i * ldb + lane] : Real(0);
+        bc2[i] = (kR > 32 && lane < kC2) ? Bs[i * ldb + 32 + lane] : Real(0);
+      }
+      __syncwarp();
+      for (int j = 0; j < R; ++j) {
+        const int jl = j & 31;
+        const bool second = j >= 32;
+        Real s4[4] = {Real(0), Real(0), Real(0), Real(0)};
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const Real v = second ? bc2[i] : bc[i];
+          s4[i & 3] += v * v;
+        }
+        const Real ss = __shfl_sync(kFull, (s4[0] + s4[1]) + (s4[2] + s4[3]), jl);
+        const Real x0 = Rs[j * ldr + j];
+        Real tau = Real(0), scale = Real(0), beta = x0;
+        if (ss > Real(0)) {
+          const Real nrm = sqrt(x0 * x0 + ss);
+          beta = x0 >= Real(0) ? -nrm : nrm;
+          tau = (beta - x0) / beta;
+          scale = Real(1) / (x0 - beta);
+        }
+        if (tau != Real(0)) {
+          Real v[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i) v[i] = __shfl_sync(kFull, second ? bc2[i] : bc[i], jl) * scale;
+          if (lane > j && lane < R) {
+            Real d4[4] = {Rs[j * ldr + lane], Real(0), Real(0), Real(0)};
+#pragma unroll
+            for (int i = 0; i < 32; ++i) d4[i & 3] += v[i] * bc[i];
+            const Real w = ((d4[0] + d4[1]) + (d4[2] + d4[3])) * tau;
+            Rs[j * ldr + lane] -= w;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) bc[i] -= w * v[i];
+          }
+          if (kR > 32 && 32 + lane > j && 32 + lane < R) {
+            Real d4[4] = {Rs[j * ldr + 32 + lane], Real(0), Real(0), Real(0)};
+#pragma unroll
+            for (int i = 0; i < 32; ++i) d4[i & 3] += v[i] * bc2[i];
+            const Real w = ((d4[0] + d4[1]) + (d4[2] + d4[3])) * tau;
+            Rs[j * ldr + 32 + lane] -= w;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) bc2[i] -= w * v[i];
+          }
+          if (lane == jl) {   // the block's column j is annihilated
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              if (second) bc2[i] = Real(0);
+              else bc[i] = Real(0);
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) Rs[j * ldr + j] = beta;
+        __syncwarp();
+      }
+    }
+    Real* Tk = T + k * R * R;
+    for (int e = lane; e < R * R; e += 32) {
+      const int r = e / R, t = e - r * R;
+      Tk[e] = Rs[r * ldr + t];
+    }
+    __syncwarp();
+    if (fma_count) {
+      const int nz = __reduce_add_sync(kFull, nnzk);
+      if (lane == 0) {
+        const unsigned long long ik = (unsigned long long)(r1 - r0), RR = (unsigned long long)R * R;
+        fma += (unsigned long long)nz * R + 2ull * ik * RR;
+      }
+    }
+  }
+  if (fma_count && lane == 0) atomicAdd(fma_count, fma);
+}
+
+template <typename Real, int kR>
+__global__ void __launch_bounds__(kWNT, 3) k_tall_pass2(
+    TensorView X, int R, const Real* __restrict__ H, const Real* __restrict__ V, const Real* __restrict__ W,
+    const int64_t* __restrict__ order, const int* __restrict__ count, int* __restrict__ counter,
+    Real* __restrict__ Q, Real* T, double* __restrict__ fh_partial, unsigned long long* __restrict__ fma_count) {
+  using Lt = TallLay<Real, kR>;
+  using Vc = Vec16<Real>;
+  constexpr int ldb = Lt::ldb, VN = Lt::VN;
+  constexpr int kTR = kR / 8, kTC = kR / 4;
+  constexpr unsigned kFull = 0xffffffffu;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* Hs = reinterpret_cast<Real*>(smem_raw);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Real* Bp = Hs + kR * kR + (size_t)warp * Lt::per_warp;   // p rows of a block
+  Real* Ba = Bp + 32 * ldb;                                 // a rows, then q rows
+  Real* Om = Ba + 32 * ldb;                                 // Omega (kR x ldb, zero-padded)
+  load_hs<Real, kR>(H, R, Hs);
+  __syncthreads();
+  double* fh = fh_partial ? fh_partial + ((size_t)blockIdx.x * (kWNT / 32) + warp) * R * R : nullptr;
+  if (fh)
+    for (int e = lane; e < R * R; e += 32) fh[e] = 0.0;
+  const int64_t nt = min((int64_t)max(*count, 0), X.K);
+  const int tr = lane >> 2, tc = lane & 3;
+  unsigned long long fma = 0;
+
+  while (true) {
+    int claim = 0;
+    if (lane == 0) claim = atomicAdd(counter, 1);
+    const int64_t idx = __shfl_sync(kFull, claim, 0);
+    if (idx >= nt) break;
+    const int64_t k = order[idx];
+    const int64_t r0 = X.subj_ptr[k], r1 = X.subj_ptr[k + 1];
+    const Real* wk = W + k * R;
+    Real* Tk = T + k * R * R;
+    // Omega was written by the previous launch: read it through L2
+    for (int r = 0; r < kR; ++r)
+      for (int t = lane; t < ldb; t += 32) Om[r * ldb + t] = (r < R && t < R) ? __ldcg(Tk + r * R + t) : Real(0);
+    __syncwarp();
+    Real acc[kTR][kTC];
+#pragma unroll
+    for (int a = 0; a < kTR; ++a)
+#pragma unroll
+      for (int b = 0; b < kTC; ++b) acc[a][b] = Real(0);
+    int nnzk = 0;
+    for (int64_t g = r0; g < r1; g += 32) {
+      const int nb = (int)min((int64_t)32, r1 - g);
+      Real z[kR];
+      nnzk += tall_row<Real, kR>(X, R, V, Hs, wk, g + lane, lane < nb, Bp + lane * ldb, z);
+#pragma unroll
+      for (int t = 0; t < kR; t += VN) Vc::st(Ba + lane * ldb + t, z + t);
+      // q_i = a_i Omega (own row of Ba, rows of Omega broadcast)
+#pragma unroll
+      for (int t = 0; t < kR; ++t) z[t] = Real(0);
+#pragma unroll 1
+      for (int r = 0; r < R; ++r) {
+        const Real ar = Ba[lane * ldb + r];
+#pragma unroll
+        for (int t = 0; t < kR; t += VN) {
+          Real ov[VN];
+          Vc::ld(Om + r * ldb + t, ov);
+#pragma unroll
+          for (int q = 0; q < VN; ++q) z[t + q] += ar * ov[q];
+        }
+      }
+      if (lane < nb) {
+        Real* qrow = Q + (g + lane) * R;
+#pragma unroll
+        for (int t = 0; t < kR; ++t)
+          if (t < R) qrow[t] = z[t];
+      }
+#pragma unroll
+      for (int t = 0; t < kR; t += VN) Vc::st(Ba + lane * ldb + t, z + t);
+      __syncwarp();
+      // T_k += sum_i q_i^T p_i over the block (rows past nb are zero)
+      for (int i = 0; i < nb; ++i) {
+        Real qr[kTR], ps[kTC];
+#pragma unroll
+        for (int a = 0; a < kTR; ++a) qr[a] = Ba[i * ldb + tr * kTR + a];
+#pragma unroll
+        for (int b = 0; b < kTC; ++b) ps[b] = Bp[i * ldb + tc * kTC + b];
+#pragma unroll
+        for (int a = 0; a < kTR; ++a)
+#pragma unroll
+          for (int b = 0; b < kTC; ++b) acc[a][b] += qr[a] * ps[b];
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int a = 0; a < kTR; ++a) {
+      const int r = tr * kTR + a;
+      if (r < R) {
+#pragma unroll
+        for (int b = 0; b < kTC; ++b) {
+          const int s = tc * kTC + b;
+          if (s < R) {
+            Tk[r * R + s] = acc[a][b];
+            if (fh) fh[r * R + s] += (double)acc[a][b] * (double)wk[s];
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (fma_count) {
+      const int nz = __reduce_add_sync(kFull, nnzk);
+      if (lane == 0) {
+        const unsigned long long ik = (unsigned long long)(r1 - r0), RR = (unsigned long long)R * R;
+        fma += (unsigned long long)nz * R + 3ull * ik * RR;
+      }
+    }
+  }
+  if (fma_count && lane == 0) atomicAdd(fma_count, fma);
+}
+
 template <typename Real>
 __global__ void k_reduce_partials(const double* __restrict__ part, int nparts, int n,
                                   Real* __restrict__ out) {
@@ -796,31 +1151,74 @@ template <typename Real>
 using WarpKernel = void (*)(TensorView, int, const Real*, const Real*, const Real*, double, Real*, Real*, Real*,
                             int32_t*, double*, const int64_t*, const int*, int*, unsigned long long*, Real*,
                             const int64_t*, int, int*);
-
-// Instantiation of the warp path for R padded to kr components, or nullptr where the
-// registers of a lane cannot hold a row (float: R <= 48, double: R <= 16).
 template <typename Real>
-WarpKernel<Real> warp_kernel_for(int kr, size_t* smem);
+using TallQrKernel = void (*)(TensorView, int, const Real*, const Real*, const Real*, const int64_t*, const int*, int*,
+                              Real*, unsigned long long*);
+template <typename Real>
+using TallPass2Kernel = void (*)(TensorView, int, const Real*, const Real*, const Real*, const int64_t*, const int*,
+                                 int*, Real*, Real*, double*, unsigned long long*);
+
+// The lane-per-row kernels for one padded width kR.
+template <typename Real>
+struct RowKernels {
+  WarpKernel<Real> small = nullptr;
+  TallQrKernel<Real> qr = nullptr;
+  TallPass2Kernel<Real> pass2 = nullptr;
+  size_t small_smem = 0, qr_smem = 0, tall_smem = 0;
+};
+
+template <typename Real, int KR>
+RowKernels<Real> row_kernels_of() {
+  RowKernels<Real> r;
+  r.small = k_procrustes_warp<Real, KR>;
+  r.qr = k_tall_qr<Real, KR>;
+  r.pass2 = k_tall_pass2<Real, KR>;
+  r.small_smem = WarpLay<Real, KR>::bytes;
+  r.qr_smem = TallLay<Real, KR>::qr_bytes;
+  r.tall_smem = TallLay<Real, KR>::bytes;
+  return r;
+}
+
+// Kernels for R padded to kr components; empty where the registers of a lane cannot hold
+// a row (float: R <= 48, double: R <= 16).
+template <typename Real>
+RowKernels<Real> row_kernels_for(int kr);
 template <>
-WarpKernel<float> warp_kernel_for<float>(int kr, size_t* smem) {
+RowKernels<float> row_kernels_for<float>(int kr) {
   switch (kr) {
-#define COPA_WARP_CASE(KR) \
-  case KR:                 \
-    *smem = WarpLay<float, KR>::bytes; \
-    return k_procrustes_warp<float, KR>;
-    COPA_WARP_CASE(8) COPA_WARP_CASE(16) COPA_WARP_CASE(24) COPA_WARP_CASE(32) COPA_WARP_CASE(40)
-    COPA_WARP_CASE(48)
-#undef COPA_WARP_CASE
-    default: return nullptr;
+    case 8: return row_kernels_of<float, 8>();
+    case 16: return row_kernels_of<float, 16>();
+    case 24: return row_kernels_of<float, 24>();
+    case 32: return row_kernels_of<float, 32>();
+    case 40: return row_kernels_of<float, 40>();
+    case 48: return row_kernels_of<float, 48>();
+    default: return RowKernels<float>{};
   }
 }
 template <>
-WarpKernel<double> warp_kernel_for<double>(int kr, size_t* smem) {
+RowKernels<double> row_kernels_for<double>(int kr) {
   switch (kr) {
-    case 8: *smem = WarpLay<double, 8>::bytes; return k_procrustes_warp<double, 8>;
-    case 16: *smem = WarpLay<double, 16>::bytes; return k_procrustes_warp<double, 16>;
-    default: return nullptr;
+    case 8: return row_kernels_of<double, 8>();
+    case 16: return row_kernels_of<double, 16>();
+    default: return RowKernels<double>{};
   }
+}
+
+// grid of a lane-per-row kernel: SMs x resident blocks, no more than the subjects need
+template <typename Kern>
+copa_status_t row_grid(copa_ctx* h, Kern kern, size_t smem, int64_t K, int64_t* blocks) {
+  copa_status_t st;
+  if ((st = cuda_check(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                       "cudaFuncSetAttribute")) != COPA_OK)
+    return st;
+  int per_sm = 0;
+  if ((st = cuda_check(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWNT, smem), "occupancy")) !=
+      COPA_OK)
+    return st;
+  *blocks = (int64_t)h->num_sms * std::max(per_sm, 1);
+  const int64_t need = (K + kWNT / 32 - 1) / (kWNT / 32);
+  if (*blocks > need) *blocks = std::max<int64_t>(need, 1);
+  return COPA_OK;
 }
 
 }  // namespace
@@ -830,6 +1228,11 @@ size_t procrustes_smem(int R) {
   return lay_of<Real>(R).total * sizeof(Real);
 }
 
+// Launch order (lane-per-row kernels available for this R and precision):
+//   k_tall_qr (I_k > R: R_A -> T_k), k_procrustes (I_k > min(R, 32): the Jacobi of the
+//   tall subjects on R_A -> Omega in T_k, the whole path for the remaining wide ones),
+//   k_tall_pass2 (I_k > R: Q rows, T_k, F_H), k_procrustes_warp (I_k <= min(R, 32)).
+// Otherwise k_procrustes takes every subject.
 template <typename Real>
 copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const Real* H,
                                 const Real* V, const Real* W, double tau, Real* Q, Real* T,
@@ -852,46 +1255,49 @@ copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const R
   int64_t blocks = (int64_t)h->num_sms * per_sm;
   if (blocks > X.K) blocks = X.K > 0 ? X.K : 1;
 
-  // Subjects with I_k <= min(R, 32) (the tail of the largest-first schedule) take the
-  // warp-per-subject kernel; the block kernel takes the prefix before them.
-  size_t wsmem = 0;
-  const WarpKernel<Real> wkern = warp_kernel_for<Real>((R + 7) / 8 * 8, &wsmem);
-  int64_t wblocks = 0;
-  if (wkern) {
-    if ((st = cuda_check(h, cudaFuncSetAttribute(wkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem),
-                         "cudaFuncSetAttribute")) != COPA_OK)
-      return st;
-    int wper_sm = 0;
-    if ((st = cuda_check(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wper_sm, wkern, kWNT, wsmem),
-                         "occupancy")) != COPA_OK)
-      return st;
-    wblocks = (int64_t)h->num_sms * std::max(wper_sm, 1);
-    const int64_t need = (X.K + kWNT / 32 - 1) / (kWNT / 32);
-    if (wblocks > need) wblocks = std::max<int64_t>(need, 1);
+  const RowKernels<Real> rk = row_kernels_for<Real>((R + 7) / 8 * 8);
+  const bool rows = rk.small != nullptr;
+  int64_t sblocks = 0, qblocks = 0, pblocks = 0;
+  if (rows) {
+    if ((st = row_grid(h, rk.small, rk.small_smem, X.K, &sblocks)) != COPA_OK) return st;
+    if ((st = row_grid(h, rk.qr, rk.qr_smem, X.K, &qblocks)) != COPA_OK) return st;
+    if ((st = row_grid(h, rk.pass2, rk.tall_smem, X.K, &pblocks)) != COPA_OK) return st;
   }
   const int64_t* order = nullptr;
   if ((st = get_schedule(h, X, &order)) != COPA_OK) return st;
-  const int* split = wkern ? schedule_count_above(h, std::min(R, 32)) : nullptr;
+  const int* n_big = rows ? schedule_count_above(h, std::min(R, 32)) : nullptr;   // I_k > min(R, 32)
+  const int* n_tall = rows ? schedule_count_above(h, R) : nullptr;                // I_k > R
   int* counter = nullptr;
   if ((st = ws_get(h, SLOT_COUNTER, 64, (void**)&counter)) != COPA_OK) return st;
   unsigned long long* fma_count = reinterpret_cast<unsigned long long*>(counter + 2);
-  const int64_t nparts = blocks + wblocks * (kWNT / 32);
+  const int64_t wpb = kWNT / 32;
+  const int64_t nparts = blocks + (sblocks + pblocks) * wpb;
   double* part = nullptr;
   if (F_H) {
     if ((st = ws_get(h, SLOT_PARTIAL, (size_t)nparts * R * R * sizeof(double), (void**)&part)) != COPA_OK)
       return st;
   }
-  // counter[0]: block kernel, [2..3]: work tally, [4]: warp kernel
+  // counter[0]: block kernel, [2..3]: work tally, [4]: small subjects, [5]: tall QR, [6]: tall pass 2
   if ((st = cuda_check(h, cudaMemsetAsync(counter, 0, 32, h->stream), "memset")) != COPA_OK)
     return st;
+  if (rows) {
+    rk.qr<<<(unsigned)qblocks, kWNT, rk.qr_smem, h->stream>>>(X, R, H, V, W, order, n_tall, counter + 5, T,
+                                                                  fma_count);
+    if ((st = cuda_check(h, cudaGetLastError(), "k_tall_qr launch")) != COPA_OK) return st;
+  }
   k_procrustes<Real><<<(unsigned)blocks, kNT, smem, h->stream>>>(X, R, H, V, W, tau, Q, T, Pi, rank, part,
                                                                 order, counter, fma_count, Uw, woff,
-                                                                warm_in ? 1 : 0, split);
+                                                                warm_in ? 1 : 0, n_big, rows ? 1 : 0);
   if ((st = cuda_check(h, cudaGetLastError(), "k_procrustes launch")) != COPA_OK) return st;
-  if (wkern) {
-    wkern<<<(unsigned)wblocks, kWNT, wsmem, h->stream>>>(
-        X, R, H, V, W, tau, Q, T, Pi, rank, part ? part + (size_t)blocks * R * R : nullptr, order, split,
-        counter + 4, fma_count, Uw, woff, warm_in ? 1 : 0, h->d_status);
+  if (rows) {
+    double* ppart = part ? part + (size_t)blocks * R * R : nullptr;
+    rk.pass2<<<(unsigned)pblocks, kWNT, rk.tall_smem, h->stream>>>(X, R, H, V, W, order, n_tall, counter + 6, Q, T,
+                                                                     ppart, fma_count);
+    if ((st = cuda_check(h, cudaGetLastError(), "k_tall_pass2 launch")) != COPA_OK) return st;
+    double* spart = part ? part + (size_t)(blocks + pblocks * wpb) * R * R : nullptr;
+    rk.small<<<(unsigned)sblocks, kWNT, rk.small_smem, h->stream>>>(
+        X, R, H, V, W, tau, Q, T, Pi, rank, spart, order, n_big, counter + 4, fma_count, Uw, woff,
+        warm_in ? 1 : 0, h->d_status);
     if ((st = cuda_check(h, cudaGetLastError(), "k_procrustes_warp launch")) != COPA_OK) return st;
   }
   if (F_H) {

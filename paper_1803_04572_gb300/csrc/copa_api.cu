@@ -135,8 +135,7 @@ __global__ void k_xnorm2(TensorView X, double* __restrict__ out) {
 __global__ void k_warm_sizes(const int64_t* __restrict__ subj_ptr, int64_t K, int R, int64_t* __restrict__ out) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K; k += gridDim.x * (int64_t)blockDim.x) {
     const int64_t ik = subj_ptr[k + 1] - subj_ptr[k];
-    const int64_t m = ik < R ? ik : R;
-    out[k] = m * m;
+    out[k] = ik <= R ? ik * ik : 0;   // tall subjects keep no rotation between iterations
   }
 }
 

@@ -396,6 +396,94 @@ __global__ void k_csc_scatter(TensorView X, const int64_t* __restrict__ cptr, in
   }
 }
 
+// Row-ordered form (every column lists its visit rows in ascending order up to a
+// permutation inside 32-row steps; the order depends only on X, so F_V is summed in a fixed
+// order and the gathers of a column walk U forward), for J <= kHistSmem: the visit rows
+// are cut into nb contiguous ranges, one warp each. k_csc_count counts the columns of
+// every range into rel[j * nb + b]; k_csc_colscan turns each column's counts into offsets
+// over the ranges and its total; k_csc_place walks every range again, 32 rows at a time
+// (lane = row, the rows' q-th nonzeros together), and puts each nonzero after the ones of
+// its column already placed (ranks among equal columns from __match_any_sync, a
+// shared-memory cursor per column).
+__device__ __forceinline__ void csc_range(int64_t S, int nb, int b, int64_t* lo, int64_t* hi) {
+  *lo = S * b / nb;
+  *hi = S * (b + 1) / nb;
+}
+
+__global__ void __launch_bounds__(32) k_csc_count(TensorView X, int nb, int* __restrict__ rel) {
+  extern __shared__ int cnt[];   // J counters
+  const int lane = threadIdx.x, b = blockIdx.x;
+  for (int j = lane; j < X.J; j += 32) cnt[j] = 0;
+  __syncwarp();
+  int64_t lo, hi;
+  csc_range(X.S, nb, b, &lo, &hi);
+  const int64_t t1 = X.row_ptr[hi];
+  for (int64_t t = X.row_ptr[lo] + lane; t < t1; t += 32) atomicAdd(&cnt[X.col[t]], 1);
+  __syncwarp();
+  for (int j = lane; j < X.J; j += 32) rel[(int64_t)j * nb + b] = cnt[j];
+}
+
+// one warp per column: exclusive scan of its range counts in place, column total -> tot[j]
+__global__ void k_csc_colscan(int J, int nb, int* __restrict__ rel, int64_t* __restrict__ tot) {
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= J) return;
+  int* r = rel + (int64_t)j * nb;
+  int run = 0;
+  for (int b0 = 0; b0 < nb; b0 += 32) {
+    const int v = b0 + lane < nb ? r[b0 + lane] : 0;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int n = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += n;
+    }
+    if (b0 + lane < nb) r[b0 + lane] = run + incl - v;
+    run += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (lane == 0) tot[j] = run;
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(32) k_csc_place(TensorView X, int nb, const int* __restrict__ rel,
+                                                  const int64_t* __restrict__ cptr, int32_t* __restrict__ crow,
+                                                  Real* __restrict__ cval) {
+  extern __shared__ int cur[];   // J cursors
+  const int lane = threadIdx.x, b = blockIdx.x;
+  for (int j = lane; j < X.J; j += 32) cur[j] = 0;
+  __syncwarp();
+  int64_t lo, hi;
+  csc_range(X.S, nb, b, &lo, &hi);
+  for (int64_t i0 = lo; i0 < hi; i0 += 32) {
+    const int64_t i = i0 + lane;
+    int64_t t = 0, e = 0;
+    if (i < hi) {
+      t = X.row_ptr[i];
+      e = X.row_ptr[i + 1];
+    }
+    int len = (int)(e - t);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, o));
+    for (int q = 0; q < len; ++q, ++t) {
+      const bool act = t < e;
+      const unsigned amask = __ballot_sync(0xffffffffu, act);
+      int c = 0;
+      unsigned peers = 0u;
+      if (act) {
+        c = X.col[t];
+        peers = __match_any_sync(amask, c);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        const int64_t pos = cptr[c] + rel[(int64_t)c * nb + b] + cur[c] + rank;
+        crow[pos] = (int32_t)i;
+        cval[pos] = load_x<Real>(X, t);
+      }
+      __syncwarp();
+      if (act && (peers >> lane) == 1u) cur[c] += __popc(peers);   // highest lane of its group
+      __syncwarp();
+    }
+  }
+}
+
 // subject of every visit row
 __global__ void k_row_subject(const int64_t* __restrict__ subj_ptr, int64_t K, int32_t* __restrict__ rs) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K; k += gridDim.x * (int64_t)blockDim.x)
@@ -712,8 +800,12 @@ static copa_status_t get_csc(copa_ctx* h, const TensorView& X, bool reuse, const
   int32_t* rs = nullptr;
   if (!(reuse && h->csc_key == X.col && h->csc_nnz == X.nnz && h->csc_J == X.J && h->csc_prec == prec &&
         h->csc_S == X.S && h->slot_ptr[SLOT_CSC])) {
+    // stable build: J fits the shared-memory counters and every count fits an int
+    const bool stable = X.J <= kHistSmem && X.nnz < (int64_t)INT32_MAX;
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(8192, X.S / 64));
+    const size_t rel_bytes = stable ? sizeof(int) * (size_t)X.J * nb + 16 : 0;
     const size_t bytes = sizeof(int64_t) * 2 * ((size_t)X.J + 1) + sizeof(int32_t) * (size_t)X.nnz +
-                         sizeof(Real) * (size_t)X.nnz + sizeof(int32_t) * (size_t)X.S + 64;
+                         sizeof(Real) * (size_t)X.nnz + sizeof(int32_t) * (size_t)X.S + 64 + rel_bytes;
     char* p = nullptr;
     if ((st = ws_get(h, SLOT_CSC, bytes, (void**)&p)) != COPA_OK) return st;
     layout(p, &ptr, &rows, &vals, &rs);
@@ -721,11 +813,21 @@ static copa_status_t get_csc(copa_ctx* h, const TensorView& X, bool reuse, const
     if ((st = cuda_check(h, cudaMemsetAsync(ptr, 0, sizeof(int64_t) * 2 * ((size_t)X.J + 1), h->stream),
                          "memset")) != COPA_OK)
       return st;
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((X.nnz + 255) / 256, (int64_t)h->num_sms * 8));
-    k_csc_hist<<<blocks, 256, 0, h->stream>>>(X, ptr);
-    k_scan_cols<<<1, 32, 0, h->stream>>>(ptr, X.J);
-    const int rblocks = (int)std::max<int64_t>(1, std::min<int64_t>((X.S + 255) / 256, (int64_t)h->num_sms * 16));
-    k_csc_scatter<Real><<<rblocks, 256, 0, h->stream>>>(X, ptr, cur, rows, vals);
+    if (stable) {
+      int* rel = reinterpret_cast<int*>(al16(reinterpret_cast<uintptr_t>(rs + X.S)));
+      const size_t jsm = sizeof(int) * (size_t)X.J;
+      k_csc_count<<<nb, 32, jsm, h->stream>>>(X, nb, rel);
+      k_csc_colscan<<<(X.J + 7) / 8, 256, 0, h->stream>>>(X.J, nb, rel, ptr);
+      k_scan_cols<<<1, 32, 0, h->stream>>>(ptr, X.J);
+      k_csc_place<Real><<<nb, 32, jsm, h->stream>>>(X, nb, rel, ptr, rows, vals);
+      h->setup_launches += 1;
+    } else {
+      const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((X.nnz + 255) / 256, (int64_t)h->num_sms * 8));
+      k_csc_hist<<<blocks, 256, 0, h->stream>>>(X, ptr);
+      k_scan_cols<<<1, 32, 0, h->stream>>>(ptr, X.J);
+      const int rblocks = (int)std::max<int64_t>(1, std::min<int64_t>((X.S + 255) / 256, (int64_t)h->num_sms * 16));
+      k_csc_scatter<Real><<<rblocks, 256, 0, h->stream>>>(X, ptr, cur, rows, vals);
+    }
     const int kblocks = (int)std::max<int64_t>(1, std::min<int64_t>((X.K + 255) / 256, (int64_t)h->num_sms * 16));
     k_row_subject<<<kblocks, 256, 0, h->stream>>>(X.subj_ptr, X.K, rs);
     if ((st = cuda_check(h, cudaGetLastError(), "csc build")) != COPA_OK) return st;

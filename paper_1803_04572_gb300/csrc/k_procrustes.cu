@@ -83,6 +83,20 @@ __device__ __forceinline__ int rr_next(int e, int n2) { return e == 0 ? 0 : (e =
 __device__ __forceinline__ float fdiv_(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double fdiv_(double a, double b) { return a / b; }
 
+// Jacobi rotation (c, s) that makes the pair with squared norms aa, bb and dot product gg
+// orthogonal: x' = c x - s y, y' = s x + c y.
+template <typename Real>
+__device__ __forceinline__ void rotation_of(Real aa, Real bb, Real gg, Real* c, Real* s) {
+  const Real zeta = fdiv_(bb - aa, Real(2) * gg);
+  Real tt;
+  if (fabs(zeta) > Real(1e15)) tt = fdiv_(Real(0.5), zeta);
+  else tt = fdiv_(zeta >= Real(0) ? Real(1) : Real(-1), fabs(zeta) + sqrt(Real(1) + zeta * zeta));
+  *c = rsqrt_(Real(1) + tt * tt);
+  *s = *c * tt;
+}
+
+constexpr int kEPL = 12;   // components per thread held in registers by the block Jacobi
+
 template <typename Real>
 __device__ __forceinline__ Real warp_sum_r(Real v) {
 #pragma unroll
@@ -190,7 +204,7 @@ __device__ void tsqr_block(Real* Z, int ld, int R, int nb, Real* vb, Real* misc)
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(kNT) k_procrustes(
+__global__ void __launch_bounds__(kNT, 5) k_procrustes(
     TensorView X, int R, const Real* __restrict__ H, const Real* __restrict__ V,
     const Real* __restrict__ W, double tau_rank, Real* __restrict__ Q, Real* T,
     Real* __restrict__ Pi, int32_t* __restrict__ rank, double* __restrict__ fh_partial,
@@ -280,9 +294,11 @@ __global__ void __launch_bounds__(kNT) k_procrustes(
 
     // ---- Hestenes one-sided Jacobi on rows 0..m-1 of Zb. U (Z = U A) is accumulated for
     //      wide subjects (it gives Q) and whenever a warm-start buffer is given; a warm
-    //      start begins from the previous outer iteration's U: Z = U_prev A. ----
-    const bool accU = wide || Uw != nullptr;
-    Real* Uk = Uw ? Uw + woff[k] : nullptr;
+    //      start begins from the previous outer iteration's U: Z = U_prev A. Tall subjects
+    //      need only Sigma and C (the rows of Z), so they keep no U: accumulating it would
+    //      cost more per sweep than a warm start saves in sweeps there. ----
+    const bool accU = wide;
+    Real* Uk = (wide && Uw) ? Uw + woff[k] : nullptr;
     if (accU) {
       for (int e = tid; e < m * m; e += kNT) {
         const int r = e / m, t = e - r * m;
@@ -311,6 +327,7 @@ __global__ void __launch_bounds__(kNT) k_procrustes(
     while (LP < 32 && npairs * LP * 2 <= kNT) LP <<= 1;
     const int pj = tid / LP, sl = tid % LP;
     const bool act = pj < npairs;
+    const bool few = (R + LP - 1) / LP <= kEPL && (m + LP - 1) / LP <= kEPL;
     for (int sweep = 0; sweep < kMaxSweeps && n2 > 1; ++sweep) {
       int nrot = 0;
       int e1 = act ? rr_elem(pj, 0, n2) : 0, e2 = act ? rr_elem(n2 - 1 - pj, 0, n2) : 0;
@@ -320,43 +337,87 @@ __global__ void __launch_bounds__(kNT) k_procrustes(
         e1 = rr_next(e1, n2);
         e2 = rr_next(e2, n2);
         const bool real_pair = act && jj < m;
-        Real aa = Real(0), bb = Real(0), gg = Real(0);
         Real* zi = Zb + ii * ld;
         Real* zj = Zb + jj * ld;
-        if (real_pair)
-          for (int t = sl; t < R; t += LP) {
-            const Real x = zi[t], y = zj[t];
-            aa += x * x;
-            bb += y * y;
-            gg += x * y;
+        if (few) {
+          // at most kEPL components per thread: keep them in registers for the update
+          Real xi[kEPL], xj[kEPL];
+          Real aa = Real(0), bb = Real(0), gg = Real(0);
+#pragma unroll
+          for (int q = 0; q < kEPL; ++q) {
+            const int t = sl + q * LP;
+            const bool in = real_pair && t < R;
+            xi[q] = in ? zi[t] : Real(0);
+            xj[q] = in ? zj[t] : Real(0);
+            aa += xi[q] * xi[q];
+            bb += xj[q] * xj[q];
+            gg += xi[q] * xj[q];
           }
-        // reduce over the LP threads of the pair (aligned groups inside one warp)
-        for (int o = LP >> 1; o > 0; o >>= 1) {
-          aa += __shfl_xor_sync(0xffffffffu, aa, o);
-          bb += __shfl_xor_sync(0xffffffffu, bb, o);
-          gg += __shfl_xor_sync(0xffffffffu, gg, o);
-        }
-        if (real_pair && gg != Real(0) && fabs(gg) > tol * sqrt(aa * bb)) {
-          const Real zeta = fdiv_(bb - aa, Real(2) * gg);
-          Real tt;
-          if (fabs(zeta) > Real(1e15)) tt = fdiv_(Real(0.5), zeta);
-          else tt = fdiv_(zeta >= Real(0) ? Real(1) : Real(-1), fabs(zeta) + sqrt(Real(1) + zeta * zeta));
-          const Real c = rsqrt_(Real(1) + tt * tt), s = c * tt;
-          for (int t = sl; t < R; t += LP) {
-            const Real x = zi[t], y = zj[t];
-            zi[t] = c * x - s * y;
-            zj[t] = s * x + c * y;
+          for (int o = LP >> 1; o > 0; o >>= 1) {
+            aa += __shfl_xor_sync(0xffffffffu, aa, o);
+            bb += __shfl_xor_sync(0xffffffffu, bb, o);
+            gg += __shfl_xor_sync(0xffffffffu, gg, o);
           }
-          if (accU) {
-            Real* ui = Ub + ii * ld;
-            Real* uj = Ub + jj * ld;
-            for (int t = sl; t < m; t += LP) {
-              const Real x = ui[t], y = uj[t];
-              ui[t] = c * x - s * y;
-              uj[t] = s * x + c * y;
+          if (real_pair && gg != Real(0) && fabs(gg) > tol * sqrt(aa * bb)) {
+            Real c, s;
+            rotation_of(aa, bb, gg, &c, &s);
+#pragma unroll
+            for (int q = 0; q < kEPL; ++q) {
+              const int t = sl + q * LP;
+              if (t < R) {
+                zi[t] = c * xi[q] - s * xj[q];
+                zj[t] = s * xi[q] + c * xj[q];
+              }
             }
+            if (accU) {
+              Real* ui = Ub + ii * ld;
+              Real* uj = Ub + jj * ld;
+#pragma unroll
+              for (int q = 0; q < kEPL; ++q) {
+                const int t = sl + q * LP;
+                if (t < m) {
+                  const Real x = ui[t], y = uj[t];
+                  ui[t] = c * x - s * y;
+                  uj[t] = s * x + c * y;
+                }
+              }
+            }
+            rotated = sl == 0;
           }
-          rotated = sl == 0;
+        } else {
+          Real aa = Real(0), bb = Real(0), gg = Real(0);
+          if (real_pair)
+            for (int t = sl; t < R; t += LP) {
+              const Real x = zi[t], y = zj[t];
+              aa += x * x;
+              bb += y * y;
+              gg += x * y;
+            }
+          // reduce over the LP threads of the pair (aligned groups inside one warp)
+          for (int o = LP >> 1; o > 0; o >>= 1) {
+            aa += __shfl_xor_sync(0xffffffffu, aa, o);
+            bb += __shfl_xor_sync(0xffffffffu, bb, o);
+            gg += __shfl_xor_sync(0xffffffffu, gg, o);
+          }
+          if (real_pair && gg != Real(0) && fabs(gg) > tol * sqrt(aa * bb)) {
+            Real c, s;
+            rotation_of(aa, bb, gg, &c, &s);
+            for (int t = sl; t < R; t += LP) {
+              const Real x = zi[t], y = zj[t];
+              zi[t] = c * x - s * y;
+              zj[t] = s * x + c * y;
+            }
+            if (accU) {
+              Real* ui = Ub + ii * ld;
+              Real* uj = Ub + jj * ld;
+              for (int t = sl; t < m; t += LP) {
+                const Real x = ui[t], y = uj[t];
+                ui[t] = c * x - s * y;
+                uj[t] = s * x + c * y;
+              }
+            }
+            rotated = sl == 0;
+          }
         }
         nrot += __syncthreads_count(rotated);
       }
@@ -676,14 +737,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
         any = true;
         if (lane == 0) nrot += __popc(rmask) / 2;
         Real c = Real(1), s = Real(0);
-        if (rot) {
-          const Real zeta = fdiv_(bb - aa, Real(2) * gg);
-          Real tt;
-          if (fabs(zeta) > Real(1e15)) tt = fdiv_(Real(0.5), zeta);
-          else tt = fdiv_(zeta >= Real(0) ? Real(1) : Real(-1), fabs(zeta) + sqrt(Real(1) + zeta * zeta));
-          c = rsqrt_(Real(1) + tt * tt);
-          s = c * tt;
-        }
+        if (rot) rotation_of(aa, bb, gg, &c, &s);
         // lower row x, upper row y: x' = c x - s y, y' = s x + c y
         const Real so = lo ? -s : s;
         Real na[4] = {Real(0), Real(0), Real(0), Real(0)};
@@ -851,10 +905,11 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
 template <typename Real, int kR>
 struct TallLay {
   static constexpr int VN = Vec16<Real>::n;
-  static constexpr int ldb = kR + VN;   // row blocks (lane-per-row vector stores)
+  static constexpr int ldb = kR + 1;    // row blocks: odd, so lane-per-row accesses are conflict-free
   static constexpr int ldr = kR + 1;    // R_A (read by columns)
-  static constexpr int per_warp = 2 * 32 * ldb + kR * ldb + VN;   // pass 2: p and a/q blocks, Omega
-  static constexpr int per_warp_qr = 32 * ldb + kR * ldb + VN;     // QR: one row block, R_A
+  static constexpr int pad = (2 * 32 * ldb + VN - 1) / VN * VN;   // keeps Omega 16-byte aligned
+  static constexpr int per_warp = pad + kR * kR;                  // pass 2: p and a/q blocks, Omega
+  static constexpr int per_warp_qr = (32 * ldb + kR * ldr + VN - 1) / VN * VN;   // QR: one row block, R_A
   static constexpr size_t bytes = sizeof(Real) * ((size_t)kR * kR + (kWNT / 32) * (size_t)per_warp) + 16;
   static constexpr size_t qr_bytes = sizeof(Real) * ((size_t)kR * kR + (kWNT / 32) * (size_t)per_warp_qr) + 16;
 };
@@ -882,7 +937,7 @@ __device__ __forceinline__ int tall_row(const TensorView& X, int R, const Real* 
     }
   }
 #pragma unroll
-  for (int t = 0; t < kR; t += VN) Vc::st(prow + t, p + t);
+  for (int t = 0; t < kR; ++t) prow[t] = p[t];
 #pragma unroll
   for (int t = 0; t < kR; ++t) z[t] = Real(0);
   if (valid) {
@@ -915,8 +970,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_qr(
     const int64_t* __restrict__ order, const int* __restrict__ count, int* __restrict__ counter,
     Real* __restrict__ T, unsigned long long* __restrict__ fma_count) {
   using Lt = TallLay<Real, kR>;
-  using Vc = Vec16<Real>;
-  constexpr int ldb = Lt::ldb, ldr = Lt::ldr, VN = Lt::VN;
+  constexpr int ldb = Lt::ldb, ldr = Lt::ldr;
   constexpr int kC2 = kR > 32 ? kR - 32 : 1;   // second columns (lanes 0 .. kR-33)
   constexpr unsigned kFull = 0xffffffffu;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -944,7 +998,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_qr(
       Real z[kR];
       nnzk += tall_row<Real, kR>(X, R, V, Hs, wk, g + lane, lane < nb, Bs + lane * ldb, z);
 #pragma unroll
-      for (int t = 0; t < kR; t += VN) Vc::st(Bs + lane * ldb + t, z + t);
+      for (int t = 0; t < kR; ++t) Bs[lane * ldb + t] = z[t];
       __syncwarp();
       // block columns: c1 = lane, c2 = 32 + lane
       Real bc[32], bc2[32];
@@ -1007,6 +1061,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_qr(
         __syncwarp();
       }
     }
+    __syncwarp();
     Real* Tk = T + k * R * R;
     for (int e = lane; e < R * R; e += 32) {
       const int r = e / R, t = e - r * R;
@@ -1039,7 +1094,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_pass2(
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   Real* Bp = Hs + kR * kR + (size_t)warp * Lt::per_warp;   // p rows of a block
   Real* Ba = Bp + 32 * ldb;                                 // a rows, then q rows
-  Real* Om = Ba + 32 * ldb;                                 // Omega (kR x ldb, zero-padded)
+  Real* Om = Bp + Lt::pad;                                  // Omega (kR x kR, zero-padded)
   load_hs<Real, kR>(H, R, Hs);
   __syncthreads();
   double* fh = fh_partial ? fh_partial + ((size_t)blockIdx.x * (kWNT / 32) + warp) * R * R : nullptr;
@@ -1060,7 +1115,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_pass2(
     Real* Tk = T + k * R * R;
     // Omega was written by the previous launch: read it through L2
     for (int r = 0; r < kR; ++r)
-      for (int t = lane; t < ldb; t += 32) Om[r * ldb + t] = (r < R && t < R) ? __ldcg(Tk + r * R + t) : Real(0);
+      for (int t = lane; t < kR; t += 32) Om[r * kR + t] = (r < R && t < R) ? __ldcg(Tk + r * R + t) : Real(0);
     __syncwarp();
     Real acc[kTR][kTC];
 #pragma unroll
@@ -1073,7 +1128,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_pass2(
       Real z[kR];
       nnzk += tall_row<Real, kR>(X, R, V, Hs, wk, g + lane, lane < nb, Bp + lane * ldb, z);
 #pragma unroll
-      for (int t = 0; t < kR; t += VN) Vc::st(Ba + lane * ldb + t, z + t);
+      for (int t = 0; t < kR; ++t) Ba[lane * ldb + t] = z[t];
       // q_i = a_i Omega (own row of Ba, rows of Omega broadcast)
 #pragma unroll
       for (int t = 0; t < kR; ++t) z[t] = Real(0);
@@ -1083,7 +1138,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_pass2(
 #pragma unroll
         for (int t = 0; t < kR; t += VN) {
           Real ov[VN];
-          Vc::ld(Om + r * ldb + t, ov);
+          Vc::ld(Om + r * kR + t, ov);
 #pragma unroll
           for (int q = 0; q < VN; ++q) z[t + q] += ar * ov[q];
         }
@@ -1095,7 +1150,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_pass2(
           if (t < R) qrow[t] = z[t];
       }
 #pragma unroll
-      for (int t = 0; t < kR; t += VN) Vc::st(Ba + lane * ldb + t, z + t);
+      for (int t = 0; t < kR; ++t) Ba[lane * ldb + t] = z[t];
       __syncwarp();
       // T_k += sum_i q_i^T p_i over the block (rows past nb are zero)
       for (int i = 0; i < nb; ++i) {
@@ -1282,7 +1337,7 @@ copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const R
     return st;
   if (rows) {
     rk.qr<<<(unsigned)qblocks, kWNT, rk.qr_smem, h->stream>>>(X, R, H, V, W, order, n_tall, counter + 5, T,
-                                                                  fma_count);
+                                                                fma_count);
     if ((st = cuda_check(h, cudaGetLastError(), "k_tall_qr launch")) != COPA_OK) return st;
   }
   k_procrustes<Real><<<(unsigned)blocks, kNT, smem, h->stream>>>(X, R, H, V, W, tau, Q, T, Pi, rank, part,

@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(kNT, 5) k_procrustes(
     Real* __restrict__ Pi, int32_t* __restrict__ rank, double* __restrict__ fh_partial,
     const int64_t* __restrict__ order, int* __restrict__ counter,
     unsigned long long* __restrict__ fma_count, Real* __restrict__ Uw,
-    const int64_t* __restrict__ woff, int warm_in, const int* __restrict__ limit, int tall_split) {
+    const int64_t* __restrict__ woff, int warm_in, const int* __restrict__ limit, const int* __restrict__ first) {
   extern __shared__ unsigned char smem_raw[];
   Real* sm = reinterpret_cast<Real*>(smem_raw);
   const Lay L = lay_of<Real>(R);
@@ -229,8 +229,9 @@ __global__ void __launch_bounds__(kNT, 5) k_procrustes(
   int* sidx = reinterpret_cast<int*>(misc + 8);
   const Real tol = Tol<Real>::v();
   unsigned long long fma = 0;   // work tally (thread 0), for the roofline
-  // subjects order[0 .. kend) are this kernel's; the rest take the warp path
+  // subjects order[kbeg .. kend) are this kernel's; the others take the lane-per-row kernels
   const int64_t kend = limit ? min((int64_t)max(*limit, 0), X.K) : X.K;
+  const int64_t kbeg = first ? min((int64_t)max(*first, 0), kend) : 0;
 
   double* fh = fh_partial ? fh_partial + (size_t)blockIdx.x * R * R : nullptr;
   if (fh)
@@ -240,36 +241,33 @@ __global__ void __launch_bounds__(kNT, 5) k_procrustes(
     __syncthreads();
     if (tid == 0) sidx[0] = atomicAdd(counter, 1);
     __syncthreads();
-    const int idx = sidx[0];
+    const int64_t idx = kbeg + sidx[0];
     if (idx >= kend) break;
     const int64_t k = order ? order[idx] : idx;
     const int64_t r0 = X.subj_ptr[k], r1 = X.subj_ptr[k + 1];
     const int64_t Ik64 = r1 - r0;
     const bool wide = Ik64 <= R;
     const int m = wide ? (int)Ik64 : R;
-    // split tall subject: R_A comes from the QR kernel (in T_k), Omega goes back there
-    const bool split = !wide && tall_split != 0;
     if (tid == 0) {
       const unsigned long long nnzk = (unsigned long long)(X.row_ptr[r1] - X.row_ptr[r0]);
       const unsigned long long ik = (unsigned long long)Ik64, RR = (unsigned long long)R * R;
       fma += 2ull * m * R;
       if (wide) fma += nnzk * R + ik * RR + 2ull * m * m * R + 2ull * RR * m;
-      else if (split) fma += 2 * RR * R;
       else fma += 2 * nnzk * R + 5 * ik * RR + 2 * RR * R;
     }
 
-    // ---- E = S_k H^T; tall: clear R_A (or load it, split) ----
+    // ---- E = S_k H^T; tall: clear R_A ----
     for (int e = tid; e < R * R; e += kNT) {
       const int r = e / R, t = e - r * R;
       Es[r * ld + t] = W[k * R + r] * __ldg(H + t * R + r);
-      if (!wide) Zb[r * ld + t] = split ? __ldcg(T + k * R * R + e) : Real(0);   // R_A from the QR launch
+      if (!wide) Zb[r * ld + t] = Real(0);
     }
     __syncthreads();
 
     // ---- pass 1: rows four at a time, a_i = (x_i V) E; wide: keep p_i and a_i;
     //      tall: fill a QR block of up to R rows, then fold it into R_A ----
     int nb = 0;   // rows in the QR block (tall); always < R before a group
-    for (int64_t g = r0; g < (split ? r0 : r1);) {
+    for (int64_t g = r0; g < r1;) {
       int nrow = (int)min((int64_t)kNW, r1 - g);
       if (!wide && nrow > R - nb) nrow = R - nb;   // the block holds at most R rows
       const int64_t i = g + warp;
@@ -493,10 +491,8 @@ __global__ void __launch_bounds__(kNT, 5) k_procrustes(
         Pb[r * ld + t] = acc;
         if (Pi) Pi[k * R * R + e] = pacc;
         Ub[r * ld + t] = Real(0);
-        if (split) T[k * R * R + e] = acc;
       }
       __syncthreads();
-      if (split) continue;
       // pass 2, rows four at a time: q_i = (p_i E) Omega; T_k += q_i^T p_i
       for (int64_t g = r0; g < r1; g += kNW) {
         const int64_t i = g + warp;
@@ -894,14 +890,14 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
   if (fma_count && lane == 0) atomicAdd(fma_count, fma);
 }
 
-// ---- tall subjects (I_k > R), split in three launches around the block kernel ----
-// k_tall_qr: warp per subject; the rows of A_k = X_k V S_k H^T are formed 32 at a time
-// (lane = row) and folded into R_A by Householder reflections on the stacked [R_A; block]
-// (lane = column, the block's columns in registers, each reflector broadcast by shuffles).
-// R_A goes to T_k. The block kernel then runs the Jacobi on R_A and leaves
-// Omega = C_K Sigma_K^{-1} C_K^T in T_k; k_tall_pass2 (warp per subject, lane = row)
-// recomputes the rows, writes q_i = a_i Omega and accumulates T_k = sum_i q_i^T p_i and
-// the F_H partial sums. Same arithmetic as the block kernel's tall branch.
+// ---- tall subjects (I_k > R), in three warp-per-subject launches ----
+// k_tall_qr: the rows of A_k = X_k V S_k H^T are formed 32 at a time (lane = row) and
+// folded into R_A by Householder reflections on the stacked [R_A; block] (lane = column,
+// the block's columns in registers, each reflector broadcast by shuffles); R_A goes to
+// T_k. k_tall_jacobi runs the one-sided Jacobi on the rows of R_A and leaves
+// Omega = C_K Sigma_K^{-1} C_K^T in T_k. k_tall_pass2 (lane = row) recomputes the rows,
+// writes q_i = a_i Omega and accumulates T_k = sum_i q_i^T p_i and the F_H partial sums.
+// Same arithmetic as the block kernel's tall branch.
 template <typename Real, int kR>
 struct TallLay {
   static constexpr int VN = Vec16<Real>::n;
@@ -1192,6 +1188,174 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_pass2(
   if (fma_count && lane == 0) atomicAdd(fma_count, fma);
 }
 
+// k_tall_jacobi: warp per tall subject, the one-sided Jacobi on the rows of R_A (left in
+// T_k by k_tall_qr) without block barriers. The n2 = R + (R & 1) rows sit two per lane in
+// lanes 0 .. n2/2 - 1, the two rows of a pair in the same registers-resident lane; after
+// each round the rows move one step along the circle of the circle method (tops one lane
+// up, bottoms one lane down, lane 0's top fixed), so the n2 - 1 rounds of a sweep meet
+// every pair once. Omega_k = C_K Sigma_K^{-1} C_K^T goes back to T_k, with rank_k and,
+// on request, Pi_k = C_K C_K^T.
+template <typename Real, int kR>
+struct TallJLay {
+  static constexpr int ld = kR + 1;
+  static constexpr int per_warp = (kR + 2) * ld + kR;   // c_j rows, 1/sigma_j
+  static constexpr size_t bytes = sizeof(Real) * (kWNT / 32) * (size_t)per_warp + 16;
+};
+
+template <typename Real, int kR>
+__global__ void __launch_bounds__(kWNT, 3) k_tall_jacobi(
+    int64_t K, int R, double tau_rank, const int64_t* __restrict__ order, const int* __restrict__ count,
+    int* __restrict__ counter, Real* T, Real* __restrict__ Pi, int32_t* __restrict__ rank,
+    unsigned long long* __restrict__ fma_count) {
+  using Lj = TallJLay<Real, kR>;
+  constexpr int ld = Lj::ld;
+  constexpr int kTR = kR / 8, kTC = kR / 4;
+  constexpr unsigned kFull = 0xffffffffu;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Real* Cs = reinterpret_cast<Real*>(smem_raw) + (size_t)warp * Lj::per_warp;   // c_j rows
+  Real* Is = Cs + (kR + 2) * ld;                                               // 1/sigma_j
+  const Real tol = Tol<Real>::v();
+  const int n2 = R + (R & 1), L = n2 / 2;
+  const bool own = lane < L;
+  const int ra = lane, rb = L + lane;   // rows held at the start (top, bottom)
+  const int64_t nt = min((int64_t)max(*count, 0), K);
+  const int tr = lane >> 2, tc = lane & 3;
+  unsigned long long fma = 0;
+
+  while (true) {
+    int claim = 0;
+    if (lane == 0) claim = atomicAdd(counter, 1);
+    const int64_t idx = __shfl_sync(kFull, claim, 0);
+    if (idx >= nt) break;
+    const int64_t k = order[idx];
+    Real* Tk = T + k * R * R;
+    Real top[kR], bot[kR];
+#pragma unroll
+    for (int t = 0; t < kR; ++t) {   // R_A was written by the previous launch: read it through L2
+      top[t] = (own && ra < R && t < R) ? __ldcg(Tk + ra * R + t) : Real(0);
+      bot[t] = (own && rb < R && t < R) ? __ldcg(Tk + rb * R + t) : Real(0);
+    }
+    Real na, nb;
+    {
+      Real a4[4] = {Real(0), Real(0), Real(0), Real(0)}, b4[4] = {Real(0), Real(0), Real(0), Real(0)};
+#pragma unroll
+      for (int t = 0; t < kR; ++t) {
+        a4[t & 3] += top[t] * top[t];
+        b4[t & 3] += bot[t] * bot[t];
+      }
+      na = (a4[0] + a4[1]) + (a4[2] + a4[3]);
+      nb = (b4[0] + b4[1]) + (b4[2] + b4[3]);
+    }
+    int sweeps = 0;
+    unsigned long long nrot = 0;
+    for (int sweep = 0; sweep < kMaxSweeps && n2 > 1; ++sweep) {
+      ++sweeps;
+      bool any = false;
+      for (int rd = 0; rd < n2 - 1; ++rd) {
+        Real g4[4] = {Real(0), Real(0), Real(0), Real(0)};
+#pragma unroll
+        for (int t = 0; t < kR; ++t) g4[t & 3] += top[t] * bot[t];
+        const Real gg = (g4[0] + g4[1]) + (g4[2] + g4[3]);
+        const bool rot = own && gg != Real(0) && fabs(gg) > tol * sqrt(na * nb);
+        if (rot) {
+          Real c, s;
+          rotation_of(na, nb, gg, &c, &s);
+          Real a4[4] = {Real(0), Real(0), Real(0), Real(0)}, b4[4] = {Real(0), Real(0), Real(0), Real(0)};
+#pragma unroll
+          for (int t = 0; t < kR; ++t) {
+            const Real x = top[t], y = bot[t];
+            top[t] = c * x - s * y;
+            bot[t] = s * x + c * y;
+            a4[t & 3] += top[t] * top[t];
+            b4[t & 3] += bot[t] * bot[t];
+          }
+          na = (a4[0] + a4[1]) + (a4[2] + a4[3]);
+          nb = (b4[0] + b4[1]) + (b4[2] + b4[3]);
+        }
+        const unsigned rmask = __ballot_sync(kFull, rot);
+        any |= rmask != 0u;
+        if (lane == 0) nrot += __popc(rmask);
+        // next round: lane l's top <- lane l-1's top (lane 1 <- lane 0's bottom), lane l's
+        // bottom <- lane l+1's bottom (the last lane's bottom <- its own top)
+        const int up_src = lane > 0 ? lane - 1 : 0;
+#pragma unroll
+        for (int t = 0; t < kR; ++t) {
+          const Real up = __shfl_sync(kFull, lane == 0 ? bot[t] : top[t], up_src);
+          const Real dn = __shfl_down_sync(kFull, bot[t], 1);
+          const Real nbt = lane == L - 1 ? top[t] : dn;
+          if (lane > 0 && own) top[t] = up;
+          if (own) bot[t] = nbt;
+        }
+        {
+          const Real up = __shfl_sync(kFull, lane == 0 ? nb : na, up_src);
+          const Real dn = __shfl_down_sync(kFull, nb, 1);
+          const Real nbn = lane == L - 1 ? na : dn;
+          if (lane > 0 && own) na = up;
+          if (own) nb = nbn;
+        }
+      }
+      if (!any) break;
+    }
+
+    // ---- rank cut; c_j = z_j / sigma_j, Omega = sum_j c_j c_j^T / sigma_j ----
+    const Real amax = warp_max(own ? (na > nb ? na : nb) : Real(0));
+    const bool ka = own && amax > Real(0) && (double)na > tau_rank * (double)amax;
+    const bool kb = own && amax > Real(0) && (double)nb > tau_rank * (double)amax;
+    const int kept = __popc(__ballot_sync(kFull, ka)) + __popc(__ballot_sync(kFull, kb));
+    if (rank && lane == 0) rank[k] = kept;
+    const Real sa = ka ? rsqrt_(na) : Real(0), sb = kb ? rsqrt_(nb) : Real(0);
+    if (own) {
+#pragma unroll
+      for (int t = 0; t < kR; ++t) {
+        Cs[lane * ld + t] = top[t] * sa;
+        Cs[(L + lane) * ld + t] = bot[t] * sb;
+      }
+      Is[lane] = sa;
+      Is[L + lane] = sb;
+    }
+    __syncwarp();
+#pragma unroll 1
+    for (int pass = 0; pass < (Pi ? 2 : 1); ++pass) {
+      Real acc[kTR][kTC];
+#pragma unroll
+      for (int a = 0; a < kTR; ++a)
+#pragma unroll
+        for (int b = 0; b < kTC; ++b) acc[a][b] = Real(0);
+      for (int j = 0; j < n2; ++j) {
+        const Real w = pass == 0 ? Is[j] : Real(1);
+        Real cr[kTR], cs[kTC];
+#pragma unroll
+        for (int a = 0; a < kTR; ++a) cr[a] = Cs[j * ld + tr * kTR + a] * w;
+#pragma unroll
+        for (int b = 0; b < kTC; ++b) cs[b] = Cs[j * ld + tc * kTC + b];
+#pragma unroll
+        for (int a = 0; a < kTR; ++a)
+#pragma unroll
+          for (int b = 0; b < kTC; ++b) acc[a][b] += cr[a] * cs[b];
+      }
+      Real* out = pass == 0 ? Tk : Pi + k * R * R;
+#pragma unroll
+      for (int a = 0; a < kTR; ++a) {
+        const int r = tr * kTR + a;
+        if (r < R) {
+#pragma unroll
+          for (int b = 0; b < kTC; ++b) {
+            const int s = tc * kTC + b;
+            if (s < R) out[r * R + s] = acc[a][b];
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (fma_count && lane == 0) {
+      const unsigned long long RR = (unsigned long long)R * R, mm = (unsigned long long)R;
+      fma += (unsigned long long)sweeps * (mm * (mm - 1) / 2) * 3 * R + nrot * 4ull * R + 2 * RR * R + 2 * mm * R;
+    }
+  }
+  if (fma_count && lane == 0) atomicAdd(fma_count, fma);
+}
+
 template <typename Real>
 __global__ void k_reduce_partials(const double* __restrict__ part, int nparts, int n,
                                   Real* __restrict__ out) {
@@ -1210,6 +1374,9 @@ template <typename Real>
 using TallQrKernel = void (*)(TensorView, int, const Real*, const Real*, const Real*, const int64_t*, const int*, int*,
                               Real*, unsigned long long*);
 template <typename Real>
+using TallJacobiKernel = void (*)(int64_t, int, double, const int64_t*, const int*, int*, Real*, Real*, int32_t*,
+                                  unsigned long long*);
+template <typename Real>
 using TallPass2Kernel = void (*)(TensorView, int, const Real*, const Real*, const Real*, const int64_t*, const int*,
                                  int*, Real*, Real*, double*, unsigned long long*);
 
@@ -1218,8 +1385,9 @@ template <typename Real>
 struct RowKernels {
   WarpKernel<Real> small = nullptr;
   TallQrKernel<Real> qr = nullptr;
+  TallJacobiKernel<Real> jac = nullptr;
   TallPass2Kernel<Real> pass2 = nullptr;
-  size_t small_smem = 0, qr_smem = 0, tall_smem = 0;
+  size_t small_smem = 0, qr_smem = 0, jac_smem = 0, tall_smem = 0;
 };
 
 template <typename Real, int KR>
@@ -1227,6 +1395,8 @@ RowKernels<Real> row_kernels_of() {
   RowKernels<Real> r;
   r.small = k_procrustes_warp<Real, KR>;
   r.qr = k_tall_qr<Real, KR>;
+  r.jac = k_tall_jacobi<Real, KR>;
+  r.jac_smem = TallJLay<Real, KR>::bytes;
   r.pass2 = k_tall_pass2<Real, KR>;
   r.small_smem = WarpLay<Real, KR>::bytes;
   r.qr_smem = TallLay<Real, KR>::qr_bytes;
@@ -1284,10 +1454,9 @@ size_t procrustes_smem(int R) {
 }
 
 // Launch order (lane-per-row kernels available for this R and precision):
-//   k_tall_qr (I_k > R: R_A -> T_k), k_procrustes (I_k > min(R, 32): the Jacobi of the
-//   tall subjects on R_A -> Omega in T_k, the whole path for the remaining wide ones),
-//   k_tall_pass2 (I_k > R: Q rows, T_k, F_H), k_procrustes_warp (I_k <= min(R, 32)).
-// Otherwise k_procrustes takes every subject.
+//   k_tall_qr (I_k > R: R_A -> T_k), k_tall_jacobi (I_k > R: Omega -> T_k),
+//   k_procrustes (min(R, 32) < I_k <= R), k_tall_pass2 (I_k > R: Q rows, T_k, F_H),
+//   k_procrustes_warp (I_k <= min(R, 32)). Otherwise k_procrustes takes every subject.
 template <typename Real>
 copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const Real* H,
                                 const Real* V, const Real* W, double tau, Real* Q, Real* T,
@@ -1312,10 +1481,11 @@ copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const R
 
   const RowKernels<Real> rk = row_kernels_for<Real>((R + 7) / 8 * 8);
   const bool rows = rk.small != nullptr;
-  int64_t sblocks = 0, qblocks = 0, pblocks = 0;
+  int64_t sblocks = 0, qblocks = 0, jblocks = 0, pblocks = 0;
   if (rows) {
     if ((st = row_grid(h, rk.small, rk.small_smem, X.K, &sblocks)) != COPA_OK) return st;
     if ((st = row_grid(h, rk.qr, rk.qr_smem, X.K, &qblocks)) != COPA_OK) return st;
+    if ((st = row_grid(h, rk.jac, rk.jac_smem, X.K, &jblocks)) != COPA_OK) return st;
     if ((st = row_grid(h, rk.pass2, rk.tall_smem, X.K, &pblocks)) != COPA_OK) return st;
   }
   const int64_t* order = nullptr;
@@ -1332,7 +1502,8 @@ copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const R
     if ((st = ws_get(h, SLOT_PARTIAL, (size_t)nparts * R * R * sizeof(double), (void**)&part)) != COPA_OK)
       return st;
   }
-  // counter[0]: block kernel, [2..3]: work tally, [4]: small subjects, [5]: tall QR, [6]: tall pass 2
+  // counter[0]: block kernel, [2..3]: work tally, [4]: small subjects, [5]: tall QR, [6]: tall pass 2,
+  // [7]: tall Jacobi
   if ((st = cuda_check(h, cudaMemsetAsync(counter, 0, 32, h->stream), "memset")) != COPA_OK)
     return st;
   if (rows) {
@@ -1340,9 +1511,14 @@ copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const R
                                                                 fma_count);
     if ((st = cuda_check(h, cudaGetLastError(), "k_tall_qr launch")) != COPA_OK) return st;
   }
+  if (rows) {
+    rk.jac<<<(unsigned)jblocks, kWNT, rk.jac_smem, h->stream>>>(X.K, R, tau, order, n_tall, counter + 7, T, Pi, rank,
+                                                                  fma_count);
+    if ((st = cuda_check(h, cudaGetLastError(), "k_tall_jacobi launch")) != COPA_OK) return st;
+  }
   k_procrustes<Real><<<(unsigned)blocks, kNT, smem, h->stream>>>(X, R, H, V, W, tau, Q, T, Pi, rank, part,
                                                                 order, counter, fma_count, Uw, woff,
-                                                                warm_in ? 1 : 0, n_big, rows ? 1 : 0);
+                                                                warm_in ? 1 : 0, n_big, n_tall);
   if ((st = cuda_check(h, cudaGetLastError(), "k_procrustes launch")) != COPA_OK) return st;
   if (rows) {
     double* ppart = part ? part + (size_t)blocks * R * R : nullptr;

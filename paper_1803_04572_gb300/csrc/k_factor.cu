@@ -710,6 +710,104 @@ __global__ void __launch_bounds__(256) k_admm_w(const Real* __restrict__ T,
   }
 }
 
+// W update for R <= 48, batched: a block takes kWS subjects at once and runs every inner
+// iteration as one small GEMM Z = (G + rho I)^{-1} B over the tile (B = F_W + rho (Wbar + D)
+// column by subject), so Ginv is read from shared memory once per tile and iteration
+// instead of once per subject. A thread owns NC components of two subjects (state in
+// registers). F_W(k, s) = sum_r H(r, s) T_k(r, s) comes first, one warp per subject with
+// coalesced reads of T_k.
+constexpr int kWS = 64;      // subjects per block
+constexpr int kWNTH = 256;   // threads per block
+
+template <typename Real, int NC>
+__global__ void __launch_bounds__(kWNTH) k_admm_w_tiled(const Real* __restrict__ T, const Real* __restrict__ H,
+                                                        const Real* __restrict__ Ginv,
+                                                        const double* __restrict__ rho_dev, int n_inner, int c,
+                                                        double lam, Real* __restrict__ Wbar, Real* __restrict__ DW,
+                                                        int64_t K, int R) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ldg = R + 1;
+  Real* Gs = reinterpret_cast<Real*>(smem_raw);   // R x (R+1): Ginv
+  Real* Hs = Gs + R * ldg;                         // R x R
+  constexpr int ldw = kWS + 1;                     // odd stride: conflict-free columns
+  Real* Bs = Hs + R * R;                           // R x ldw: B, column per subject
+  Real* Fs = Bs + R * ldw;                         // R x ldw: F_W
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int sr = tid & 7, kc = tid >> 3;           // components sr*NC.., subjects 2kc, 2kc+1
+  for (int e = tid; e < R * ldg; e += kWNTH) Gs[e] = Ginv[e];
+  for (int e = tid; e < R * R; e += kWNTH) Hs[e] = H[e];
+  const double rho = *rho_dev;
+  const Real rr = (Real)rho, lor = (Real)(lam / rho);
+  for (int64_t k0 = (int64_t)blockIdx.x * kWS; k0 < K; k0 += (int64_t)gridDim.x * kWS) {
+    const int nk = (int)min((int64_t)kWS, K - k0);
+    __syncthreads();   // Gs/Hs ready; the previous tile's reads of Fs/Bs are done
+    for (int q = warp; q < kWS; q += kWNTH / 32) {
+      for (int s = lane; s < R; s += 32) {
+        Real acc = Real(0);
+        if (q < nk) {
+          const Real* Tk = T + (k0 + q) * R * R;
+          for (int r = 0; r < R; ++r) acc += Hs[r * R + s] * Tk[r * R + s];
+        }
+        Fs[s * ldw + q] = acc;
+      }
+    }
+    __syncthreads();
+    Real f[NC][2], zb[NC][2], d[NC][2];
+#pragma unroll
+    for (int a = 0; a < NC; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const int s = sr * NC + a, q = 2 * kc + b;
+        const bool in = s < R && q < nk;
+        f[a][b] = in ? Fs[s * ldw + q] : Real(0);
+        zb[a][b] = in ? Wbar[(k0 + q) * R + s] : Real(0);
+        d[a][b] = in ? DW[(k0 + q) * R + s] : Real(0);
+      }
+    for (int it = 0; it < n_inner; ++it) {
+#pragma unroll
+      for (int a = 0; a < NC; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          const int s = sr * NC + a;
+          if (s < R) Bs[s * ldw + 2 * kc + b] = f[a][b] + rr * (zb[a][b] + d[a][b]);
+        }
+      __syncthreads();
+      Real z[NC][2];
+#pragma unroll
+      for (int a = 0; a < NC; ++a) z[a][0] = z[a][1] = Real(0);
+      for (int t = 0; t < R; ++t) {
+        const Real b0 = Bs[t * ldw + 2 * kc], b1 = Bs[t * ldw + 2 * kc + 1];
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+          const int s = sr * NC + a;
+          const Real g = s < R ? Gs[s * ldg + t] : Real(0);
+          z[a][0] += g * b0;
+          z[a][1] += g * b1;
+        }
+      }
+      __syncthreads();   // every read of Bs is done before the next iteration writes it
+#pragma unroll
+      for (int a = 0; a < NC; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          const Real nz = prox<Real>(z[a][b] - d[a][b], c, lor);
+          d[a][b] = d[a][b] + nz - z[a][b];
+          zb[a][b] = nz;
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < NC; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const int s = sr * NC + a, q = 2 * kc + b;
+        if (s < R && q < nk) {
+          Wbar[(k0 + q) * R + s] = zb[a][b];
+          DW[(k0 + q) * R + s] = d[a][b];
+        }
+      }
+  }
+}
+
 // ------------------------------------------------------------------------------------
 // FIT = 1 - (x_norm2 - ||X||^2 + ||X||^2 - 2 <V, F_V> + <V^T V, U^T U>) / x_norm2
 // ------------------------------------------------------------------------------------
@@ -987,8 +1085,30 @@ template <typename Real>
 copa_status_t launch_admm_w(copa_ctx* h, const Real* T, const Real* H, const Real* Ginv,
                             const double* rho_dev, int n_inner, int c, double lam, Real* Wbar,
                             Real* DW, int64_t K, int R) {
-  const size_t smem = sizeof(Real) * ((size_t)R * (R + 1) + (size_t)R * R + 8 * (size_t)R);
   copa_status_t st;
+  if (R <= 48) {
+    void (*kern)(const Real*, const Real*, const Real*, const double*, int, int, double, Real*, Real*, int64_t,
+                 int) = nullptr;
+    switch ((R + 7) / 8) {
+      case 1: kern = k_admm_w_tiled<Real, 1>; break;
+      case 2: kern = k_admm_w_tiled<Real, 2>; break;
+      case 3: kern = k_admm_w_tiled<Real, 3>; break;
+      case 4: kern = k_admm_w_tiled<Real, 4>; break;
+      case 5: kern = k_admm_w_tiled<Real, 5>; break;
+      default: kern = k_admm_w_tiled<Real, 6>; break;
+    }
+    const size_t tsm = sizeof(Real) * ((size_t)R * (R + 1) + (size_t)R * R + 2 * (size_t)R * (kWS + 1));
+    if ((st = cuda_check(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm),
+                         "cudaFuncSetAttribute")) != COPA_OK)
+      return st;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWNTH, tsm);
+    const int64_t tiles = (K + kWS - 1) / kWS;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)h->num_sms * std::max(per_sm, 1)));
+    kern<<<blocks, kWNTH, tsm, h->stream>>>(T, H, Ginv, rho_dev, n_inner, c, lam, Wbar, DW, K, R);
+    return cuda_check(h, cudaGetLastError(), "k_admm_w_tiled");
+  }
+  const size_t smem = sizeof(Real) * ((size_t)R * (R + 1) + (size_t)R * R + 8 * (size_t)R);
   if ((st = cuda_check(h, cudaFuncSetAttribute(k_admm_w<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem), "cudaFuncSetAttribute")) != COPA_OK)
     return st;

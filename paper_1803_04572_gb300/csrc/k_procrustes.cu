@@ -1,30 +1,30 @@
 // Procrustes step of COPA (Sec. 3.1, Eq. 5; Algorithm 1 per-subject loop) and the
-// fused mode-1 MTTKRP, for all subjects in one persistent launch: one CTA of 128 threads
-// (4 warps) per subject, dynamic scheduling over a largest-first subject order.
+// fused mode-1 MTTKRP, for all subjects, over a largest-first subject order.
 //
 // For subject k: P_k = X_k V (I_k x R), E_k = S_k H^T, A_k = P_k E_k. With the thin SVD
 // A_k = B D C^T, the update is Q_k = B C^T over the singular values kept by the rank
 // cut sigma_i^2 > tau sigma_max^2. It is computed without forming A_k^T A_k (which would
 // square the condition number) by one-sided (Hestenes) Jacobi on row vectors:
-//   * I_k <= R ("wide"): rotate the I_k rows of A_k until they are orthogonal,
-//     Z = U A_k with U orthogonal (accumulated). Then A_k = U^T Z = U^T Sigma C^T, and
-//     Q_k = U^T C_K^T (kept columns), a product of orthonormal factors.
-//   * I_k > R ("tall"): a blocked Householder QR of the streamed rows gives
-//     A_k = Q_A R_A (R_A upper triangular R x R); Hestenes on the rows of R_A gives
-//     Sigma and C, so Omega = C_K Sigma_K^{-1} C_K^T and Q_k = A_k Omega (rows recomputed
-//     in a second pass over X_k, which also accumulates T_k = sum_i q_i^T p_i).
-// Warm start (copa_fit): the left rotation U of each subject (Z = U A) is kept between
-// outer iterations; the next iteration starts the Jacobi sweeps from U_prev A, which is
-// nearly row-orthogonal once the factors settle, so fewer sweeps are needed. The result
-// is the same SVD (up to rounding).
+//   * "wide" (I_k rows rotated directly): Z = U A_k with U orthogonal (accumulated), then
+//     A_k = U^T Z = U^T Sigma C^T and Q_k = U^T C_K^T (kept columns), a product of
+//     orthonormal factors.
+//   * "tall": a blocked Householder QR of the streamed rows gives A_k = Q_A R_A (R_A
+//     upper triangular R x R); Hestenes on the rows of R_A gives Sigma and C, so
+//     Omega = C_K Sigma_K^{-1} C_K^T and Q_k = A_k Omega (rows recomputed in a second pass
+//     over X_k, which also accumulates T_k = sum_i q_i^T p_i).
 // Outputs per subject: Q_k rows (S x R), T_k = Q_k^T P_k (= Y_k V, R x R), optionally
-// Pi_k = Q_k^T Q_k = C_K C_K^T and the rank |K|; and F_H = sum_k T_k S_k through per-CTA
-// FP64 partial sums. The same code runs in float (mixed) or double (plain FP64).
+// Pi_k = Q_k^T Q_k = C_K C_K^T and the rank |K|; and F_H = sum_k T_k S_k through FP64
+// partial sums. The same code runs in float (mixed) or double (plain FP64).
 //
-// Parallel layout inside the CTA: rows of X_k are handled four at a time, one per warp
-// (lanes over the R components); the Jacobi pairs of a round are spread over the 128
-// threads with LP = 128 / pairs threads per pair (a power of two), each thread holding
-// R / LP components of the two vectors and the pair's dot products reduced by shuffles.
+// Kernels (the lane-per-row ones exist for R <= 48 in float and R <= 16 in double):
+//   * k_procrustes_warp: I_k <= min(R, 32), wide form, one warp per subject, lane = row.
+//     Warm start (copa_fit): U of each subject is kept between outer iterations and the
+//     next iteration starts the sweeps from U_prev A, which is nearly row-orthogonal once
+//     the factors settle, so fewer sweeps are needed (same SVD up to rounding).
+//   * k_tall_qr, k_tall_jacobi, k_tall_pass2: I_k > min(R, 32), tall form, one warp per
+//     subject in each launch.
+//   * k_procrustes: every subject, one 128-thread block per subject (both forms), for the
+//     R and precisions the lane-per-row kernels do not cover.
 #include "copa_internal.cuh"
 
 namespace copa {
@@ -84,15 +84,17 @@ __device__ __forceinline__ float fdiv_(float a, float b) { return __fdividef(a, 
 __device__ __forceinline__ double fdiv_(double a, double b) { return a / b; }
 
 // Jacobi rotation (c, s) that makes the pair with squared norms aa, bb and dot product gg
-// orthogonal: x' = c x - s y, y' = s x + c y.
+// orthogonal: x' = c x - s y, y' = s x + c y. Then |x'|^2 = aa - t gg and |y'|^2 = bb + t gg
+// with t = s / c (returned in *t).
 template <typename Real>
-__device__ __forceinline__ void rotation_of(Real aa, Real bb, Real gg, Real* c, Real* s) {
+__device__ __forceinline__ void rotation_of(Real aa, Real bb, Real gg, Real* c, Real* s, Real* t = nullptr) {
   const Real zeta = fdiv_(bb - aa, Real(2) * gg);
   Real tt;
   if (fabs(zeta) > Real(1e15)) tt = fdiv_(Real(0.5), zeta);
   else tt = fdiv_(zeta >= Real(0) ? Real(1) : Real(-1), fabs(zeta) + sqrt(Real(1) + zeta * zeta));
   *c = rsqrt_(Real(1) + tt * tt);
   *s = *c * tt;
+  if (t) *t = tt;
 }
 
 constexpr int kEPL = 12;   // components per thread held in registers by the block Jacobi
@@ -203,6 +205,11 @@ __device__ void tsqr_block(Real* Z, int ld, int R, int nb, Real* vb, Real* misc)
   }
 }
 
+// Block kernel, one 128-thread CTA per subject. Rows of X_k are handled four at a time,
+// one per warp (lanes over the R components); the Jacobi pairs of a round are spread over
+// the block with LP = 128 / pairs threads per pair (a power of two), each thread holding
+// R / LP components of the two vectors and the pair's dot products reduced by shuffles;
+// one barrier per round.
 template <typename Real>
 __global__ void __launch_bounds__(kNT, 5) k_procrustes(
     TensorView X, int R, const Real* __restrict__ H, const Real* __restrict__ V,
@@ -529,6 +536,36 @@ __global__ void __launch_bounds__(kNT, 5) k_procrustes(
   if (fma_count && tid == 0) atomicAdd(fma_count, fma);
 }
 
+// p = x_i V for the visit row i of this lane (components padded to kR with zeros): the
+// row's column indices and values are fetched four at a time before their V rows, so that
+// the dependent gathers of a row overlap. Returns the row's number of nonzeros.
+template <typename Real, int kR>
+__device__ __forceinline__ int row_p(const TensorView& X, int R, const Real* __restrict__ V, int64_t i, bool valid,
+                                     Real* p) {
+#pragma unroll
+  for (int t = 0; t < kR; ++t) p[t] = Real(0);
+  if (!valid) return 0;
+  const int64_t a = X.row_ptr[i], b = X.row_ptr[i + 1];
+  for (int64_t q0 = a; q0 < b; q0 += 4) {
+    int c[4];
+    Real x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const bool in = q0 + u < b;
+      c[u] = in ? __ldg(X.col + q0 + u) : 0;
+      x[u] = in ? load_x<Real>(X, q0 + u) : Real(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const Real* vr = V + (int64_t)c[u] * R;
+#pragma unroll
+      for (int t = 0; t < kR; ++t)
+        if (t < R) p[t] += x[u] * __ldg(vr + t);
+    }
+  }
+  return (int)(b - a);
+}
+
 // ---- warp-per-subject path for the many small subjects (I_k <= min(R, 32)) ----
 // One warp per subject, lane i holding row i of A_k (then of Z = U A_k) and row i of U in
 // registers, so that a Jacobi round needs no block barrier: the partner row is read with
@@ -575,7 +612,7 @@ struct WarpLay {
   static constexpr int VN = Vec16<Real>::n;
   static constexpr int ld = kR + VN;             // row stride of the row buffers
   static constexpr int ldu = kM + 1;             // U: odd stride, read by columns
-  static constexpr int per_warp = 2 * kM * ld + kM * ldu + VN;
+  static constexpr int per_warp = 2 * kM * ld + kM * ldu + kR + VN;
   static constexpr size_t bytes = sizeof(Real) * ((size_t)kR * kR + (kWNT / 32) * (size_t)per_warp) + 16;
 };
 
@@ -598,6 +635,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
   Real* B1 = Hs + kR * kR + (size_t)warp * Lw::per_warp;   // A rows, then c_j rows
   Real* B2 = B1 + kM * ld;                                  // p rows, then b = U P rows
   Real* Us = B2 + kM * ld;                                  // U, for its transpose
+  Real* Wb = Us + kM * ldu;                                 // this subject's row of W
   for (int e = threadIdx.x; e < kR * kR; e += kWNT) {
     const int r = e / kR, t = e - r * kR;
     Hs[e] = (t < R && r < R) ? H[t * R + r] : Real(0);
@@ -625,23 +663,11 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
     }
     const int m = (int)ik;
     const Real* wk = W + k * R;
+    for (int r = lane; r < kR; r += 32) Wb[r] = r < R ? wk[r] : Real(0);
 
     // ---- p_i = x_i V (lane i); a_i = (p_i * w) H^T ----
     Real p[kR];
-#pragma unroll
-    for (int t = 0; t < kR; ++t) p[t] = Real(0);
-    int nnz_row = 0;
-    if (lane < m) {
-      const int64_t a = X.row_ptr[r0 + lane], b = X.row_ptr[r0 + lane + 1];
-      nnz_row = (int)(b - a);
-      for (int64_t q = a; q < b; ++q) {
-        const Real x = load_x<Real>(X, q);
-        const Real* vr = V + (int64_t)__ldg(X.col + q) * R;
-#pragma unroll
-        for (int t = 0; t < kR; ++t)
-          if (t < R) p[t] += x * __ldg(vr + t);
-      }
-    }
+    const int nnz_row = row_p<Real, kR>(X, R, V, r0 + lane, lane < m, p);
     if (lane < kM) {
 #pragma unroll
       for (int t = 0; t < kR; t += VN) Vc::st(B2 + lane * ld + t, p + t);
@@ -653,7 +679,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
     if (lane < m) {
 #pragma unroll 1
       for (int r = 0; r < R; ++r) {
-        const Real pw = B2[lane * ld + r] * wk[r];
+        const Real pw = B2[lane * ld + r] * Wb[r];
 #pragma unroll
         for (int t = 0; t < kR; t += VN) {
           Real hv[VN];
@@ -675,24 +701,27 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
 #pragma unroll
         for (int t = 0; t < kR; t += VN) Vc::st(B1 + lane * ld + t, z + t);
       }
+      if (lane < m) {   // the row of U_prev: independent loads, issued together
+#pragma unroll
+        for (int j = 0; j < kM; ++j)
+          if (j < m) u[j] = Uk[lane * m + j];
+      }
       __syncwarp();
 #pragma unroll
       for (int t = 0; t < kR; ++t) z[t] = Real(0);
       if (lane < m) {
-#pragma unroll 1
-        for (int j = 0; j < m; ++j) {
-          const Real uij = Uk[lane * m + j];
 #pragma unroll
-          for (int t = 0; t < kR; t += VN) {
-            Real av[VN];
-            Vc::ld(B1 + j * ld + t, av);
+        for (int j = 0; j < kM; ++j) {
+          if (j < m) {
 #pragma unroll
-            for (int q = 0; q < VN; ++q) z[t + q] += uij * av[q];
+            for (int t = 0; t < kR; t += VN) {
+              Real av[VN];
+              Vc::ld(B1 + j * ld + t, av);
+#pragma unroll
+              for (int q = 0; q < VN; ++q) z[t + q] += u[j] * av[q];
+            }
           }
         }
-#pragma unroll
-        for (int j = 0; j < kM; ++j)
-          if (j < m) u[j] = Uk[lane * m + j];
       }
       __syncwarp();
     }
@@ -890,7 +919,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
   if (fma_count && lane == 0) atomicAdd(fma_count, fma);
 }
 
-// ---- tall subjects (I_k > R), in three warp-per-subject launches ----
+// ---- tall form (I_k > min(R, 32)), in three warp-per-subject launches ----
 // k_tall_qr: the rows of A_k = X_k V S_k H^T are formed 32 at a time (lane = row) and
 // folded into R_A by Householder reflections on the stacked [R_A; block] (lane = column,
 // the block's columns in registers, each reflector broadcast by shuffles); R_A goes to
@@ -904,8 +933,8 @@ struct TallLay {
   static constexpr int ldb = kR + 1;    // row blocks: odd, so lane-per-row accesses are conflict-free
   static constexpr int ldr = kR + 1;    // R_A (read by columns)
   static constexpr int pad = (2 * 32 * ldb + VN - 1) / VN * VN;   // keeps Omega 16-byte aligned
-  static constexpr int per_warp = pad + kR * kR;                  // pass 2: p and a/q blocks, Omega
-  static constexpr int per_warp_qr = (32 * ldb + kR * ldr + VN - 1) / VN * VN;   // QR: one row block, R_A
+  static constexpr int per_warp = pad + kR * kR + kR;             // pass 2: p and a/q blocks, Omega, W row
+  static constexpr int per_warp_qr = (32 * ldb + kR * ldr + kR + VN - 1) / VN * VN;   // QR: row block, R_A, W row
   static constexpr size_t bytes = sizeof(Real) * ((size_t)kR * kR + (kWNT / 32) * (size_t)per_warp) + 16;
   static constexpr size_t qr_bytes = sizeof(Real) * ((size_t)kR * kR + (kWNT / 32) * (size_t)per_warp_qr) + 16;
 };
@@ -914,24 +943,11 @@ struct TallLay {
 // a_i = (p_i * w) H^T from the p row kept in shared memory. Returns the row's nonzeros.
 template <typename Real, int kR>
 __device__ __forceinline__ int tall_row(const TensorView& X, int R, const Real* __restrict__ V, const Real* Hs,
-                                        const Real* __restrict__ wk, int64_t i, bool valid, Real* prow, Real* z) {
+                                        const Real* wk, int64_t i, bool valid, Real* prow, Real* z) {
   using Vc = Vec16<Real>;
   constexpr int VN = Vc::n;
   Real p[kR];
-#pragma unroll
-  for (int t = 0; t < kR; ++t) p[t] = Real(0);
-  int nnz = 0;
-  if (valid) {
-    const int64_t a = X.row_ptr[i], b = X.row_ptr[i + 1];
-    nnz = (int)(b - a);
-    for (int64_t q = a; q < b; ++q) {
-      const Real x = load_x<Real>(X, q);
-      const Real* vr = V + (int64_t)__ldg(X.col + q) * R;
-#pragma unroll
-      for (int t = 0; t < kR; ++t)
-        if (t < R) p[t] += x * __ldg(vr + t);
-    }
-  }
+  const int nnz = row_p<Real, kR>(X, R, V, i, valid, p);
 #pragma unroll
   for (int t = 0; t < kR; ++t) prow[t] = p[t];
 #pragma unroll
@@ -974,6 +990,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_qr(
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   Real* Bs = Hs + kR * kR + (size_t)warp * Lt::per_warp_qr;   // 32 rows of A_k
   Real* Rs = Bs + 32 * ldb;                                     // R_A
+  Real* Wb = Rs + kR * ldr;                                     // this subject's row of W
   load_hs<Real, kR>(H, R, Hs);
   __syncthreads();
   const int64_t nt = min((int64_t)max(*count, 0), X.K);
@@ -987,12 +1004,14 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_qr(
     const int64_t k = order[idx];
     const int64_t r0 = X.subj_ptr[k], r1 = X.subj_ptr[k + 1];
     const Real* wk = W + k * R;
+    for (int r = lane; r < kR; r += 32) Wb[r] = r < R ? wk[r] : Real(0);
     for (int e = lane; e < kR * ldr; e += 32) Rs[e] = Real(0);
+    __syncwarp();
     int nnzk = 0;
     for (int64_t g = r0; g < r1; g += 32) {
       const int nb = (int)min((int64_t)32, r1 - g);
       Real z[kR];
-      nnzk += tall_row<Real, kR>(X, R, V, Hs, wk, g + lane, lane < nb, Bs + lane * ldb, z);
+      nnzk += tall_row<Real, kR>(X, R, V, Hs, Wb, g + lane, lane < nb, Bs + lane * ldb, z);
 #pragma unroll
       for (int t = 0; t < kR; ++t) Bs[lane * ldb + t] = z[t];
       __syncwarp();
@@ -1091,6 +1110,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_pass2(
   Real* Bp = Hs + kR * kR + (size_t)warp * Lt::per_warp;   // p rows of a block
   Real* Ba = Bp + 32 * ldb;                                 // a rows, then q rows
   Real* Om = Bp + Lt::pad;                                  // Omega (kR x kR, zero-padded)
+  Real* Wb = Om + kR * kR;                                  // this subject's row of W
   load_hs<Real, kR>(H, R, Hs);
   __syncthreads();
   double* fh = fh_partial ? fh_partial + ((size_t)blockIdx.x * (kWNT / 32) + warp) * R * R : nullptr;
@@ -1112,6 +1132,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_pass2(
     // Omega was written by the previous launch: read it through L2
     for (int r = 0; r < kR; ++r)
       for (int t = lane; t < kR; t += 32) Om[r * kR + t] = (r < R && t < R) ? __ldcg(Tk + r * R + t) : Real(0);
+    for (int r = lane; r < kR; r += 32) Wb[r] = r < R ? wk[r] : Real(0);
     __syncwarp();
     Real acc[kTR][kTC];
 #pragma unroll
@@ -1122,7 +1143,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_pass2(
     for (int64_t g = r0; g < r1; g += 32) {
       const int nb = (int)min((int64_t)32, r1 - g);
       Real z[kR];
-      nnzk += tall_row<Real, kR>(X, R, V, Hs, wk, g + lane, lane < nb, Bp + lane * ldb, z);
+      nnzk += tall_row<Real, kR>(X, R, V, Hs, Wb, g + lane, lane < nb, Bp + lane * ldb, z);
 #pragma unroll
       for (int t = 0; t < kR; ++t) Ba[lane * ldb + t] = z[t];
       // q_i = a_i Omega (own row of Ba, rows of Omega broadcast)
@@ -1188,7 +1209,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_pass2(
   if (fma_count && lane == 0) atomicAdd(fma_count, fma);
 }
 
-// k_tall_jacobi: warp per tall subject, the one-sided Jacobi on the rows of R_A (left in
+// k_tall_jacobi: warp per subject, the one-sided Jacobi on the rows of R_A (left in
 // T_k by k_tall_qr) without block barriers. The n2 = R + (R & 1) rows sit two per lane in
 // lanes 0 .. n2/2 - 1, the two rows of a pair in the same registers-resident lane; after
 // each round the rows move one step along the circle of the circle method (tops one lane
@@ -1218,7 +1239,10 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_jacobi(
   const Real tol = Tol<Real>::v();
   const int n2 = R + (R & 1), L = n2 / 2;
   const bool own = lane < L;
-  const int ra = lane, rb = L + lane;   // rows held at the start (top, bottom)
+  // rows held at the start: lane l holds positions l (top) and n2-1-l (bottom) of the circle
+  // method, except lane 0, which keeps the fixed position 0 in its bottom registers and
+  // the moving position n2-1 in its top ones (so both moves below are plain shuffles)
+  const int ra = lane == 0 ? n2 - 1 : lane, rb = lane == 0 ? 0 : n2 - 1 - lane;
   const int64_t nt = min((int64_t)max(*count, 0), K);
   const int tr = lane >> 2, tc = lane & 3;
   unsigned long long fma = 0;
@@ -1236,8 +1260,85 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_jacobi(
       top[t] = (own && ra < R && t < R) ? __ldcg(Tk + ra * R + t) : Real(0);
       bot[t] = (own && rb < R && t < R) ? __ldcg(Tk + rb * R + t) : Real(0);
     }
-    Real na, nb;
-    {
+    Real na = Real(0), nb = Real(0);
+    int sweeps = 0;
+    unsigned long long nrot = 0;
+    for (int sweep = 0; sweep < kMaxSweeps && n2 > 1; ++sweep) {
+      ++sweeps;
+      bool any = false;
+      {   // exact squared norms at the start of every sweep
+        Real a4[4] = {Real(0), Real(0), Real(0), Real(0)}, b4[4] = {Real(0), Real(0), Real(0), Real(0)};
+#pragma unroll
+        for (int t = 0; t < kR; ++t) {
+          a4[t & 3] += top[t] * top[t];
+          b4[t & 3] += bot[t] * bot[t];
+        }
+        na = (a4[0] + a4[1]) + (a4[2] + a4[3]);
+        nb = (b4[0] + b4[1]) + (b4[2] + b4[3]);
+      }
+      for (int rd = 0; rd < n2 - 1; ++rd) {
+        Real g4[4] = {Real(0), Real(0), Real(0), Real(0)};
+#pragma unroll
+        for (int t = 0; t < kR; ++t) g4[t & 3] += top[t] * bot[t];
+        const Real gg = (g4[0] + g4[1]) + (g4[2] + g4[3]);
+        const bool rot = own && gg != Real(0) && fabs(gg) > tol * sqrt(na * nb);
+        if (rot) {
+          Real c, s, tt;
+          rotation_of(na, nb, gg, &c, &s, &tt);
+#pragma unroll
+          for (int t = 0; t < kR; ++t) {
+            const Real x = top[t], y = bot[t];
+            top[t] = c * x - s * y;
+            bot[t] = s * x + c * y;
+          }
+          // updated norms; recomputed where one of them drops by half or more, so that
+          // rounding in the update stays small relative to the new norm
+          const Real na1 = na - tt * gg, nb1 = nb + tt * gg;
+          if (na1 < Real(0.5) * na || nb1 < Real(0.5) * nb) {
+            Real a4[4] = {Real(0), Real(0), Real(0), Real(0)}, b4[4] = {Real(0), Real(0), Real(0), Real(0)};
+#pragma unroll
+            for (int t = 0; t < kR; ++t) {
+              a4[t & 3] += top[t] * top[t];
+              b4[t & 3] += bot[t] * bot[t];
+            }
+            na = (a4[0] + a4[1]) + (a4[2] + a4[3]);
+            nb = (b4[0] + b4[1]) + (b4[2] + b4[3]);
+          } else {
+            na = na1;
+            nb = nb1;
+          }
+        }
+        const unsigned rmask = __ballot_sync(kFull, rot);
+        any |= rmask != 0u;
+        if (lane == 0) nrot += __popc(rmask);
+        // next round: lane l's top <- lane l-1's top (lane 1 takes lane 0's moving row), lane
+        // l's bottom <- lane l+1's bottom; lane 0's moving row <- lane 1's bottom, the last
+        // lane's bottom <- its own top
+        if (L < 2) continue;   // a single pair: nothing moves
+        const int up_src = lane > 0 ? lane - 1 : 0;
+#pragma unroll
+        for (int t = 0; t < kR; ++t) {
+          const Real up = __shfl_sync(kFull, top[t], up_src);
+          const Real dn = __shfl_down_sync(kFull, bot[t], 1);
+          const Real old_top = top[t];
+          if (own) {
+            top[t] = lane == 0 ? dn : up;
+            if (lane > 0) bot[t] = lane == L - 1 ? old_top : dn;
+          }
+        }
+        {
+          const Real up = __shfl_sync(kFull, na, up_src);
+          const Real dn = __shfl_down_sync(kFull, nb, 1);
+          const Real old_na = na;
+          if (own) {
+            na = lane == 0 ? dn : up;
+            if (lane > 0) nb = lane == L - 1 ? old_na : dn;
+          }
+        }
+      }
+      if (!any) break;
+    }
+    {   // exact squared norms for the rank cut
       Real a4[4] = {Real(0), Real(0), Real(0), Real(0)}, b4[4] = {Real(0), Real(0), Real(0), Real(0)};
 #pragma unroll
       for (int t = 0; t < kR; ++t) {
@@ -1246,56 +1347,6 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_jacobi(
       }
       na = (a4[0] + a4[1]) + (a4[2] + a4[3]);
       nb = (b4[0] + b4[1]) + (b4[2] + b4[3]);
-    }
-    int sweeps = 0;
-    unsigned long long nrot = 0;
-    for (int sweep = 0; sweep < kMaxSweeps && n2 > 1; ++sweep) {
-      ++sweeps;
-      bool any = false;
-      for (int rd = 0; rd < n2 - 1; ++rd) {
-        Real g4[4] = {Real(0), Real(0), Real(0), Real(0)};
-#pragma unroll
-        for (int t = 0; t < kR; ++t) g4[t & 3] += top[t] * bot[t];
-        const Real gg = (g4[0] + g4[1]) + (g4[2] + g4[3]);
-        const bool rot = own && gg != Real(0) && fabs(gg) > tol * sqrt(na * nb);
-        if (rot) {
-          Real c, s;
-          rotation_of(na, nb, gg, &c, &s);
-          Real a4[4] = {Real(0), Real(0), Real(0), Real(0)}, b4[4] = {Real(0), Real(0), Real(0), Real(0)};
-#pragma unroll
-          for (int t = 0; t < kR; ++t) {
-            const Real x = top[t], y = bot[t];
-            top[t] = c * x - s * y;
-            bot[t] = s * x + c * y;
-            a4[t & 3] += top[t] * top[t];
-            b4[t & 3] += bot[t] * bot[t];
-          }
-          na = (a4[0] + a4[1]) + (a4[2] + a4[3]);
-          nb = (b4[0] + b4[1]) + (b4[2] + b4[3]);
-        }
-        const unsigned rmask = __ballot_sync(kFull, rot);
-        any |= rmask != 0u;
-        if (lane == 0) nrot += __popc(rmask);
-        // next round: lane l's top <- lane l-1's top (lane 1 <- lane 0's bottom), lane l's
-        // bottom <- lane l+1's bottom (the last lane's bottom <- its own top)
-        const int up_src = lane > 0 ? lane - 1 : 0;
-#pragma unroll
-        for (int t = 0; t < kR; ++t) {
-          const Real up = __shfl_sync(kFull, lane == 0 ? bot[t] : top[t], up_src);
-          const Real dn = __shfl_down_sync(kFull, bot[t], 1);
-          const Real nbt = lane == L - 1 ? top[t] : dn;
-          if (lane > 0 && own) top[t] = up;
-          if (own) bot[t] = nbt;
-        }
-        {
-          const Real up = __shfl_sync(kFull, lane == 0 ? nb : na, up_src);
-          const Real dn = __shfl_down_sync(kFull, nb, 1);
-          const Real nbn = lane == L - 1 ? na : dn;
-          if (lane > 0 && own) na = up;
-          if (own) nb = nbn;
-        }
-      }
-      if (!any) break;
     }
 
     // ---- rank cut; c_j = z_j / sigma_j, Omega = sum_j c_j c_j^T / sigma_j ----
@@ -1453,10 +1504,10 @@ size_t procrustes_smem(int R) {
   return lay_of<Real>(R).total * sizeof(Real);
 }
 
-// Launch order (lane-per-row kernels available for this R and precision):
-//   k_tall_qr (I_k > R: R_A -> T_k), k_tall_jacobi (I_k > R: Omega -> T_k),
-//   k_procrustes (min(R, 32) < I_k <= R), k_tall_pass2 (I_k > R: Q rows, T_k, F_H),
-//   k_procrustes_warp (I_k <= min(R, 32)). Otherwise k_procrustes takes every subject.
+// Launch order where the lane-per-row kernels exist for this R and precision: the subjects
+// with I_k > min(R, 32) go through k_tall_qr (R_A -> T_k), k_tall_jacobi (Omega -> T_k) and
+// k_tall_pass2 (Q rows, T_k, F_H); the others through k_procrustes_warp. Otherwise the
+// block kernel k_procrustes takes every subject.
 template <typename Real>
 copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const Real* H,
                                 const Real* V, const Real* W, double tau, Real* Q, Real* T,
@@ -1476,11 +1527,13 @@ copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const R
                        "occupancy")) != COPA_OK)
     return st;
   if (per_sm < 1) per_sm = 1;
-  int64_t blocks = (int64_t)h->num_sms * per_sm;
-  if (blocks > X.K) blocks = X.K > 0 ? X.K : 1;
-
   const RowKernels<Real> rk = row_kernels_for<Real>((R + 7) / 8 * 8);
   const bool rows = rk.small != nullptr;
+  int64_t blocks = 0;   // block kernel grid (only without the lane-per-row kernels)
+  if (!rows) {
+    blocks = (int64_t)h->num_sms * per_sm;
+    if (blocks > X.K) blocks = X.K > 0 ? X.K : 1;
+  }
   int64_t sblocks = 0, qblocks = 0, jblocks = 0, pblocks = 0;
   if (rows) {
     if ((st = row_grid(h, rk.small, rk.small_smem, X.K, &sblocks)) != COPA_OK) return st;
@@ -1491,7 +1544,6 @@ copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const R
   const int64_t* order = nullptr;
   if ((st = get_schedule(h, X, &order)) != COPA_OK) return st;
   const int* n_big = rows ? schedule_count_above(h, std::min(R, 32)) : nullptr;   // I_k > min(R, 32)
-  const int* n_tall = rows ? schedule_count_above(h, R) : nullptr;                // I_k > R
   int* counter = nullptr;
   if ((st = ws_get(h, SLOT_COUNTER, 64, (void**)&counter)) != COPA_OK) return st;
   unsigned long long* fma_count = reinterpret_cast<unsigned long long*>(counter + 2);
@@ -1507,29 +1559,24 @@ copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const R
   if ((st = cuda_check(h, cudaMemsetAsync(counter, 0, 32, h->stream), "memset")) != COPA_OK)
     return st;
   if (rows) {
-    rk.qr<<<(unsigned)qblocks, kWNT, rk.qr_smem, h->stream>>>(X, R, H, V, W, order, n_tall, counter + 5, T,
-                                                                fma_count);
+    rk.qr<<<(unsigned)qblocks, kWNT, rk.qr_smem, h->stream>>>(X, R, H, V, W, order, n_big, counter + 5, T, fma_count);
     if ((st = cuda_check(h, cudaGetLastError(), "k_tall_qr launch")) != COPA_OK) return st;
-  }
-  if (rows) {
-    rk.jac<<<(unsigned)jblocks, kWNT, rk.jac_smem, h->stream>>>(X.K, R, tau, order, n_tall, counter + 7, T, Pi, rank,
+    rk.jac<<<(unsigned)jblocks, kWNT, rk.jac_smem, h->stream>>>(X.K, R, tau, order, n_big, counter + 7, T, Pi, rank,
                                                                   fma_count);
     if ((st = cuda_check(h, cudaGetLastError(), "k_tall_jacobi launch")) != COPA_OK) return st;
-  }
-  k_procrustes<Real><<<(unsigned)blocks, kNT, smem, h->stream>>>(X, R, H, V, W, tau, Q, T, Pi, rank, part,
-                                                                order, counter, fma_count, Uw, woff,
-                                                                warm_in ? 1 : 0, n_big, n_tall);
-  if ((st = cuda_check(h, cudaGetLastError(), "k_procrustes launch")) != COPA_OK) return st;
-  if (rows) {
-    double* ppart = part ? part + (size_t)blocks * R * R : nullptr;
-    rk.pass2<<<(unsigned)pblocks, kWNT, rk.tall_smem, h->stream>>>(X, R, H, V, W, order, n_tall, counter + 6, Q, T,
-                                                                     ppart, fma_count);
+    rk.pass2<<<(unsigned)pblocks, kWNT, rk.tall_smem, h->stream>>>(X, R, H, V, W, order, n_big, counter + 6, Q, T,
+                                                                     part, fma_count);
     if ((st = cuda_check(h, cudaGetLastError(), "k_tall_pass2 launch")) != COPA_OK) return st;
-    double* spart = part ? part + (size_t)(blocks + pblocks * wpb) * R * R : nullptr;
+    double* spart = part ? part + (size_t)pblocks * wpb * R * R : nullptr;
     rk.small<<<(unsigned)sblocks, kWNT, rk.small_smem, h->stream>>>(
         X, R, H, V, W, tau, Q, T, Pi, rank, spart, order, n_big, counter + 4, fma_count, Uw, woff,
         warm_in ? 1 : 0, h->d_status);
     if ((st = cuda_check(h, cudaGetLastError(), "k_procrustes_warp launch")) != COPA_OK) return st;
+  } else {
+    k_procrustes<Real><<<(unsigned)blocks, kNT, smem, h->stream>>>(X, R, H, V, W, tau, Q, T, Pi, rank, part, order,
+                                                                  counter, fma_count, Uw, woff, warm_in ? 1 : 0,
+                                                                  nullptr, nullptr);
+    if ((st = cuda_check(h, cudaGetLastError(), "k_procrustes launch")) != COPA_OK) return st;
   }
   if (F_H) {
     k_reduce_partials<Real><<<(R * R + 255) / 256, 256, 0, h->stream>>>(part, (int)nparts, R * R, F_H);

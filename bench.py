@@ -12,6 +12,7 @@ a bounded random sample of subjects, scaled to the full K.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -177,6 +178,31 @@ def kernel_breakdown(h, P, Xd, R, H, V, W, reps=2):
     return {n: acc[n] / reps for n in names}
 
 
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_procrustes_step_dram_ehr_K100k_J1500_R40.txt")
+
+
+def procrustes_traffic(K):
+    """DRAM bytes (read + write) of one Procrustes step over K subjects, from the committed
+    ncu summary of the same kernels on the K = 100,000 workload, scaled by the number of
+    subjects (the workload draws subjects independently, so traffic grows in proportion);
+    None when k_procrustes.cu changed since the counters were taken."""
+    try:
+        with open(TRAFFIC_PROFILE) as f:
+            lines = f.read().splitlines()
+        with open(os.path.join(ROOT, "paper_1803_04572_gb300", "csrc", "k_procrustes.cu"), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    kv = {}
+    for ln in lines:
+        if "=" in ln and not ln.lstrip().startswith("#"):
+            k, v = ln.split("=", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_sha256") != sha or "dram_bytes_per_step" not in kv:
+        return None
+    return float(kv["dram_bytes_per_step"]) * K / float(kv["subjects"])
+
+
 def procrustes_roofline(h, P, Xd, X, R, H, V, W, peaks, reps=3):
     """Average duration of the Procrustes launch (the dominant kernel), timed with CUDA
     events on the handle's stream, and its algorithmic work: the multiply-adds the kernel
@@ -196,7 +222,7 @@ def procrustes_roofline(h, P, Xd, X, R, H, V, W, peaks, reps=3):
     key = "fp32_tflops" if h.precision == "mixed" else "fp64_tflops"
     peak = peaks[key]
     return ms, {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "k_procrustes",
+                "frac": achieved / peak, "traffic": procrustes_traffic(X.K), "kernel": "k_procrustes",
                 "work_fma_per_launch": fma, "peak_source": peaks[key.replace("tflops", "source")]}
 
 

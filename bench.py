@@ -30,6 +30,16 @@ WORKLOAD = "ehr_K500k_J1500_R40"
 METRIC = "AO-ADMM outer iters/sec (K=500k, J=1500, R=40)"
 R_RANK, N_INNER, LAM_V = 40, 20, 1.0
 
+# The other configurations: parity cases of the tests, measured here on request.
+#   smoothing (K=20k, J=500, R=10): the B-spline projection once, then the fit on it;
+#   backward (K=50k, J=1000, R=20): loss and gradients with Q from one Procrustes step;
+#   rank sweep (K=100k, J=1000, R from --rank).
+OTHER_WORKLOADS = {
+    "ehr_K20k_J500_R10_smooth": dict(gen="ehr_K20k", R=10, n_inner=10, smooth=True),
+    "ehr_K50k_J1000_R20_backward": dict(gen="ehr_K50k", R=20, backward=True),
+    "ehr_K100k_J1000": dict(gen="ehr_K100k", R=None, n_inner=10),
+}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -43,6 +53,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD] + sorted(OTHER_WORKLOADS),
+                    help="the headline workload (default) or one of the other configurations, "
+                         "which print their own line (no e2e, no CPU baseline)")
+    ap.add_argument("--rank", type=int, default=40, help="R for ehr_K100k_J1000 (the rank sweep)")
     return ap.parse_args()
 
 
@@ -294,6 +308,76 @@ def gpu_leg(args, X, init, rank, world):
     return out
 
 
+def config_leg(args):
+    """One line for a configuration other than the headline one (1 GPU)."""
+    import torch
+    import synth
+    import paper_1803_04572_gb300 as P
+    cfg = OTHER_WORKLOADS[args.workload]
+    R = cfg["R"] or args.rank
+    t = time.time()
+    X = getattr(synth, cfg["gen"])()
+    gen_s = time.time() - t
+    H0, V0, W0 = synth.init_factors(X.K, X.J, R)
+    h = P.Copa(0, args.precision)
+    vd = "bf16" if args.precision == "mixed" else "f64"
+    Xd = P.DeviceTensor.from_host(X, h.device, vd)
+    h.validate(Xd)
+    H, V, W = (torch.as_tensor(a, dtype=h.dtype, device=h.device) for a in (H0, V0, W0))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    extra = {}
+    if cfg.get("backward"):
+        metric = f"backward passes/sec (K={X.K // 1000}k, J={X.J}, R={R})"
+        st = h.procrustes(Xd, R, H, V, W, want_pi=True)
+        for _ in range(args.warmup):
+            h.loss_grad(Xd, R, st, H, V, W)
+        h.sync()
+        clk = Clocks(0)
+        clk.start()
+        e0.record(h.stream)
+        for _ in range(args.steps):
+            loss, gH, gV, gW = h.loss_grad(Xd, R, st, H, V, W)
+        e1.record(h.stream)
+        h.sync()
+        extra["loss"] = float(loss.cpu()[0])
+        launches = None
+    else:
+        Xfit, xn2 = Xd, 0.0
+        if cfg.get("smooth"):
+            days = torch.as_tensor(X.days, dtype=torch.float64, device=h.device)
+            h.sync()
+            t0 = time.perf_counter()
+            Xfit, _ = h.smooth(Xd, days, 7, 3, out_dtype="f64" if args.precision == "fp64" else "f32")
+            h.sync()
+            extra["smoothing_setup_ms"] = (time.perf_counter() - t0) * 1e3
+            xn2 = float(np.sum(np.asarray(X.val, dtype=np.float64) ** 2))
+        metric = (f"AO-ADMM outer iters/sec (K={X.K // 1000}k, J={X.J}, R={R}"
+                  + (", smoothed)" if cfg.get("smooth") else ")"))
+        DH, DV, DW = torch.zeros_like(H), torch.zeros_like(V), torch.zeros_like(W)
+        mk = lambda n: P.Options(R, n_outer=n, n_inner=cfg["n_inner"], c_H="none", c_W="nonneg", c_V="l1",
+                                 lam_V=LAM_V, x_norm2=xn2, use_graph=True)
+        h.fit(Xfit, mk(args.warmup), H, V, W, DH, DV, DW)
+        h.sync()
+        clk = Clocks(0)
+        clk.start()
+        e0.record(h.stream)
+        hist = h.fit(Xfit, mk(args.steps), H, V, W, DH, DV, DW)
+        e1.record(h.stream)
+        h.sync()
+        launches = h.fit_launches()
+        extra["fit_last"] = float(hist[-1])
+    ms = e0.elapsed_time(e1) / args.steps
+    line = {"metric": metric, "unit": "1/s", "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": args.workload, "K": X.K, "J": X.J, "R": R, "nnz": X.nnz, "visits": X.S,
+                       "precision": args.precision, "parallelism": "1 GPU"},
+            "value": 1000.0 / ms, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 bulk (bf16 counts), f64 Gram/eigen/Cholesky/FIT" if args.precision == "mixed" else "f64",
+            "clocks": clk.stop(), "gpu_launches": launches, "generation_s": gen_s}
+    line.update(extra)
+    print(json.dumps(line))
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     d = json.load(open(p)) if os.path.exists(p) else {}
@@ -313,6 +397,9 @@ PEAKS = load_peaks()
 
 def main():
     args = parse()
+    if args.workload != WORKLOAD:
+        config_leg(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1:

@@ -173,12 +173,26 @@ __global__ void __launch_bounds__(kUNT) k_uvec(
   }
 }
 
+// Compensated (two-float) accumulation of FP32 addends: hi + lo carries the sum to about
+// twice the float precision (Knuth's TwoSum per addend) at a few float operations, where a
+// float-to-double conversion and a double add per addend would run on the FP64 unit
+// (1/58 of the FP32 rate on this part). The FP64 path accumulates in double directly.
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x) {
+  const float s = hi + x, bp = s - hi;
+  lo += (hi - (s - bp)) + (x - bp);
+  hi = s;
+}
+__device__ __forceinline__ void two_sum_add(double& hi, double& lo, double x) {
+  hi += x;
+  (void)lo;
+}
+
 // Tiled form of step 1 for R <= 48: a block takes kVT consecutive visit rows at a time
 // (rows of any subjects; the subject of a row comes from the row -> subject map), forms
 // the kVT x R tile of U = (Q H) .* W(k(i), :) as a small GEMM from shared memory (a thread
 // owns 4 rows x NC columns), writes the tile out coalesced, and adds the tile's Gram to
 // U^T U: four groups of 64 threads take 32 rows each, a thread owning an NC x NC block,
-// summed in FP32 within a tile and in FP64 across tiles.
+// summed in FP32 within a tile and across tiles as a compensated float pair (double at the end).
 constexpr int kVT = 128;    // rows per tile
 constexpr int kVNT = 256;   // threads per block
 
@@ -199,11 +213,11 @@ __global__ void __launch_bounds__(kVNT, 2) k_uvec_tiled(int64_t S, int R, const 
     const int r = e / HL, c = e - r * HL;
     Hs[e] = (r < R && c < R) ? H[r * R + c] : Real(0);
   }
-  double dacc[NC][NC];
+  Real ghi[NC][NC], glo[NC][NC];   // this thread's U^T U block, compensated
 #pragma unroll
   for (int a = 0; a < NC; ++a)
 #pragma unroll
-    for (int b = 0; b < NC; ++b) dacc[a][b] = 0.0;
+    for (int b = 0; b < NC; ++b) ghi[a][b] = glo[a][b] = Real(0);
 
   for (int64_t i0 = (int64_t)blockIdx.x * kVT; i0 < S; i0 += (int64_t)gridDim.x * kVT) {
     const int nrow = (int)min((int64_t)kVT, S - i0);
@@ -274,7 +288,7 @@ __global__ void __launch_bounds__(kVNT, 2) k_uvec_tiled(int64_t S, int R, const 
 #pragma unroll
       for (int a = 0; a < NC; ++a)
 #pragma unroll
-        for (int b = 0; b < NC; ++b) dacc[a][b] += (double)sacc[a][b];
+        for (int b = 0; b < NC; ++b) two_sum_add(ghi[a][b], glo[a][b], sacc[a][b]);
     }
   }
   if (utu_part) {
@@ -284,7 +298,7 @@ __global__ void __launch_bounds__(kVNT, 2) k_uvec_tiled(int64_t S, int R, const 
 #pragma unroll
       for (int b = 0; b < NC; ++b) {
         const int r = gp * NC + a, c = gq * NC + b;
-        if (r < R && c < R) up[r * R + c] = dacc[a][b];
+        if (r < R && c < R) up[r * R + c] = (double)ghi[a][b] + (double)glo[a][b];
       }
   }
 }

@@ -726,16 +726,23 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
       __syncwarp();
     }
 
-    // ---- Hestenes sweeps ----
-    Real al = Real(0);
+    // ---- Hestenes sweeps. The squared row norm is exact at the start of every sweep and
+    //      for the rank cut; within a sweep a rotation updates it by -+ t * gamma, recomputed
+    //      where it drops by half or more (so that its rounding stays relative). ----
+    auto sq_norm = [&]() {
+      Real a4[4] = {Real(0), Real(0), Real(0), Real(0)};
 #pragma unroll
-    for (int t = 0; t < kR; ++t) al += z[t] * z[t];
+      for (int t = 0; t < kR; ++t) a4[t & 3] += z[t] * z[t];
+      return (a4[0] + a4[1]) + (a4[2] + a4[3]);
+    };
+    Real al = Real(0);
     const int n2 = m + (m & 1);
     unsigned long long nrot = 0;
     int sweeps = 0;
     for (int sweep = 0; sweep < kMaxSweeps && n2 > 1; ++sweep) {
       ++sweeps;
       bool any = false;
+      al = sq_norm();
       for (int rd = 0; rd < n2 - 1; ++rd) {
         int j;
         if (lane >= n2) j = lane;
@@ -761,17 +768,16 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
         if (rmask == 0u) continue;
         any = true;
         if (lane == 0) nrot += __popc(rmask) / 2;
-        Real c = Real(1), s = Real(0);
-        if (rot) rotation_of(aa, bb, gg, &c, &s);
+        Real c = Real(1), s = Real(0), tt = Real(0);
+        if (rot) rotation_of(aa, bb, gg, &c, &s, &tt);
         // lower row x, upper row y: x' = c x - s y, y' = s x + c y
         const Real so = lo ? -s : s;
-        Real na[4] = {Real(0), Real(0), Real(0), Real(0)};
 #pragma unroll
-        for (int t = 0; t < kR; ++t) {
-          z[t] = c * z[t] + so * zp[t];
-          na[t & 3] += z[t] * z[t];
+        for (int t = 0; t < kR; ++t) z[t] = c * z[t] + so * zp[t];
+        if (rot) {
+          const Real al1 = lo ? al - tt * gg : al + tt * gg;
+          al = al1 < Real(0.5) * al ? sq_norm() : al1;
         }
-        if (rot) al = (na[0] + na[1]) + (na[2] + na[3]);
         // U rows, in chunks of 8 entries up to m
 #pragma unroll
         for (int c8 = 0; c8 < kM; c8 += 8) {
@@ -786,6 +792,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
       }
       if (!any) break;
     }
+    al = sq_norm();
     if (Uk && lane < m) {
 #pragma unroll
       for (int jj = 0; jj < kM; ++jj)

@@ -97,6 +97,48 @@ __device__ __forceinline__ void rotation_of(Real aa, Real bb, Real gg, Real* c, 
   if (t) *t = tt;
 }
 
+template <typename Real, int kR>
+__device__ __forceinline__ Real sq_sum(const Real (&x)[kR]) {
+  Real a4[4] = {Real(0), Real(0), Real(0), Real(0)};
+#pragma unroll
+  for (int t = 0; t < kR; ++t) a4[t & 3] += x[t] * x[t];
+  return (a4[0] + a4[1]) + (a4[2] + a4[3]);
+}
+
+// One row of a pair split over two lanes (this lane's row x, the partner's in lane j).
+// Rows are held scaled: the row is f * x, and n is its squared norm. The partner row is
+// read with shuffles and both lanes form the same rotation (the same products summed in
+// the same order, the same norms); each lane then updates only its own row, which in the
+// scaled form is one multiply-add per component: x += m * x_partner with
+// m = -+ t * f_partner / f, and f *= c (c >= 1/sqrt(2), so f stays far from underflow
+// within a sweep). lo: this lane holds the pair's first row. Returns whether it rotated.
+template <typename Real, int kR>
+__device__ __forceinline__ bool pair_rotate(Real (&x)[kR], Real& f, Real& n, int j, bool lo, bool pair, Real tol) {
+  constexpr unsigned kFull = 0xffffffffu;
+  Real xp[kR];
+  Real g4[4] = {Real(0), Real(0), Real(0), Real(0)};
+#pragma unroll
+  for (int t = 0; t < kR; ++t) {
+    xp[t] = __shfl_sync(kFull, x[t], j);
+    g4[t & 3] += x[t] * xp[t];
+  }
+  const Real fp = __shfl_sync(kFull, f, j), np = __shfl_sync(kFull, n, j);
+  const Real gg = (f * fp) * ((g4[0] + g4[1]) + (g4[2] + g4[3]));
+  const Real aa = lo ? n : np, bb = lo ? np : n;
+  const bool rot = pair && gg != Real(0) && fabs(gg) > tol * sqrt(aa * bb);
+  if (rot) {
+    Real c, s, tt;
+    rotation_of(aa, bb, gg, &c, &s, &tt);
+    const Real m = (lo ? -tt : tt) * fdiv_(fp, f);
+#pragma unroll
+    for (int t = 0; t < kR; ++t) x[t] += m * xp[t];
+    f *= c;
+    const Real n1 = lo ? n - tt * gg : n + tt * gg;
+    n = n1 < Real(0.5) * n ? f * f * sq_sum<Real, kR>(x) : n1;
+  }
+  return rot;
+}
+
 constexpr int kEPL = 12;   // components per thread held in registers by the block Jacobi
 
 template <typename Real>
@@ -726,23 +768,28 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
       __syncwarp();
     }
 
-    // ---- Hestenes sweeps. The squared row norm is exact at the start of every sweep and
-    //      for the rank cut; within a sweep a rotation updates it by -+ t * gamma, recomputed
-    //      where it drops by half or more (so that its rounding stays relative). ----
-    auto sq_norm = [&]() {
-      Real a4[4] = {Real(0), Real(0), Real(0), Real(0)};
+    // ---- Hestenes sweeps. The lane's rows of Z and U are held scaled by f (the rows are
+    //      f z and f u), so that a rotation is one multiply-add per component (see
+    //      pair_rotate); f is folded back at the start of every sweep. The squared row norm
+    //      al is exact at the start of every sweep and for the rank cut; within a sweep a
+    //      rotation updates it by -+ t * gamma, recomputed where it drops by half or more
+    //      (so that its rounding stays relative). ----
+    auto fold = [&](Real f) {
 #pragma unroll
-      for (int t = 0; t < kR; ++t) a4[t & 3] += z[t] * z[t];
-      return (a4[0] + a4[1]) + (a4[2] + a4[3]);
+      for (int t = 0; t < kR; ++t) z[t] *= f;
+#pragma unroll
+      for (int jj = 0; jj < kM; ++jj) u[jj] *= f;
     };
-    Real al = Real(0);
+    Real al = Real(0), f = Real(1);
     const int n2 = m + (m & 1);
     unsigned long long nrot = 0;
     int sweeps = 0;
     for (int sweep = 0; sweep < kMaxSweeps && n2 > 1; ++sweep) {
       ++sweeps;
       bool any = false;
-      al = sq_norm();
+      fold(f);
+      f = Real(1);
+      al = sq_sum<Real, kR>(z);
       for (int rd = 0; rd < n2 - 1; ++rd) {
         int j;
         if (lane >= n2) j = lane;
@@ -760,23 +807,27 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
           zp[t] = __shfl_sync(kFull, z[t], j);
           g[t & 3] += z[t] * zp[t];
         }
-        const Real be = __shfl_sync(kFull, al, j);
+        const Real be = __shfl_sync(kFull, al, j), fp = __shfl_sync(kFull, f, j);
         const bool lo = lane < j;
-        const Real aa = lo ? al : be, bb = lo ? be : al, gg = (g[0] + g[1]) + (g[2] + g[3]);
+        const Real aa = lo ? al : be, bb = lo ? be : al;
+        const Real gg = (f * fp) * ((g[0] + g[1]) + (g[2] + g[3]));
         const bool rot = j != lane && gg != Real(0) && fabs(gg) > tol * sqrt(aa * bb);
         const unsigned rmask = __ballot_sync(kFull, rot);
         if (rmask == 0u) continue;
         any = true;
         if (lane == 0) nrot += __popc(rmask) / 2;
-        Real c = Real(1), s = Real(0), tt = Real(0);
-        if (rot) rotation_of(aa, bb, gg, &c, &s, &tt);
-        // lower row x, upper row y: x' = c x - s y, y' = s x + c y
-        const Real so = lo ? -s : s;
-#pragma unroll
-        for (int t = 0; t < kR; ++t) z[t] = c * z[t] + so * zp[t];
+        // lower row x, upper row y: x' = c x - s y, y' = s x + c y; in the scaled form
+        // the own row takes -+ t (fp / f) times the partner's and the scale takes c
+        Real mu = Real(0);
         if (rot) {
+          Real c, s, tt;
+          rotation_of(aa, bb, gg, &c, &s, &tt);
+          mu = (lo ? -tt : tt) * fdiv_(fp, f);
+#pragma unroll
+          for (int t = 0; t < kR; ++t) z[t] += mu * zp[t];
+          f *= c;
           const Real al1 = lo ? al - tt * gg : al + tt * gg;
-          al = al1 < Real(0.5) * al ? sq_norm() : al1;
+          al = al1 < Real(0.5) * al ? f * f * sq_sum<Real, kR>(z) : al1;
         }
         // U rows, in chunks of 8 entries up to m
 #pragma unroll
@@ -785,14 +836,15 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
 #pragma unroll
             for (int jj = c8; jj < c8 + 8; ++jj) {
               const Real up = __shfl_sync(kFull, u[jj], j);
-              u[jj] = c * u[jj] + so * up;
+              u[jj] += mu * up;
             }
           }
         }
       }
       if (!any) break;
     }
-    al = sq_norm();
+    fold(f);
+    al = sq_sum<Real, kR>(z);
     if (Uk && lane < m) {
 #pragma unroll
       for (int jj = 0; jj < kM; ++jj)
@@ -1217,12 +1269,16 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_pass2(
 }
 
 // k_tall_jacobi: warp per subject, the one-sided Jacobi on the rows of R_A (left in
-// T_k by k_tall_qr) without block barriers. The n2 = R + (R & 1) rows sit two per lane in
-// lanes 0 .. n2/2 - 1, the two rows of a pair in the same registers-resident lane; after
-// each round the rows move one step along the circle of the circle method (tops one lane
-// up, bottoms one lane down, lane 0's top fixed), so the n2 - 1 rounds of a sweep meet
-// every pair once. Omega_k = C_K Sigma_K^{-1} C_K^T goes back to T_k, with rank_k and,
-// on request, Pi_k = C_K C_K^T.
+// T_k by k_tall_qr) without block barriers. The n2 = R + (R & 1) rows sit two per lane
+// (a "top" and a "bottom" row) in lanes 0 .. L - 1, L = n2 / 2. A sweep meets every pair
+// once in two phases: (1) L rounds of top against bottom in the same lane, the bottoms
+// moving one lane down the ring after each round (one shuffle per component, the same
+// source rule in every lane); (2) the top-top and bottom-bottom pairs across lanes, the
+// lanes paired by the circle method, each lane updating its own rows (pair_rotate).
+// Rows are held scaled (row = f * x), so that a rotation costs one multiply-add per
+// component and row; the scales are folded back at the start of every sweep.
+// Omega_k = C_K Sigma_K^{-1} C_K^T goes back to T_k, with rank_k and, on request,
+// Pi_k = C_K C_K^T.
 template <typename Real, int kR>
 struct TallJLay {
   static constexpr int ld = kR + 1;
@@ -1246,12 +1302,10 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_jacobi(
   const Real tol = Tol<Real>::v();
   const int n2 = R + (R & 1), L = n2 / 2;
   const bool own = lane < L;
-  // rows held at the start: lane l holds positions l (top) and n2-1-l (bottom) of the circle
-  // method, except lane 0, which keeps the fixed position 0 in its bottom registers and
-  // the moving position n2-1 in its top ones (so both moves below are plain shuffles)
-  const int ra = lane == 0 ? n2 - 1 : lane, rb = lane == 0 ? 0 : n2 - 1 - lane;
+  const int Le = L + (L & 1);   // circle-method positions of phase 2 (lane L is idle when L is odd)
   const int64_t nt = min((int64_t)max(*count, 0), K);
   const int tr = lane >> 2, tc = lane & 3;
+  const int down = own ? (lane + 1 == L ? 0 : lane + 1) : lane;   // phase-1 bottom source
   unsigned long long fma = 0;
 
   while (true) {
@@ -1262,99 +1316,92 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_jacobi(
     const int64_t k = order[idx];
     Real* Tk = T + k * R * R;
     Real top[kR], bot[kR];
+    const int ra = lane, rb = L + lane;   // rows held at the start
 #pragma unroll
     for (int t = 0; t < kR; ++t) {   // R_A was written by the previous launch: read it through L2
       top[t] = (own && ra < R && t < R) ? __ldcg(Tk + ra * R + t) : Real(0);
       bot[t] = (own && rb < R && t < R) ? __ldcg(Tk + rb * R + t) : Real(0);
     }
-    Real na = Real(0), nb = Real(0);
+    Real na = Real(0), nb = Real(0), fa = Real(1), fb = Real(1);
     int sweeps = 0;
     unsigned long long nrot = 0;
     for (int sweep = 0; sweep < kMaxSweeps && n2 > 1; ++sweep) {
       ++sweeps;
       bool any = false;
-      {   // exact squared norms at the start of every sweep
-        Real a4[4] = {Real(0), Real(0), Real(0), Real(0)}, b4[4] = {Real(0), Real(0), Real(0), Real(0)};
+      // fold the scales back; exact squared norms at the start of every sweep
 #pragma unroll
-        for (int t = 0; t < kR; ++t) {
-          a4[t & 3] += top[t] * top[t];
-          b4[t & 3] += bot[t] * bot[t];
-        }
-        na = (a4[0] + a4[1]) + (a4[2] + a4[3]);
-        nb = (b4[0] + b4[1]) + (b4[2] + b4[3]);
+      for (int t = 0; t < kR; ++t) {
+        top[t] *= fa;
+        bot[t] *= fb;
       }
-      for (int rd = 0; rd < n2 - 1; ++rd) {
+      fa = fb = Real(1);
+      na = sq_sum<Real, kR>(top);
+      nb = sq_sum<Real, kR>(bot);
+      // phase 1: top against bottom in each lane; the bottoms then move one lane down
+      for (int rd = 0; rd < L; ++rd) {
         Real g4[4] = {Real(0), Real(0), Real(0), Real(0)};
 #pragma unroll
         for (int t = 0; t < kR; ++t) g4[t & 3] += top[t] * bot[t];
-        const Real gg = (g4[0] + g4[1]) + (g4[2] + g4[3]);
+        const Real gg = (fa * fb) * ((g4[0] + g4[1]) + (g4[2] + g4[3]));
         const bool rot = own && gg != Real(0) && fabs(gg) > tol * sqrt(na * nb);
         if (rot) {
           Real c, s, tt;
           rotation_of(na, nb, gg, &c, &s, &tt);
+          // top' = c top - s bot, bot' = s top + c bot, in the scaled form
+          const Real ma = tt * fdiv_(fb, fa), mb = tt * fdiv_(fa, fb);
 #pragma unroll
           for (int t = 0; t < kR; ++t) {
             const Real x = top[t], y = bot[t];
-            top[t] = c * x - s * y;
-            bot[t] = s * x + c * y;
+            top[t] = x - ma * y;
+            bot[t] = y + mb * x;
           }
+          fa *= c;
+          fb *= c;
           // updated norms; recomputed where one of them drops by half or more, so that
           // rounding in the update stays small relative to the new norm
           const Real na1 = na - tt * gg, nb1 = nb + tt * gg;
-          if (na1 < Real(0.5) * na || nb1 < Real(0.5) * nb) {
-            Real a4[4] = {Real(0), Real(0), Real(0), Real(0)}, b4[4] = {Real(0), Real(0), Real(0), Real(0)};
-#pragma unroll
-            for (int t = 0; t < kR; ++t) {
-              a4[t & 3] += top[t] * top[t];
-              b4[t & 3] += bot[t] * bot[t];
-            }
-            na = (a4[0] + a4[1]) + (a4[2] + a4[3]);
-            nb = (b4[0] + b4[1]) + (b4[2] + b4[3]);
-          } else {
-            na = na1;
-            nb = nb1;
-          }
+          na = na1 < Real(0.5) * na ? fa * fa * sq_sum<Real, kR>(top) : na1;
+          nb = nb1 < Real(0.5) * nb ? fb * fb * sq_sum<Real, kR>(bot) : nb1;
         }
         const unsigned rmask = __ballot_sync(kFull, rot);
         any |= rmask != 0u;
         if (lane == 0) nrot += __popc(rmask);
-        // next round: lane l's top <- lane l-1's top (lane 1 takes lane 0's moving row), lane
-        // l's bottom <- lane l+1's bottom; lane 0's moving row <- lane 1's bottom, the last
-        // lane's bottom <- its own top
-        if (L < 2) continue;   // a single pair: nothing moves
-        const int up_src = lane > 0 ? lane - 1 : 0;
+        if (rd + 1 < L) {
 #pragma unroll
-        for (int t = 0; t < kR; ++t) {
-          const Real up = __shfl_sync(kFull, top[t], up_src);
-          const Real dn = __shfl_down_sync(kFull, bot[t], 1);
-          const Real old_top = top[t];
-          if (own) {
-            top[t] = lane == 0 ? dn : up;
-            if (lane > 0) bot[t] = lane == L - 1 ? old_top : dn;
-          }
+          for (int t = 0; t < kR; ++t) bot[t] = __shfl_sync(kFull, bot[t], down);
+          fb = __shfl_sync(kFull, fb, down);
+          nb = __shfl_sync(kFull, nb, down);
         }
-        {
-          const Real up = __shfl_sync(kFull, na, up_src);
-          const Real dn = __shfl_down_sync(kFull, nb, 1);
-          const Real old_na = na;
-          if (own) {
-            na = lane == 0 ? dn : up;
-            if (lane > 0) nb = lane == L - 1 ? old_na : dn;
-          }
+      }
+      // phase 2: tops against tops and bottoms against bottoms, lanes paired by the circle
+      // method on Le positions (position Le - 1 meets r in round r, position i != r meets
+      // (2r - i) mod (Le - 1))
+      for (int rd = 0; rd < Le - 1; ++rd) {
+        int j;
+        if (lane >= Le) j = lane;
+        else if (lane == Le - 1) j = rd;
+        else if (lane == rd) j = Le - 1;
+        else {
+          j = 2 * rd - lane;
+          if (j < 0) j += Le - 1;
+          else if (j >= Le - 1) j -= Le - 1;
         }
+        const bool pair = own && j < L && j != lane, lo = lane < j;
+        const bool r1 = pair_rotate<Real, kR>(top, fa, na, j, lo, pair, tol);
+        const bool r2 = pair_rotate<Real, kR>(bot, fb, nb, j, lo, pair, tol);
+        const unsigned m1 = __ballot_sync(kFull, r1), m2 = __ballot_sync(kFull, r2);
+        any |= (m1 | m2) != 0u;
+        if (lane == 0) nrot += (__popc(m1) + __popc(m2)) / 2;
       }
       if (!any) break;
     }
-    {   // exact squared norms for the rank cut
-      Real a4[4] = {Real(0), Real(0), Real(0), Real(0)}, b4[4] = {Real(0), Real(0), Real(0), Real(0)};
 #pragma unroll
-      for (int t = 0; t < kR; ++t) {
-        a4[t & 3] += top[t] * top[t];
-        b4[t & 3] += bot[t] * bot[t];
-      }
-      na = (a4[0] + a4[1]) + (a4[2] + a4[3]);
-      nb = (b4[0] + b4[1]) + (b4[2] + b4[3]);
+    for (int t = 0; t < kR; ++t) {   // exact squared norms for the rank cut
+      top[t] *= fa;
+      bot[t] *= fb;
     }
+    na = sq_sum<Real, kR>(top);
+    nb = sq_sum<Real, kR>(bot);
 
     // ---- rank cut; c_j = z_j / sigma_j, Omega = sum_j c_j c_j^T / sigma_j ----
     const Real amax = warp_max(own ? (na > nb ? na : nb) : Real(0));

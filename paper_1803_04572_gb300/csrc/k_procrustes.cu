@@ -656,13 +656,15 @@ struct WarpLay {
   static constexpr int ldu = kM + 1;             // U: odd stride, read by columns
   static constexpr int per_warp = 2 * kM * ld + kM * ldu + kR + VN;
   static constexpr size_t bytes = sizeof(Real) * ((size_t)kR * kR + (kWNT / 32) * (size_t)per_warp) + 16;
+  static_assert(kM * ld + kM * ldu >= kR * kR && kM * ld + kM * ldu >= kM * kR,
+                "the B2 and U buffers stage T_k and the Q rows");
 };
 
 template <typename Real, int kR>
 __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
     TensorView X, int R, const Real* __restrict__ H, const Real* __restrict__ V,
     const Real* __restrict__ W, double tau_rank, Real* __restrict__ Q, Real* __restrict__ T,
-    Real* __restrict__ Pi, int32_t* __restrict__ rank, double* __restrict__ fh_partial,
+    Real* __restrict__ Pi, int32_t* __restrict__ rank,
     const int64_t* __restrict__ order, const int* __restrict__ first, int* __restrict__ counter,
     unsigned long long* __restrict__ fma_count, Real* __restrict__ Uw,
     const int64_t* __restrict__ woff, int warm_in, int* __restrict__ status) {
@@ -683,9 +685,6 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
     Hs[e] = (t < R && r < R) ? H[t * R + r] : Real(0);
   }
   __syncthreads();
-  double* fh = fh_partial ? fh_partial + ((size_t)blockIdx.x * (kWNT / 32) + warp) * R * R : nullptr;
-  if (fh)
-    for (int e = lane; e < R * R; e += 32) fh[e] = 0.0;
   const Real tol = Tol<Real>::v();
   const int64_t k0 = min((int64_t)max(*first, 0), X.K);
   const int tr = lane >> 2, tc = lane & 3;
@@ -888,19 +887,16 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
       }
     }
     __syncwarp();
-    if (lane < m) {
-      Real* qrow = Q + (r0 + lane) * R;
-#pragma unroll
-      for (int t = 0; t < kR; ++t)
-        if (t < R) qrow[t] = z[t];
-    }
     if (lane < kM) {
 #pragma unroll
       for (int t = 0; t < kR; t += VN) Vc::st(B2 + lane * ld + t, p + t);
     }
     __syncwarp();
 
-    // ---- T_k = sum_j c_j^T b_j (lane tile kTR x kTC), F_H partial, optional Pi_k ----
+    // ---- T_k = sum_j c_j^T b_j (lane tile kTR x kTC), optional Pi_k. T_k and the rows
+    //      q_i go out through shared memory (the B2 and U buffers, free by then), so that
+    //      the global stores are contiguous. ----
+    Real* St = B2;   // staging: B2 and Us are adjacent and hold >= max(R * R, kM * R) values
     {
       Real acc[kTR][kTC];
 #pragma unroll
@@ -918,7 +914,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
 #pragma unroll
           for (int b = 0; b < kTC; ++b) acc[a][b] += cr[a] * bs[b];
       }
-      Real* Tk = T + k * R * R;
+      __syncwarp();   // every lane is done reading B2
 #pragma unroll
       for (int a = 0; a < kTR; ++a) {
         const int r = tr * kTR + a;
@@ -926,13 +922,22 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
 #pragma unroll
           for (int b = 0; b < kTC; ++b) {
             const int s = tc * kTC + b;
-            if (s < R) {
-              Tk[r * R + s] = acc[a][b];
-              if (fh) fh[r * R + s] += (double)acc[a][b] * (double)wk[s];
-            }
+            if (s < R) St[r * R + s] = acc[a][b];
           }
         }
       }
+      __syncwarp();
+      Real* Tk = T + k * R * R;
+      for (int e = lane; e < R * R; e += 32) Tk[e] = St[e];
+      __syncwarp();
+      if (lane < m) {
+#pragma unroll
+        for (int t = 0; t < kR; ++t)
+          if (t < R) St[lane * R + t] = z[t];
+      }
+      __syncwarp();
+      Real* Qk = Q + r0 * R;
+      for (int e = lane; e < m * R; e += 32) Qk[e] = St[e];
     }
     if (Pi) {
       Real acc[kTR][kTC];
@@ -996,6 +1001,7 @@ struct TallLay {
   static constexpr int per_warp_qr = (32 * ldb + kR * ldr + kR + VN - 1) / VN * VN;   // QR: row block, R_A, W row
   static constexpr size_t bytes = sizeof(Real) * ((size_t)kR * kR + (kWNT / 32) * (size_t)per_warp) + 16;
   static constexpr size_t qr_bytes = sizeof(Real) * ((size_t)kR * kR + (kWNT / 32) * (size_t)per_warp_qr) + 16;
+  static_assert(2 * 32 * ldb >= kR * kR, "the two row blocks stage T_k");
 };
 
 // p_i = x_i V into the registers of the lane owning row i (rows past the block: 0), then
@@ -1157,7 +1163,7 @@ template <typename Real, int kR>
 __global__ void __launch_bounds__(kWNT, 3) k_tall_pass2(
     TensorView X, int R, const Real* __restrict__ H, const Real* __restrict__ V, const Real* __restrict__ W,
     const int64_t* __restrict__ order, const int* __restrict__ count, int* __restrict__ counter,
-    Real* __restrict__ Q, Real* T, double* __restrict__ fh_partial, unsigned long long* __restrict__ fma_count) {
+    Real* __restrict__ Q, Real* T, unsigned long long* __restrict__ fma_count) {
   using Lt = TallLay<Real, kR>;
   using Vc = Vec16<Real>;
   constexpr int ldb = Lt::ldb, VN = Lt::VN;
@@ -1172,9 +1178,6 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_pass2(
   Real* Wb = Om + kR * kR;                                  // this subject's row of W
   load_hs<Real, kR>(H, R, Hs);
   __syncthreads();
-  double* fh = fh_partial ? fh_partial + ((size_t)blockIdx.x * (kWNT / 32) + warp) * R * R : nullptr;
-  if (fh)
-    for (int e = lane; e < R * R; e += 32) fh[e] = 0.0;
   const int64_t nt = min((int64_t)max(*count, 0), X.K);
   const int tr = lane >> 2, tc = lane & 3;
   unsigned long long fma = 0;
@@ -1219,15 +1222,12 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_pass2(
           for (int q = 0; q < VN; ++q) z[t + q] += ar * ov[q];
         }
       }
-      if (lane < nb) {
-        Real* qrow = Q + (g + lane) * R;
-#pragma unroll
-        for (int t = 0; t < kR; ++t)
-          if (t < R) qrow[t] = z[t];
-      }
 #pragma unroll
       for (int t = 0; t < kR; ++t) Ba[lane * ldb + t] = z[t];
       __syncwarp();
+      // the block's q rows are contiguous in Q: written row by row from shared memory
+      for (int i = 0; i < nb; ++i)
+        for (int t = lane; t < R; t += 32) Q[(g + i) * R + t] = Ba[i * ldb + t];
       // T_k += sum_i q_i^T p_i over the block (rows past nb are zero)
       for (int i = 0; i < nb; ++i) {
         Real qr[kTR], ps[kTC];
@@ -1242,6 +1242,8 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_pass2(
       }
       __syncwarp();
     }
+    // T_k through shared memory (the row blocks, free now), then contiguous stores
+    Real* St = Bp;
 #pragma unroll
     for (int a = 0; a < kTR; ++a) {
       const int r = tr * kTR + a;
@@ -1249,13 +1251,12 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_pass2(
 #pragma unroll
         for (int b = 0; b < kTC; ++b) {
           const int s = tc * kTC + b;
-          if (s < R) {
-            Tk[r * R + s] = acc[a][b];
-            if (fh) fh[r * R + s] += (double)acc[a][b] * (double)wk[s];
-          }
+          if (s < R) St[r * R + s] = acc[a][b];
         }
       }
     }
+    __syncwarp();
+    for (int e = lane; e < R * R; e += 32) Tk[e] = St[e];
     __syncwarp();
     if (fma_count) {
       const int nz = __reduce_add_sync(kFull, nnzk);
@@ -1471,9 +1472,73 @@ __global__ void k_reduce_partials(const double* __restrict__ part, int nparts, i
   }
 }
 
+// F_H = sum_k Y_k V S_k = sum_k T_k S_k (the MTTKRP of the H update, Sec. 3.1) from the stored
+// T_k, for the lane-per-row path: block b takes a contiguous range of subjects, thread e
+// the entries e, e + 512, ... of the R x R matrix (coalesced reads of T). In float every
+// product is split exactly (p + e = T_k(r,s) w_k(s), by a fused multiply-add) and summed
+// in a compensated pair; in double it is a plain sum. The per-block sums go to FP64
+// partials, which k_reduce_partials adds in a fixed order.
+constexpr int kFhThreads = 512, kFhE = 5;   // entries per thread: R*R <= 5 * 512 (R <= 48)
+constexpr int kFhU = 8;                      // subjects whose T_k entries are loaded ahead
+
+// (the _rn intrinsics keep the compiler from fusing the product into the sum)
+__device__ __forceinline__ void fh_add(float& s, float& c, float a, float b) {
+  const float p = __fmul_rn(a, b), pe = fmaf(a, b, -p);
+  const float t = __fadd_rn(s, p), bp = __fsub_rn(t, s);
+  const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  s = t;
+  c += e + pe;
+}
+__device__ __forceinline__ void fh_add(double& s, double&, double a, double b) { s = fma(a, b, s); }
+
+template <typename Real>
+__global__ void __launch_bounds__(kFhThreads) k_fh_stream(int64_t K, int R, const Real* __restrict__ T,
+                                                          const Real* __restrict__ W, double* __restrict__ part) {
+  const int n = R * R;
+  const int64_t per = (K + gridDim.x - 1) / gridDim.x;
+  const int64_t k0 = min(K, (int64_t)blockIdx.x * per), k1 = min(K, k0 + per);
+  Real s[kFhE], c[kFhE];
+  int col[kFhE];
+#pragma unroll
+  for (int j = 0; j < kFhE; ++j) {
+    const int e = threadIdx.x + j * kFhThreads;
+    col[j] = e < n ? e % R : 0;
+    s[j] = c[j] = Real(0);
+  }
+  // kFhU subjects' loads are issued before their sums, so that enough reads are in flight
+  int64_t k = k0;
+  for (; k + kFhU <= k1; k += kFhU) {
+    Real tv[kFhU][kFhE];
+#pragma unroll
+    for (int u = 0; u < kFhU; ++u)
+#pragma unroll
+      for (int j = 0; j < kFhE; ++j) {
+        const int e = threadIdx.x + j * kFhThreads;
+        tv[u][j] = e < n ? __ldcs(T + (k + u) * n + e) : Real(0);
+      }
+#pragma unroll
+    for (int u = 0; u < kFhU; ++u)   // the W rows are shared by the block: L1 hits
+#pragma unroll
+      for (int j = 0; j < kFhE; ++j)
+        if (threadIdx.x + j * kFhThreads < n) fh_add(s[j], c[j], tv[u][j], __ldg(W + (k + u) * R + col[j]));
+  }
+  for (; k < k1; ++k) {
+#pragma unroll
+    for (int j = 0; j < kFhE; ++j) {
+      const int e = threadIdx.x + j * kFhThreads;
+      if (e < n) fh_add(s[j], c[j], __ldcs(T + k * n + e), __ldg(W + k * R + col[j]));
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kFhE; ++j) {
+    const int e = threadIdx.x + j * kFhThreads;
+    if (e < n) part[(size_t)blockIdx.x * n + e] = (double)s[j] + (double)c[j];
+  }
+}
+
 template <typename Real>
 using WarpKernel = void (*)(TensorView, int, const Real*, const Real*, const Real*, double, Real*, Real*, Real*,
-                            int32_t*, double*, const int64_t*, const int*, int*, unsigned long long*, Real*,
+                            int32_t*, const int64_t*, const int*, int*, unsigned long long*, Real*,
                             const int64_t*, int, int*);
 template <typename Real>
 using TallQrKernel = void (*)(TensorView, int, const Real*, const Real*, const Real*, const int64_t*, const int*, int*,
@@ -1483,7 +1548,7 @@ using TallJacobiKernel = void (*)(int64_t, int, double, const int64_t*, const in
                                   unsigned long long*);
 template <typename Real>
 using TallPass2Kernel = void (*)(TensorView, int, const Real*, const Real*, const Real*, const int64_t*, const int*,
-                                 int*, Real*, Real*, double*, unsigned long long*);
+                                 int*, Real*, Real*, unsigned long long*);
 
 // The lane-per-row kernels for one padded width kR.
 template <typename Real>
@@ -1601,8 +1666,16 @@ copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const R
   int* counter = nullptr;
   if ((st = ws_get(h, SLOT_COUNTER, 64, (void**)&counter)) != COPA_OK) return st;
   unsigned long long* fma_count = reinterpret_cast<unsigned long long*>(counter + 2);
-  const int64_t wpb = kWNT / 32;
-  const int64_t nparts = blocks + (sblocks + pblocks) * wpb;
+  // F_H partials: one per block of the block kernel, or one per block of k_fh_stream
+  int64_t fblocks = 0;
+  if (rows) {   // one wave of k_fh_stream
+    int fh_per_sm = 0;
+    if ((st = cuda_check(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fh_per_sm, k_fh_stream<Real>, kFhThreads, 0),
+                         "occupancy")) != COPA_OK)
+      return st;
+    fblocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)h->num_sms * std::max(fh_per_sm, 1), X.K));
+  }
+  const int64_t nparts = rows ? fblocks : blocks;
   double* part = nullptr;
   if (F_H) {
     if ((st = ws_get(h, SLOT_PARTIAL, (size_t)nparts * R * R * sizeof(double), (void**)&part)) != COPA_OK)
@@ -1619,13 +1692,16 @@ copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const R
                                                                   fma_count);
     if ((st = cuda_check(h, cudaGetLastError(), "k_tall_jacobi launch")) != COPA_OK) return st;
     rk.pass2<<<(unsigned)pblocks, kWNT, rk.tall_smem, h->stream>>>(X, R, H, V, W, order, n_big, counter + 6, Q, T,
-                                                                     part, fma_count);
+                                                                     fma_count);
     if ((st = cuda_check(h, cudaGetLastError(), "k_tall_pass2 launch")) != COPA_OK) return st;
-    double* spart = part ? part + (size_t)pblocks * wpb * R * R : nullptr;
     rk.small<<<(unsigned)sblocks, kWNT, rk.small_smem, h->stream>>>(
-        X, R, H, V, W, tau, Q, T, Pi, rank, spart, order, n_big, counter + 4, fma_count, Uw, woff,
+        X, R, H, V, W, tau, Q, T, Pi, rank, order, n_big, counter + 4, fma_count, Uw, woff,
         warm_in ? 1 : 0, h->d_status);
     if ((st = cuda_check(h, cudaGetLastError(), "k_procrustes_warp launch")) != COPA_OK) return st;
+    if (F_H && X.K > 0) {
+      k_fh_stream<Real><<<(unsigned)fblocks, kFhThreads, 0, h->stream>>>(X.K, R, T, W, part);
+      if ((st = cuda_check(h, cudaGetLastError(), "k_fh_stream launch")) != COPA_OK) return st;
+    }
   } else {
     k_procrustes<Real><<<(unsigned)blocks, kNT, smem, h->stream>>>(X, R, H, V, W, tau, Q, T, Pi, rank, part, order,
                                                                   counter, fma_count, Uw, woff, warm_in ? 1 : 0,

@@ -159,9 +159,11 @@ __global__ void k_scan_inplace(int64_t* __restrict__ v, int64_t n) {
   for (int64_t i = a; i < b; ++i) { const int64_t x = v[i]; v[i] = s; s += x; }
 }
 
-__global__ void k_store_fit(const double* __restrict__ fit, double* __restrict__ hist, int* __restrict__ it) {
+__global__ void k_store_fit(const double* __restrict__ fit, double* __restrict__ hist, int* __restrict__ it,
+                            int* __restrict__ epoch) {
   hist[*it] = *fit;
   *it += 1;
+  *epoch += 1;
 }
 
 }  // namespace
@@ -508,6 +510,7 @@ template <typename Real>
 struct FitBufs {
   Real* Uw;
   const int64_t* woff;
+  int* epoch;   // outer iterations since the warm-start buffer was laid out (schedules re-orthonormalisation)
   Real* Q;
   Real* T;
   Real* Pi;
@@ -532,7 +535,8 @@ copa_status_t one_iteration(copa_ctx* h, const TensorView& X, const copa_options
                             bool first) {
   const int R = o->R;
   // (a)+(b) Procrustes, with the H-mode MTTKRP fused
-  TRY(launch_procrustes<Real>(h, X, R, H, V, W, o->tau, b.Q, b.T, b.Pi, b.rank, b.FH, b.Uw, b.woff, warm_in));
+  TRY(launch_procrustes<Real>(h, X, R, H, V, W, o->tau, b.Q, b.T, b.Pi, b.rank, b.FH, b.Uw, b.woff, warm_in,
+                              b.epoch));
   // H: G = W^T W .* V^T V
   TRY(launch_gram<Real>(h, W, X.K, R, b.gW));
   TRY(launch_gram<Real>(h, V, X.J, R, b.gV));
@@ -549,7 +553,7 @@ copa_status_t one_iteration(copa_ctx* h, const TensorView& X, const copa_options
   TRY(launch_admm_rows<Real>(h, b.FV, b.Ginv, b.rho + 2, o->n_inner, o->c_V, o->lam_V, V, DV, X.J, R));
   // FIT of (Q_k, H, W, V) after the iteration
   TRY(launch_fit_value<Real>(h, X.J, R, V, b.FV, b.UtU, b.xn2, o->x_norm2, b.fitv));
-  k_store_fit<<<1, 1, 0, h->stream>>>(b.fitv, b.hist, b.it);
+  k_store_fit<<<1, 1, 0, h->stream>>>(b.fitv, b.hist, b.it, b.epoch);
   return cuda_check(h, cudaGetLastError(), "k_store_fit");
 }
 
@@ -601,7 +605,11 @@ copa_status_t fit_impl(copa_ctx* h, const copa_tensor_t* Xc, const copa_options_
   {
     int64_t wtot = 0;
     TRY(get_warm_offsets(h, X, R, &b.woff, &wtot));
-    TRY(ws_get(h, SLOT_WARM, sizeof(Real) * (size_t)(wtot + 1), (void**)&b.Uw));
+    const size_t ub = (sizeof(Real) * (size_t)(wtot + 1) + 15) & ~size_t(15);
+    TRY(ws_get(h, SLOT_WARM, ub + 16, (void**)&b.Uw));
+    b.epoch = reinterpret_cast<int*>(reinterpret_cast<char*>(b.Uw) + ub);
+    if (!(h->warm_valid && h->warm_prec == h->precision))
+      TRY(cuda_check(h, cudaMemsetAsync(b.epoch, 0, sizeof(int), h->stream), "memset"));
   }
   if (o->n_outer > 0) {
     // the first iteration runs eagerly: it sizes every workspace buffer

@@ -174,7 +174,8 @@ template <typename Real>
 copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const Real* H,
                                 const Real* V, const Real* W, double tau, Real* Q, Real* T,
                                 Real* Pi, int32_t* rank, Real* F_H, Real* Uw = nullptr,
-                                const int64_t* woff = nullptr, bool warm_in = false);
+                                const int64_t* woff = nullptr, bool warm_in = false,
+                                const int* epoch = nullptr);
 template <typename Real>
 size_t procrustes_smem(int R);
 template <typename Real>

@@ -34,6 +34,10 @@ namespace {
 constexpr int kNT = 128;          // threads per CTA (one subject)
 constexpr int kNW = kNT / 32;     // warps per CTA = rows handled at once
 constexpr int kMaxSweeps = 30;
+// After a sweep whose rotations all had |tan| below this, the next sweep would most likely
+// only confirm convergence; the Jacobi kernels test every pair once from shared memory
+// instead (same criterion) and stop if no pair needs a rotation.
+constexpr double kTSmall = 1e-3;
 
 template <typename Real>
 struct Tol;
@@ -111,9 +115,11 @@ __device__ __forceinline__ Real sq_sum(const Real (&x)[kR]) {
 // the same order, the same norms); each lane then updates only its own row, which in the
 // scaled form is one multiply-add per component: x += m * x_partner with
 // m = -+ t * f_partner / f, and f *= c (c >= 1/sqrt(2), so f stays far from underflow
-// within a sweep). lo: this lane holds the pair's first row. Returns whether it rotated.
+// within a sweep). lo: this lane holds the pair's first row. Returns whether it rotated;
+// tmx takes the largest |tan| of the rotations.
 template <typename Real, int kR>
-__device__ __forceinline__ bool pair_rotate(Real (&x)[kR], Real& f, Real& n, int j, bool lo, bool pair, Real tol) {
+__device__ __forceinline__ bool pair_rotate(Real (&x)[kR], Real& f, Real& n, int j, bool lo, bool pair, Real tol,
+                                            Real& tmx) {
   constexpr unsigned kFull = 0xffffffffu;
   Real xp[kR];
   Real g4[4] = {Real(0), Real(0), Real(0), Real(0)};
@@ -130,6 +136,7 @@ __device__ __forceinline__ bool pair_rotate(Real (&x)[kR], Real& f, Real& n, int
     Real c, s, tt;
     rotation_of(aa, bb, gg, &c, &s, &tt);
     const Real m = (lo ? -tt : tt) * fdiv_(fp, f);
+    tmx = fmax(tmx, fabs(tt));
 #pragma unroll
     for (int t = 0; t < kR; ++t) x[t] += m * xp[t];
     f *= c;
@@ -247,6 +254,39 @@ __device__ void tsqr_block(Real* Z, int ld, int R, int nb, Real* vb, Real* misc)
   }
 }
 
+// A warm start reuses U from the previous outer iteration. Each rotation is orthogonal
+// only to rounding, so U drifts from orthogonality by about 1e-7 per iteration; every
+// kReorth-th iteration of a fit the loaded U is re-orthonormalised (modified Gram-Schmidt
+// on its rows, two passes) before it is applied, which bounds the drift.
+constexpr unsigned kReorth = 16;
+
+// Modified Gram-Schmidt (two passes) on the rows of the m x m matrix U[r * ld + c], by the
+// whole block; red[0] is shared scratch.
+template <typename Real>
+__device__ void mgs2_rows_block(Real* U, int m, int ld, Real* red) {
+  const int tid = threadIdx.x;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int i = 0; i < m; ++i) {
+      if (tid < 32) {
+        Real ss = Real(0);
+        for (int c = tid; c < m; c += 32) ss += U[i * ld + c] * U[i * ld + c];
+        ss = warp_sum(ss);
+        if (tid == 0) red[0] = Real(1) / sqrt(ss);
+      }
+      __syncthreads();
+      const Real inv = red[0];
+      for (int c = tid; c < m; c += blockDim.x) U[i * ld + c] *= inv;
+      __syncthreads();
+      for (int r = i + 1 + tid; r < m; r += blockDim.x) {
+        Real d = Real(0);
+        for (int c = 0; c < m; ++c) d += U[r * ld + c] * U[i * ld + c];
+        for (int c = 0; c < m; ++c) U[r * ld + c] -= d * U[i * ld + c];
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // Block kernel, one 128-thread CTA per subject. Rows of X_k are handled four at a time,
 // one per warp (lanes over the R components); the Jacobi pairs of a round are spread over
 // the block with LP = 128 / pairs threads per pair (a power of two), each thread holding
@@ -259,7 +299,8 @@ __global__ void __launch_bounds__(kNT, 5) k_procrustes(
     Real* __restrict__ Pi, int32_t* __restrict__ rank, double* __restrict__ fh_partial,
     const int64_t* __restrict__ order, int* __restrict__ counter,
     unsigned long long* __restrict__ fma_count, Real* __restrict__ Uw,
-    const int64_t* __restrict__ woff, int warm_in, const int* __restrict__ limit, const int* __restrict__ first) {
+    const int64_t* __restrict__ woff, int warm_in, const int* __restrict__ epoch, const int* __restrict__ limit,
+    const int* __restrict__ first) {
   extern __shared__ unsigned char smem_raw[];
   Real* sm = reinterpret_cast<Real*>(smem_raw);
   const Lay L = lay_of<Real>(R);
@@ -352,6 +393,7 @@ __global__ void __launch_bounds__(kNT, 5) k_procrustes(
         Ub[r * ld + t] = (Uk && warm_in) ? Uk[e] : ((r == t) ? Real(1) : Real(0));
       }
       __syncthreads();
+      if (Uk && warm_in && epoch && ((unsigned)__ldg(epoch) % kReorth) == 0u) mgs2_rows_block<Real>(Ub, m, ld, misc);
       if (Uk && warm_in) {
         for (int e = tid; e < m * R; e += kNT) {
           const int i = e / R, t = e - i * R;
@@ -667,7 +709,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
     Real* __restrict__ Pi, int32_t* __restrict__ rank,
     const int64_t* __restrict__ order, const int* __restrict__ first, int* __restrict__ counter,
     unsigned long long* __restrict__ fma_count, Real* __restrict__ Uw,
-    const int64_t* __restrict__ woff, int warm_in, int* __restrict__ status) {
+    const int64_t* __restrict__ woff, int warm_in, const int* __restrict__ epoch, int* __restrict__ status) {
   using Lw = WarpLay<Real, kR>;
   using Vc = Vec16<Real>;
   constexpr int kM = Lw::kM, ld = Lw::ld, ldu = Lw::ldu, VN = Lw::VN;
@@ -747,6 +789,30 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
         for (int j = 0; j < kM; ++j)
           if (j < m) u[j] = Uk[lane * m + j];
       }
+      if (epoch && ((unsigned)__ldg(epoch) % kReorth) == 0u) {
+        // modified Gram-Schmidt on the rows of U_prev (lane = row), two passes
+#pragma unroll 1
+        for (int pass = 0; pass < 2; ++pass) {
+#pragma unroll 1
+          for (int i = 0; i < m; ++i) {
+            Real ss = Real(0);
+#pragma unroll
+            for (int jj = 0; jj < kM; ++jj) ss += u[jj] * u[jj];
+            const Real inv = Real(1) / sqrt(__shfl_sync(kFull, ss, i));
+            Real d = Real(0);
+#pragma unroll
+            for (int jj = 0; jj < kM; ++jj) {
+              const Real ui = __shfl_sync(kFull, u[jj], i) * inv;
+              if (lane == i) u[jj] = ui;
+              d += u[jj] * ui;
+            }
+            // (lane i's d is its own squared norm, 1; it does not update)
+            const Real dd = lane > i && lane < m ? d : Real(0);
+#pragma unroll
+            for (int jj = 0; jj < kM; ++jj) u[jj] -= dd * __shfl_sync(kFull, u[jj], i);
+          }
+        }
+      }
       __syncwarp();
 #pragma unroll
       for (int t = 0; t < kR; ++t) z[t] = Real(0);
@@ -786,6 +852,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
     for (int sweep = 0; sweep < kMaxSweeps && n2 > 1; ++sweep) {
       ++sweeps;
       bool any = false;
+      Real tmx = Real(0);   // largest |tan| of this lane's rotations in the sweep
       fold(f);
       f = Real(1);
       al = sq_sum<Real, kR>(z);
@@ -822,6 +889,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
           Real c, s, tt;
           rotation_of(aa, bb, gg, &c, &s, &tt);
           mu = (lo ? -tt : tt) * fdiv_(fp, f);
+          tmx = fmax(tmx, fabs(tt));
 #pragma unroll
           for (int t = 0; t < kR; ++t) z[t] += mu * zp[t];
           f *= c;
@@ -841,6 +909,40 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
         }
       }
       if (!any) break;
+      if (warp_max(tmx) < Real(kTSmall) && sweep + 1 < kMaxSweeps) {
+        // confirm convergence without a sweep: rows (scales folded) and squared norms to
+        // shared memory (B1 and Us are free during the sweeps), every pair tested once
+        fold(f);
+        f = Real(1);
+        al = sq_sum<Real, kR>(z);
+        if (lane < kM) {
+#pragma unroll
+          for (int t = 0; t < kR; t += VN) Vc::st(B1 + lane * ld + t, z + t);
+          Us[lane] = al;
+        }
+        __syncwarp();
+        bool bad = false;
+        if (lane < m) {
+#pragma unroll 1
+          for (int jj = 0; jj < m; ++jj) {
+            Real g4[4] = {Real(0), Real(0), Real(0), Real(0)};
+#pragma unroll
+            for (int t = 0; t < kR; t += VN) {
+              Real rv[VN];
+              Vc::ld(B1 + jj * ld + t, rv);
+#pragma unroll
+              for (int q = 0; q < VN; ++q) g4[(t + q) & 3] += z[t + q] * rv[q];
+            }
+            const Real gg = (g4[0] + g4[1]) + (g4[2] + g4[3]);
+            bad |= jj != lane && gg != Real(0) && fabs(gg) > tol * sqrt(al * Us[jj]);
+          }
+        }
+        __syncwarp();
+        if (!__any_sync(kFull, bad)) {
+          ++sweeps;   // the test stood in for the confirming sweep
+          break;
+        }
+      }
     }
     fold(f);
     al = sq_sum<Real, kR>(z);
@@ -1329,6 +1431,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_jacobi(
     for (int sweep = 0; sweep < kMaxSweeps && n2 > 1; ++sweep) {
       ++sweeps;
       bool any = false;
+      Real tmx = Real(0);   // largest |tan| of this lane's rotations in the sweep
       // fold the scales back; exact squared norms at the start of every sweep
 #pragma unroll
       for (int t = 0; t < kR; ++t) {
@@ -1350,6 +1453,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_jacobi(
           rotation_of(na, nb, gg, &c, &s, &tt);
           // top' = c top - s bot, bot' = s top + c bot, in the scaled form
           const Real ma = tt * fdiv_(fb, fa), mb = tt * fdiv_(fa, fb);
+          tmx = fmax(tmx, fabs(tt));
 #pragma unroll
           for (int t = 0; t < kR; ++t) {
             const Real x = top[t], y = bot[t];
@@ -1388,13 +1492,57 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_jacobi(
           else if (j >= Le - 1) j -= Le - 1;
         }
         const bool pair = own && j < L && j != lane, lo = lane < j;
-        const bool r1 = pair_rotate<Real, kR>(top, fa, na, j, lo, pair, tol);
-        const bool r2 = pair_rotate<Real, kR>(bot, fb, nb, j, lo, pair, tol);
+        const bool r1 = pair_rotate<Real, kR>(top, fa, na, j, lo, pair, tol, tmx);
+        const bool r2 = pair_rotate<Real, kR>(bot, fb, nb, j, lo, pair, tol, tmx);
         const unsigned m1 = __ballot_sync(kFull, r1), m2 = __ballot_sync(kFull, r2);
         any |= (m1 | m2) != 0u;
         if (lane == 0) nrot += (__popc(m1) + __popc(m2)) / 2;
       }
       if (!any) break;
+      if (warp_max(tmx) < Real(kTSmall) && sweep + 1 < kMaxSweeps) {
+        // confirm convergence without a sweep: rows (scales folded) and squared norms to
+        // shared memory (Cs and Is are free during the sweeps), every pair tested once
+#pragma unroll
+        for (int t = 0; t < kR; ++t) {
+          top[t] *= fa;
+          bot[t] *= fb;
+        }
+        fa = fb = Real(1);
+        na = sq_sum<Real, kR>(top);
+        nb = sq_sum<Real, kR>(bot);
+        if (own) {
+#pragma unroll
+          for (int t = 0; t < kR; ++t) {
+            Cs[lane * ld + t] = top[t];
+            Cs[(L + lane) * ld + t] = bot[t];
+          }
+          Is[lane] = na;
+          Is[L + lane] = nb;
+        }
+        __syncwarp();
+        bool bad = false;
+        if (own) {
+#pragma unroll 1
+          for (int jj = 0; jj < n2; ++jj) {
+            Real ga[4] = {Real(0), Real(0), Real(0), Real(0)}, gb[4] = {Real(0), Real(0), Real(0), Real(0)};
+#pragma unroll
+            for (int t = 0; t < kR; ++t) {
+              const Real r = Cs[jj * ld + t];
+              ga[t & 3] += top[t] * r;
+              gb[t & 3] += bot[t] * r;
+            }
+            const Real g1 = (ga[0] + ga[1]) + (ga[2] + ga[3]), g2 = (gb[0] + gb[1]) + (gb[2] + gb[3]);
+            const Real nj = Is[jj];
+            bad |= jj != lane && g1 != Real(0) && fabs(g1) > tol * sqrt(na * nj);
+            bad |= jj != L + lane && g2 != Real(0) && fabs(g2) > tol * sqrt(nb * nj);
+          }
+        }
+        __syncwarp();
+        if (!__any_sync(kFull, bad)) {
+          ++sweeps;   // the test stood in for the confirming sweep
+          break;
+        }
+      }
     }
 #pragma unroll
     for (int t = 0; t < kR; ++t) {   // exact squared norms for the rank cut
@@ -1539,7 +1687,7 @@ __global__ void __launch_bounds__(kFhThreads) k_fh_stream(int64_t K, int R, cons
 template <typename Real>
 using WarpKernel = void (*)(TensorView, int, const Real*, const Real*, const Real*, double, Real*, Real*, Real*,
                             int32_t*, const int64_t*, const int*, int*, unsigned long long*, Real*,
-                            const int64_t*, int, int*);
+                            const int64_t*, int, const int*, int*);
 template <typename Real>
 using TallQrKernel = void (*)(TensorView, int, const Real*, const Real*, const Real*, const int64_t*, const int*, int*,
                               Real*, unsigned long long*);
@@ -1631,7 +1779,7 @@ template <typename Real>
 copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const Real* H,
                                 const Real* V, const Real* W, double tau, Real* Q, Real* T,
                                 Real* Pi, int32_t* rank, Real* F_H, Real* Uw, const int64_t* woff,
-                                bool warm_in) {
+                                bool warm_in, const int* epoch) {
   const size_t smem = procrustes_smem<Real>(R);
   if (R < 1 || R > kNT || smem > 227 * 1024)
     return fail(h, COPA_ERR_UNSUPPORTED, "Procrustes: R too large for shared memory at this precision");
@@ -1696,7 +1844,7 @@ copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const R
     if ((st = cuda_check(h, cudaGetLastError(), "k_tall_pass2 launch")) != COPA_OK) return st;
     rk.small<<<(unsigned)sblocks, kWNT, rk.small_smem, h->stream>>>(
         X, R, H, V, W, tau, Q, T, Pi, rank, order, n_big, counter + 4, fma_count, Uw, woff,
-        warm_in ? 1 : 0, h->d_status);
+        warm_in ? 1 : 0, epoch, h->d_status);
     if ((st = cuda_check(h, cudaGetLastError(), "k_procrustes_warp launch")) != COPA_OK) return st;
     if (F_H && X.K > 0) {
       k_fh_stream<Real><<<(unsigned)fblocks, kFhThreads, 0, h->stream>>>(X.K, R, T, W, part);
@@ -1704,7 +1852,7 @@ copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const R
     }
   } else {
     k_procrustes<Real><<<(unsigned)blocks, kNT, smem, h->stream>>>(X, R, H, V, W, tau, Q, T, Pi, rank, part, order,
-                                                                  counter, fma_count, Uw, woff, warm_in ? 1 : 0,
+                                                                  counter, fma_count, Uw, woff, warm_in ? 1 : 0, epoch,
                                                                   nullptr, nullptr);
     if ((st = cuda_check(h, cudaGetLastError(), "k_procrustes launch")) != COPA_OK) return st;
   }
@@ -1720,10 +1868,10 @@ template size_t procrustes_smem<double>(int);
 template copa_status_t launch_procrustes<float>(copa_ctx*, const TensorView&, int, const float*,
                                                 const float*, const float*, double, float*,
                                                 float*, float*, int32_t*, float*, float*,
-                                                const int64_t*, bool);
+                                                const int64_t*, bool, const int*);
 template copa_status_t launch_procrustes<double>(copa_ctx*, const TensorView&, int, const double*,
                                                  const double*, const double*, double, double*,
                                                  double*, double*, int32_t*, double*, double*,
-                                                 const int64_t*, bool);
+                                                 const int64_t*, bool, const int*);
 
 }  // namespace copa

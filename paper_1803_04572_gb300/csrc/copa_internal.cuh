@@ -185,6 +185,12 @@ template <typename Real>
 copa_status_t launch_mttkrp_v(copa_ctx* h, const TensorView& X, int R, const Real* Q,
                               const Real* H, const Real* W, Real* F, double* UtU,
                               bool reuse_csc = false);
+// V-mode tile products on the tensor cores (FP32 path, k_vmode_tc.cu): U = (Q H) .* W(k(i),:)
+// and the UtU partials (two per CTA, *nparts). Supported for R % 4 == 0, R <= 48 and
+// 16-byte aligned Q, W, U.
+bool uvec_tc_supported(int R, const void* Q, const void* W, const void* U);
+copa_status_t launch_uvec_tc(copa_ctx* h, int64_t S, int R, const float* Q, const float* H, const float* W,
+                             const int32_t* rsubj, float* U, double* utu_part, int64_t* nparts, bool size_only);
 template <typename Real>
 copa_status_t launch_mttkrp_w(copa_ctx* h, int64_t K, int R, const Real* T, const Real* H,
                               Real* F);

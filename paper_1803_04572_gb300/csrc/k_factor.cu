@@ -10,6 +10,8 @@
 // column-sorted copy of X; U^T U = sum_i u_i^T u_i comes with the first step.
 #include <mutex>
 
+#include <type_traits>
+
 #include "copa_internal.cuh"
 
 namespace copa {
@@ -1007,7 +1009,16 @@ copa_status_t launch_mttkrp_v(copa_ctx* h, const TensorView& X, int R, const Rea
     return st;
   double* part = nullptr;
   int64_t nparts = 0;
-  if (R <= 48) {
+  bool tensor = false;   // FP32: the tensor-core tile kernel where its layout applies
+  if constexpr (std::is_same<Real, float>::value) tensor = uvec_tc_supported(R, Q, W, U);
+  if (tensor) {
+    if constexpr (std::is_same<Real, float>::value) {
+      if ((st = launch_uvec_tc(h, X.S, R, Q, H, W, rsubj, U, nullptr, &nparts, true)) != COPA_OK) return st;
+      if (UtU && (st = ws_get(h, SLOT_PARTIAL, (size_t)nparts * R * R * sizeof(double), (void**)&part)) != COPA_OK)
+        return st;
+      if ((st = launch_uvec_tc(h, X.S, R, Q, H, W, rsubj, U, part, &nparts, false)) != COPA_OK) return st;
+    }
+  } else if (R <= 48) {
     if ((st = launch_uvec_tiled<Real>(h, X.S, R, Q, H, W, rsubj, U, nullptr, &nparts, true)) != COPA_OK) return st;
     if (UtU && (st = ws_get(h, SLOT_PARTIAL, (size_t)nparts * R * R * sizeof(double), (void**)&part)) != COPA_OK)
       return st;

@@ -324,10 +324,10 @@ copa_status_t copa_destroy(copa_handle_t h) {
   cudaSetDevice(h->device);
   cudaStreamSynchronize(h->stream);
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
-  for (int i = 0; i < 16; ++i) {
+  for (int i = 0; i < 20; ++i)
     if (h->slot_ptr[i]) cudaFree(h->slot_ptr[i]);
+  for (int i = 0; i < 16; ++i)
     if (h->host_slot_ptr[i]) cudaFree(h->host_slot_ptr[i]);
-  }
   cudaFree(h->d_status);
   delete h;
   return COPA_OK;

@@ -109,8 +109,8 @@ struct copa_ctx {
   int* d_status = nullptr;       // int32[4] device status word
   int num_sms = 0;
   // generic workspace slots
-  void* slot_ptr[16] = {nullptr};
-  size_t slot_bytes[16] = {0};
+  void* slot_ptr[20] = {nullptr};
+  size_t slot_bytes[20] = {0};
   // cached per-tensor schedule (subjects ordered by decreasing I_k)
   const int64_t* sched_key = nullptr;
   int64_t sched_K = 0;
@@ -134,6 +134,9 @@ struct copa_ctx {
   const int32_t* csc_key = nullptr;
   int64_t csc_nnz = -1, csc_S = -1;
   int csc_J = 0, csc_prec = -1;
+  // cached nonzero -> row and row -> subject maps (row-order F_V path)
+  const int32_t* rmap_key = nullptr;
+  int64_t rmap_nnz = -1, rmap_S = -1, rmap_K = -1;
 };
 
 namespace copa {
@@ -154,6 +157,8 @@ enum Slot {
   SLOT_WARM_OFF = 12,  // int64[K+1] offsets of the min(I_k,R)^2 blocks
   SLOT_CSC = 13,       // column-sorted copy of X (pointers, row indices, values)
   SLOT_UVEC = 14,      // u_i = q_i H S_k for every visit row (S x R)
+  SLOT_ROWMAP = 15,    // int32 nonzero -> row map and int32 row -> subject map
+  SLOT_FV_PART = 16,   // per-CTA partial sums of F_V (row-order path)
 };
 copa_status_t get_warm_offsets(copa_ctx* h, const TensorView& X, int R, const int64_t** woff,
                                int64_t* total);

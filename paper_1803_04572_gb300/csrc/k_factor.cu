@@ -993,6 +993,108 @@ static copa_status_t launch_uvec_tiled(copa_ctx* h, int64_t S, int R, const Real
   return cuda_check(h, cudaGetLastError(), "k_uvec_tiled");
 }
 
+// ---- F_V = X^T U in row order (FP32 path) ----
+// The nonzeros of X are taken in their stored (row) order, split evenly over the CTAs (one
+// per SM). A CTA keeps its own copy of 32 columns of F_V (J x 32 floats in shared memory)
+// per pass and adds x_ij u_i(c) into it by shared-memory atomics: a warp takes 32 nonzeros
+// at a time (column, value and row loaded by the lanes, then broadcast by shuffles), each
+// lane adding one column, or several nonzeros per step when a pass is narrower than 32
+// columns. U is read in row order (consecutive nonzeros share rows), so it streams from
+// memory about once per pass, where the column-order form gathered a row of U per
+// nonzero. The per-CTA copies go to FP32 partials that k_reduce_fv adds in FP64.
+constexpr int kSRT = 1024;   // threads per CTA
+
+__global__ void k_nz_row(const int64_t* __restrict__ row_ptr, int64_t S, int32_t* __restrict__ nzrow) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S; i += gridDim.x * (int64_t)blockDim.x)
+    for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) nzrow[p] = (int32_t)i;
+}
+
+__global__ void __launch_bounds__(kSRT, 1) k_spmm_rows(TensorView X, int R, const float* __restrict__ U,
+                                                       const int32_t* __restrict__ nzrow, float* __restrict__ part) {
+  extern __shared__ float Fs[];   // J x 32: this CTA's sums of columns c0 .. c0 + 31 of F_V
+  constexpr unsigned kFull = 0xffffffffu;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int nw = kSRT / 32;
+  const int64_t per = (X.nnz + gridDim.x - 1) / gridDim.x;
+  const int64_t p0 = min(X.nnz, (int64_t)blockIdx.x * per), p1 = min(X.nnz, p0 + per);
+  const int npass = (R + 31) / 32;
+  for (int pass = 0; pass < npass; ++pass) {
+    const int c0 = 32 * pass, w = min(32, R - c0);
+    // lanes per nonzero: the pass width rounded up to a power of two
+    const int lw = w > 16 ? 32 : (w > 8 ? 16 : (w > 4 ? 8 : (w > 2 ? 4 : (w > 1 ? 2 : 1))));
+    const int per_step = 32 / lw, sub = lane / lw, c = lane - sub * lw;
+    for (int e = threadIdx.x; e < X.J * 32; e += kSRT) Fs[e] = 0.f;
+    __syncthreads();
+    for (int64_t base = p0 + (int64_t)warp * 32; base < p1; base += (int64_t)nw * 32) {
+      const int64_t p = base + lane;
+      const bool v = p < p1;
+      const int jj = v ? __ldg(X.col + p) : 0;
+      const float xx = v ? load_valf(X, p) : 0.f;
+      const int ii = v ? __ldg(nzrow + p) : 0;
+      const int cnt = (int)min((int64_t)32, p1 - base);
+#pragma unroll 4
+      for (int q = 0; q < 32; q += per_step) {
+        const int src = q + sub;   // < 32
+        const int j = __shfl_sync(kFull, jj, src);
+        const float x = __shfl_sync(kFull, xx, src);
+        const int i = __shfl_sync(kFull, ii, src);
+        if (src < cnt && c < w) atomicAdd(&Fs[j * 32 + c], x * __ldg(U + (int64_t)i * R + c0 + c));
+      }
+    }
+    __syncthreads();
+    float* pp = part + ((size_t)blockIdx.x * npass + pass) * (size_t)X.J * 32;
+    for (int e = threadIdx.x; e < X.J * 32; e += kSRT) pp[e] = Fs[e];
+    __syncthreads();
+  }
+}
+
+template <typename Real>
+__global__ void k_reduce_fv(const float* __restrict__ part, int nblocks, int npass, int J, int R,
+                            Real* __restrict__ F) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < J * R; e += gridDim.x * blockDim.x) {
+    const int j = e / R, c = e - j * R, pass = c >> 5, cc = c & 31;
+    double acc = 0.0;
+    for (int b = 0; b < nblocks; ++b) acc += (double)part[((size_t)b * npass + pass) * (size_t)J * 32 + j * 32 + cc];
+    F[e] = (Real)acc;
+  }
+}
+
+// Shared memory the row-order F_V kernel needs (J x 32 floats); the path is taken when it fits.
+static size_t spmm_rows_smem(int J) { return sizeof(float) * 32 * (size_t)J; }
+static bool spmm_rows_fits(const copa_ctx* h, const TensorView& X) {
+  (void)h;
+  return spmm_rows_smem(X.J) <= (size_t)200 * 1024 && X.nnz < (int64_t)INT32_MAX && X.S < (int64_t)INT32_MAX;
+}
+
+// Nonzero -> row and row -> subject maps in SLOT_ROWMAP, rebuilt unless `reuse` and the
+// tensor is the one they were built for.
+static copa_status_t get_rowmaps(copa_ctx* h, const TensorView& X, bool reuse, const int32_t** nzrow,
+                                 const int32_t** rsubj) {
+  copa_status_t st;
+  const size_t off = ((sizeof(int32_t) * (size_t)X.nnz + 15) & ~size_t(15));
+  if (!(reuse && h->rmap_key == X.col && h->rmap_nnz == X.nnz && h->rmap_S == X.S && h->rmap_K == X.K &&
+        h->slot_ptr[SLOT_ROWMAP])) {
+    char* p = nullptr;
+    if ((st = ws_get(h, SLOT_ROWMAP, off + sizeof(int32_t) * (size_t)X.S + 16, (void**)&p)) != COPA_OK) return st;
+    int32_t* nz = reinterpret_cast<int32_t*>(p);
+    int32_t* rs = reinterpret_cast<int32_t*>(p + off);
+    const int rblocks = (int)std::max<int64_t>(1, std::min<int64_t>((X.S + 255) / 256, (int64_t)h->num_sms * 16));
+    k_nz_row<<<rblocks, 256, 0, h->stream>>>(X.row_ptr, X.S, nz);
+    const int kblocks = (int)std::max<int64_t>(1, std::min<int64_t>((X.K + 255) / 256, (int64_t)h->num_sms * 16));
+    k_row_subject<<<kblocks, 256, 0, h->stream>>>(X.subj_ptr, X.K, rs);
+    if ((st = cuda_check(h, cudaGetLastError(), "row maps")) != COPA_OK) return st;
+    h->setup_launches += 2;
+    h->rmap_key = X.col;
+    h->rmap_nnz = X.nnz;
+    h->rmap_S = X.S;
+    h->rmap_K = X.K;
+  }
+  const char* p = reinterpret_cast<const char*>(h->slot_ptr[SLOT_ROWMAP]);
+  *nzrow = reinterpret_cast<const int32_t*>(p);
+  *rsubj = reinterpret_cast<const int32_t*>(p + off);
+  return COPA_OK;
+}
+
 template <typename Real>
 copa_status_t launch_mttkrp_v(copa_ctx* h, const TensorView& X, int R, const Real* Q, const Real* H,
                               const Real* W, Real* F, double* UtU, bool reuse_csc) {
@@ -1002,10 +1104,20 @@ copa_status_t launch_mttkrp_v(copa_ctx* h, const TensorView& X, int R, const Rea
   const int32_t* crow = nullptr;
   const Real* cval = nullptr;
   const int32_t* rsubj = nullptr;
-  if ((st = get_csc<Real>(h, X, reuse_csc, &cptr, &crow, &cval, &rsubj)) != COPA_OK) return st;
+  const int32_t* nzrow = nullptr;
+  // F_V in row order (FP32, when J x 32 floats fit in shared memory), else over the
+  // column-sorted copy of X
+  bool rows_fv = false;
+  if constexpr (std::is_same<Real, float>::value) rows_fv = spmm_rows_fits(h, X);
+  if (rows_fv) {
+    if ((st = get_rowmaps(h, X, reuse_csc, &nzrow, &rsubj)) != COPA_OK) return st;
+  } else if ((st = get_csc<Real>(h, X, reuse_csc, &cptr, &crow, &cval, &rsubj)) != COPA_OK) {
+    return st;
+  }
   Real* U = nullptr;
   if ((st = ws_get(h, SLOT_UVEC, sizeof(Real) * ((size_t)X.S * R + 16), (void**)&U)) != COPA_OK) return st;
-  if ((st = cuda_check(h, cudaMemsetAsync(F, 0, sizeof(Real) * (size_t)X.J * R, h->stream), "memset F")) != COPA_OK)
+  if (!rows_fv &&
+      (st = cuda_check(h, cudaMemsetAsync(F, 0, sizeof(Real) * (size_t)X.J * R, h->stream), "memset F")) != COPA_OK)
     return st;
   double* part = nullptr;
   int64_t nparts = 0;
@@ -1053,10 +1165,30 @@ copa_status_t launch_mttkrp_v(copa_ctx* h, const TensorView& X, int R, const Rea
     kern<<<(unsigned)blocks, kUNT, smem, h->stream>>>(X, R, Q, H, W, U, part, order, counter + 1);
     if ((st = cuda_check(h, cudaGetLastError(), "k_uvec")) != COPA_OK) return st;
   }
-  const int64_t nchunks = (X.nnz + kChunk - 1) / kChunk;
-  const int sblocks = (int)std::max<int64_t>(1, std::min<int64_t>((nchunks + 7) / 8, (int64_t)h->num_sms * 16));
-  k_spmm_csc<Real><<<sblocks, 256, 0, h->stream>>>(X.nnz, X.J, R, cptr, crow, cval, U, F);
-  if ((st = cuda_check(h, cudaGetLastError(), "k_spmm_csc")) != COPA_OK) return st;
+  if (rows_fv) {
+    if constexpr (std::is_same<Real, float>::value) {
+      const int npass = (R + 31) / 32;
+      const int fblocks = std::max(1, h->num_sms);
+      float* fpart = nullptr;
+      if ((st = ws_get(h, SLOT_FV_PART, sizeof(float) * (size_t)fblocks * npass * 32 * (size_t)X.J + 16,
+                       (void**)&fpart)) != COPA_OK)
+        return st;
+      const size_t fsm = spmm_rows_smem(X.J);
+      if ((st = cuda_check(h, cudaFuncSetAttribute(k_spmm_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm),
+                           "cudaFuncSetAttribute")) != COPA_OK)
+        return st;
+      k_spmm_rows<<<fblocks, kSRT, fsm, h->stream>>>(X, R, U, nzrow, fpart);
+      if ((st = cuda_check(h, cudaGetLastError(), "k_spmm_rows")) != COPA_OK) return st;
+      const int rb = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)X.J * R + 255) / 256, 4096));
+      k_reduce_fv<Real><<<rb, 256, 0, h->stream>>>(fpart, fblocks, npass, X.J, R, F);
+      if ((st = cuda_check(h, cudaGetLastError(), "k_reduce_fv")) != COPA_OK) return st;
+    }
+  } else {
+    const int64_t nchunks = (X.nnz + kChunk - 1) / kChunk;
+    const int sblocks = (int)std::max<int64_t>(1, std::min<int64_t>((nchunks + 7) / 8, (int64_t)h->num_sms * 16));
+    k_spmm_csc<Real><<<sblocks, 256, 0, h->stream>>>(X.nnz, X.J, R, cptr, crow, cval, U, F);
+    if ((st = cuda_check(h, cudaGetLastError(), "k_spmm_csc")) != COPA_OK) return st;
+  }
   if (UtU) {
     k_reduce_rows<double><<<(R * R + 255) / 256, 256, 0, h->stream>>>(part, (int)nparts, R * R, UtU);
     if ((st = cuda_check(h, cudaGetLastError(), "UtU reduce")) != COPA_OK) return st;

@@ -490,12 +490,14 @@ copa_status_t copa_fit_value(copa_handle_t h, const copa_tensor_t* X, int32_t R,
   TRY(check_R(h, R));
   if (!V || !F_V || !UtU || !fit) return fail(h, COPA_ERR_INVALID_ARG, "copa_fit_value: NULL argument");
   double* xn2 = nullptr;
-  TRY(ws_get(h, SLOT_PI, sizeof(double) * 4, (void**)&xn2));
+  TRY(ws_get(h, SLOT_PI, sizeof(double) * (4 + (size_t)R * R), (void**)&xn2));
   const TensorView v = view_of(X);
   TRY(launch_xnorm2(h, v, xn2));
   if (h->precision == COPA_PREC_MIXED)
-    return launch_fit_value<float>(h, X->J, R, (const float*)V, (const float*)F_V, UtU, xn2, x_norm2, fit);
-  return launch_fit_value<double>(h, X->J, R, (const double*)V, (const double*)F_V, UtU, xn2, x_norm2, fit);
+    return launch_fit_value<float>(h, X->J, R, (const float*)V, (const float*)F_V, UtU, xn2, x_norm2, fit,
+                                   xn2 + 4);
+  return launch_fit_value<double>(h, X->J, R, (const double*)V, (const double*)F_V, UtU, xn2, x_norm2, fit,
+                                  xn2 + 4);
 }
 
 }  // extern "C"
@@ -537,9 +539,10 @@ copa_status_t one_iteration(copa_ctx* h, const TensorView& X, const copa_options
   // (a)+(b) Procrustes, with the H-mode MTTKRP fused
   TRY(launch_procrustes<Real>(h, X, R, H, V, W, o->tau, b.Q, b.T, b.Pi, b.rank, b.FH, b.Uw, b.woff, warm_in,
                               b.epoch));
-  // H: G = W^T W .* V^T V
+  // H: G = W^T W .* V^T V (V^T V of the current V is left by the previous iteration's FIT
+  // within one copa_fit call)
   TRY(launch_gram<Real>(h, W, X.K, R, b.gW));
-  TRY(launch_gram<Real>(h, V, X.J, R, b.gV));
+  if (first) TRY(launch_gram<Real>(h, V, X.J, R, b.gV));
   TRY(launch_chol<Real>(h, b.gW, b.gV, R, b.Ginv, b.rho + 0));
   TRY(launch_admm_rows<Real>(h, b.FH, b.Ginv, b.rho + 0, o->n_inner, o->c_H, o->lam_H, H, DH, R, R));
   // W: G = H^T H .* V^T V, F_W fused into the ADMM
@@ -552,7 +555,7 @@ copa_status_t one_iteration(copa_ctx* h, const TensorView& X, const copa_options
   TRY(launch_chol<Real>(h, b.gH, b.gW, R, b.Ginv, b.rho + 2));
   TRY(launch_admm_rows<Real>(h, b.FV, b.Ginv, b.rho + 2, o->n_inner, o->c_V, o->lam_V, V, DV, X.J, R));
   // FIT of (Q_k, H, W, V) after the iteration
-  TRY(launch_fit_value<Real>(h, X.J, R, V, b.FV, b.UtU, b.xn2, o->x_norm2, b.fitv));
+  TRY(launch_fit_value<Real>(h, X.J, R, V, b.FV, b.UtU, b.xn2, o->x_norm2, b.fitv, b.gV));
   k_store_fit<<<1, 1, 0, h->stream>>>(b.fitv, b.hist, b.it, b.epoch);
   return cuda_check(h, cudaGetLastError(), "k_store_fit");
 }

@@ -213,9 +213,10 @@ copa_status_t launch_admm_w(copa_ctx* h, const Real* T, const Real* H, const Rea
                             const double* rho_dev, int n_inner, int c, double lam, Real* Wbar,
                             Real* DW, int64_t K, int R);
 template <typename Real>
+// VtV (R x R, FP64) receives V^T V, which the FIT needs.
 copa_status_t launch_fit_value(copa_ctx* h, int64_t J, int R, const Real* V, const Real* F_V,
                                const double* UtU, const double* xn2_dev, double x_norm2,
-                               double* fit);
+                               double* fit, double* VtV);
 template <typename Real>
 copa_status_t launch_loss_grad(copa_ctx* h, const TensorView& X, int R, const Real* Q,
                                const Real* T, const Real* Pi, const Real* H, const Real* V,

@@ -829,20 +829,12 @@ __global__ void __launch_bounds__(kWNTH) k_admm_w_tiled(const Real* __restrict__
 // ------------------------------------------------------------------------------------
 template <typename Real>
 __global__ void k_fit_value(int64_t J, int R, const Real* __restrict__ V, const Real* __restrict__ FV,
-                            const double* __restrict__ UtU, const double* __restrict__ xn2_dev,
-                            double x_norm2, double* __restrict__ fit) {
+                            const double* __restrict__ VtV, const double* __restrict__ UtU,
+                            const double* __restrict__ xn2_dev, double x_norm2, double* __restrict__ fit) {
   __shared__ double red[2][256];
   double cross = 0.0, model = 0.0;
   for (int64_t e = threadIdx.x; e < J * R; e += blockDim.x) cross += (double)V[e] * (double)FV[e];
-  const int npk = R * (R + 1) / 2;
-  for (int e = threadIdx.x; e < npk; e += blockDim.x) {
-    int r = 0, rem = e;
-    while (rem >= R - r) { rem -= R - r; ++r; }
-    const int s = r + rem;
-    double g = 0.0;
-    for (int64_t j = 0; j < J; ++j) g += (double)V[j * R + r] * (double)V[j * R + s];
-    model += (r == s ? 1.0 : 2.0) * g * UtU[r * R + s];
-  }
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) model += VtV[e] * UtU[e];
   red[0][threadIdx.x] = cross;
   red[1][threadIdx.x] = model;
   __syncthreads();
@@ -1276,8 +1268,11 @@ copa_status_t launch_admm_w(copa_ctx* h, const Real* T, const Real* H, const Rea
 
 template <typename Real>
 copa_status_t launch_fit_value(copa_ctx* h, int64_t J, int R, const Real* V, const Real* F_V,
-                               const double* UtU, const double* xn2_dev, double x_norm2, double* fit) {
-  k_fit_value<Real><<<1, 256, 0, h->stream>>>(J, R, V, F_V, UtU, xn2_dev, x_norm2, fit);
+                               const double* UtU, const double* xn2_dev, double x_norm2, double* fit,
+                               double* VtV) {
+  copa_status_t st;
+  if ((st = launch_gram<Real>(h, V, J, R, VtV)) != COPA_OK) return st;   // V^T V over many blocks
+  k_fit_value<Real><<<1, 256, 0, h->stream>>>(J, R, V, F_V, VtV, UtU, xn2_dev, x_norm2, fit);
   return cuda_check(h, cudaGetLastError(), "k_fit_value");
 }
 
@@ -1298,7 +1293,8 @@ copa_status_t launch_fit_value(copa_ctx* h, int64_t J, int R, const Real* V, con
                                              const double*, int, int, double, Real*, Real*,       \
                                              int64_t, int);                                       \
   template copa_status_t launch_fit_value<Real>(copa_ctx*, int64_t, int, const Real*, const Real*, \
-                                                const double*, const double*, double, double*);   \
+                                                const double*, const double*, double, double*,    \
+                                                double*);                                         \
 
 COPA_INST(float)
 COPA_INST(double)

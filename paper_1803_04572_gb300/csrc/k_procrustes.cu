@@ -25,6 +25,8 @@
 //     subject in each launch.
 //   * k_procrustes: every subject, one 128-thread block per subject (both forms), for the
 //     R and precisions the lane-per-row kernels do not cover.
+#include <type_traits>
+
 #include "copa_internal.cuh"
 
 namespace copa {
@@ -784,10 +786,14 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
 #pragma unroll
         for (int t = 0; t < kR; t += VN) Vc::st(B1 + lane * ld + t, z + t);
       }
-      if (lane < m) {   // the row of U_prev: independent loads, issued together
+      // U_prev (m x m, contiguous) through Us: contiguous row copies, then lane = row
+      for (int r = 0; r < m; ++r)
+        if (lane < m) Us[r * ldu + lane] = Uk[r * m + lane];
+      __syncwarp();
+      if (lane < m) {
 #pragma unroll
         for (int j = 0; j < kM; ++j)
-          if (j < m) u[j] = Uk[lane * m + j];
+          if (j < m) u[j] = Us[lane * ldu + j];
       }
       if (epoch && ((unsigned)__ldg(epoch) % kReorth) == 0u) {
         // modified Gram-Schmidt on the rows of U_prev (lane = row), two passes
@@ -946,11 +952,6 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
     }
     fold(f);
     al = sq_sum<Real, kR>(z);
-    if (Uk && lane < m) {
-#pragma unroll
-      for (int jj = 0; jj < kM; ++jj)
-        if (jj < m) Uk[lane * m + jj] = u[jj];
-    }
 
     // ---- rank cut; c_i = z_i / sigma_i for kept rows, 0 otherwise ----
     const Real amax = warp_max(al);
@@ -967,6 +968,10 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
       for (int jj = 0; jj < kM; ++jj) Us[lane * ldu + jj] = u[jj];
     }
     __syncwarp();
+    if (Uk) {   // this iteration's U for the next one: contiguous row copies from Us
+      for (int r = 0; r < m; ++r)
+        if (lane < m) Uk[r * m + lane] = Us[r * ldu + lane];
+    }
 
     // ---- q_i = sum_j U(j, i) c_j and b_i = sum_j U(i, j) p_j ----
 #pragma unroll
@@ -1684,6 +1689,68 @@ __global__ void __launch_bounds__(kFhThreads) k_fh_stream(int64_t K, int R, cons
   }
 }
 
+// The same sum in float4 units, for float with R % 4 == 0 and 16-byte aligned T and W: the
+// four entries of a unit lie in one row of T_k, so they take one float4 of w_k as well.
+// kFh4U subjects' units are loaded before their sums.
+constexpr int kFh4Threads = 256, kFh4E = 3;   // units per thread: R*R/4 <= 3 * 256 (R <= 48)
+constexpr int kFh4U = 4;
+
+__global__ void __launch_bounds__(kFh4Threads) k_fh_stream4(int64_t K, int R, const float* __restrict__ T,
+                                                            const float* __restrict__ W, double* __restrict__ part) {
+  const int n4 = R * R / 4;
+  const int64_t per = (K + gridDim.x - 1) / gridDim.x;
+  const int64_t k0 = min(K, (int64_t)blockIdx.x * per), k1 = min(K, k0 + per);
+  float s[kFh4E][4], c[kFh4E][4];
+  int col4[kFh4E];
+#pragma unroll
+  for (int j = 0; j < kFh4E; ++j) {
+    const int e4 = threadIdx.x + j * kFh4Threads;
+    col4[j] = e4 < n4 ? (4 * e4) % R / 4 : 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s[j][q] = c[j][q] = 0.f;
+  }
+  const float4* T4 = reinterpret_cast<const float4*>(T);
+  const float4* W4 = reinterpret_cast<const float4*>(W);
+  const int r4 = R / 4;
+  auto add4 = [&](int j, float4 t, float4 w) {
+    fh_add(s[j][0], c[j][0], t.x, w.x);
+    fh_add(s[j][1], c[j][1], t.y, w.y);
+    fh_add(s[j][2], c[j][2], t.z, w.z);
+    fh_add(s[j][3], c[j][3], t.w, w.w);
+  };
+  int64_t k = k0;
+  for (; k + kFh4U <= k1; k += kFh4U) {
+    float4 tv[kFh4U][kFh4E];
+#pragma unroll
+    for (int u = 0; u < kFh4U; ++u)
+#pragma unroll
+      for (int j = 0; j < kFh4E; ++j) {
+        const int e4 = threadIdx.x + j * kFh4Threads;
+        tv[u][j] = e4 < n4 ? __ldcs(T4 + (k + u) * n4 + e4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+    for (int u = 0; u < kFh4U; ++u)
+#pragma unroll
+      for (int j = 0; j < kFh4E; ++j)
+        if (threadIdx.x + j * kFh4Threads < n4) add4(j, tv[u][j], __ldg(W4 + (k + u) * r4 + col4[j]));
+  }
+  for (; k < k1; ++k) {
+#pragma unroll
+    for (int j = 0; j < kFh4E; ++j) {
+      const int e4 = threadIdx.x + j * kFh4Threads;
+      if (e4 < n4) add4(j, __ldcs(T4 + k * n4 + e4), __ldg(W4 + k * r4 + col4[j]));
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kFh4E; ++j) {
+    const int e4 = threadIdx.x + j * kFh4Threads;
+    if (e4 < n4) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) part[(size_t)blockIdx.x * R * R + 4 * e4 + q] = (double)s[j][q] + (double)c[j][q];
+    }
+  }
+}
+
 template <typename Real>
 using WarpKernel = void (*)(TensorView, int, const Real*, const Real*, const Real*, double, Real*, Real*, Real*,
                             int32_t*, const int64_t*, const int*, int*, unsigned long long*, Real*,
@@ -1816,9 +1883,14 @@ copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const R
   unsigned long long* fma_count = reinterpret_cast<unsigned long long*>(counter + 2);
   // F_H partials: one per block of the block kernel, or one per block of k_fh_stream
   int64_t fblocks = 0;
-  if (rows) {   // one wave of k_fh_stream
+  bool fh4 = false;   // float4 form of the F_H stream
+  if constexpr (std::is_same<Real, float>::value)
+    fh4 = R % 4 == 0 && (reinterpret_cast<uintptr_t>(T) & 15u) == 0 && (reinterpret_cast<uintptr_t>(W) & 15u) == 0;
+  if (rows) {   // one wave of the F_H stream
     int fh_per_sm = 0;
-    if ((st = cuda_check(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fh_per_sm, k_fh_stream<Real>, kFhThreads, 0),
+    if ((st = cuda_check(h, fh4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fh_per_sm, k_fh_stream4, kFh4Threads, 0)
+                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fh_per_sm, k_fh_stream<Real>,
+                                                                                kFhThreads, 0),
                          "occupancy")) != COPA_OK)
       return st;
     fblocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)h->num_sms * std::max(fh_per_sm, 1), X.K));
@@ -1847,8 +1919,13 @@ copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const R
         warm_in ? 1 : 0, epoch, h->d_status);
     if ((st = cuda_check(h, cudaGetLastError(), "k_procrustes_warp launch")) != COPA_OK) return st;
     if (F_H && X.K > 0) {
-      k_fh_stream<Real><<<(unsigned)fblocks, kFhThreads, 0, h->stream>>>(X.K, R, T, W, part);
-      if ((st = cuda_check(h, cudaGetLastError(), "k_fh_stream launch")) != COPA_OK) return st;
+      if constexpr (std::is_same<Real, float>::value) {
+        if (fh4) k_fh_stream4<<<(unsigned)fblocks, kFh4Threads, 0, h->stream>>>(X.K, R, T, W, part);
+        else k_fh_stream<Real><<<(unsigned)fblocks, kFhThreads, 0, h->stream>>>(X.K, R, T, W, part);
+      } else {
+        k_fh_stream<Real><<<(unsigned)fblocks, kFhThreads, 0, h->stream>>>(X.K, R, T, W, part);
+      }
+      if ((st = cuda_check(h, cudaGetLastError(), "F_H stream launch")) != COPA_OK) return st;
     }
   } else {
     k_procrustes<Real><<<(unsigned)blocks, kNT, smem, h->stream>>>(X, R, H, V, W, tau, Q, T, Pi, rank, part, order,

@@ -54,6 +54,12 @@ struct Tol<double> {
 
 __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
+// Square root for the rotation set-up and the rotation test: x * rsqrt(x) in float (the
+// rotation is orthogonal to rounding whatever the last bits of its tangent are, since c
+// and s are formed from it, and both lanes of a pair evaluate the same expression),
+// IEEE in double.
+__device__ __forceinline__ float sqrt_r(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+__device__ __forceinline__ double sqrt_r(double x) { return sqrt(x); }
 
 struct Lay {
   int R, ld;
@@ -97,7 +103,7 @@ __device__ __forceinline__ void rotation_of(Real aa, Real bb, Real gg, Real* c, 
   const Real zeta = fdiv_(bb - aa, Real(2) * gg);
   Real tt;
   if (fabs(zeta) > Real(1e15)) tt = fdiv_(Real(0.5), zeta);
-  else tt = fdiv_(zeta >= Real(0) ? Real(1) : Real(-1), fabs(zeta) + sqrt(Real(1) + zeta * zeta));
+  else tt = fdiv_(zeta >= Real(0) ? Real(1) : Real(-1), fabs(zeta) + sqrt_r(Real(1) + zeta * zeta));
   *c = rsqrt_(Real(1) + tt * tt);
   *s = *c * tt;
   if (t) *t = tt;
@@ -133,7 +139,7 @@ __device__ __forceinline__ bool pair_rotate(Real (&x)[kR], Real& f, Real& n, int
   const Real fp = __shfl_sync(kFull, f, j), np = __shfl_sync(kFull, n, j);
   const Real gg = (f * fp) * ((g4[0] + g4[1]) + (g4[2] + g4[3]));
   const Real aa = lo ? n : np, bb = lo ? np : n;
-  const bool rot = pair && gg != Real(0) && fabs(gg) > tol * sqrt(aa * bb);
+  const bool rot = pair && gg != Real(0) && fabs(gg) > tol * sqrt_r(aa * bb);
   if (rot) {
     Real c, s, tt;
     rotation_of(aa, bb, gg, &c, &s, &tt);
@@ -883,7 +889,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
         const bool lo = lane < j;
         const Real aa = lo ? al : be, bb = lo ? be : al;
         const Real gg = (f * fp) * ((g[0] + g[1]) + (g[2] + g[3]));
-        const bool rot = j != lane && gg != Real(0) && fabs(gg) > tol * sqrt(aa * bb);
+        const bool rot = j != lane && gg != Real(0) && fabs(gg) > tol * sqrt_r(aa * bb);
         const unsigned rmask = __ballot_sync(kFull, rot);
         if (rmask == 0u) continue;
         any = true;
@@ -1452,7 +1458,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_jacobi(
 #pragma unroll
         for (int t = 0; t < kR; ++t) g4[t & 3] += top[t] * bot[t];
         const Real gg = (fa * fb) * ((g4[0] + g4[1]) + (g4[2] + g4[3]));
-        const bool rot = own && gg != Real(0) && fabs(gg) > tol * sqrt(na * nb);
+        const bool rot = own && gg != Real(0) && fabs(gg) > tol * sqrt_r(na * nb);
         if (rot) {
           Real c, s, tt;
           rotation_of(na, nb, gg, &c, &s, &tt);

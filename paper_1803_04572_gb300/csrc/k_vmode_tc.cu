@@ -307,14 +307,9 @@ copa_status_t launch_uvec_tc(copa_ctx* h, int64_t S, int R, const float* Q, cons
   if ((st = cuda_check(h, cudaFuncSetAttribute(k_uvec_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100),
                        "cudaFuncSetAttribute")) != COPA_OK)
     return st;
-  int per_sm = 0;
-  if ((st = cuda_check(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_uvec_tc, kTM, L.total),
-                       "occupancy")) != COPA_OK)
-    return st;
   // Two CTAs per SM (2 x 256 tensor-memory columns): shared memory (2 x 91 KB) and registers
-  // (2 x 128 x 256) fit; the occupancy query reports one for this kernel, so it is not used.
-  (void)per_sm;
-  per_sm = 2;
+  // (2 x 128 x 256) fit. (The occupancy query reported one for this kernel.)
+  const int per_sm = 2;
   const int64_t ntiles = (S + kTM - 1) / kTM;
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)h->num_sms * per_sm, ntiles));
   *nparts = blocks * 2;

@@ -1017,12 +1017,27 @@ __global__ void __launch_bounds__(kSRT, 1) k_spmm_rows(TensorView X, int R, cons
     const int per_step = 32 / lw, sub = lane / lw, c = lane - sub * lw;
     for (int e = threadIdx.x; e < X.J * 32; e += kSRT) Fs[e] = 0.f;
     __syncthreads();
-    for (int64_t base = p0 + (int64_t)warp * 32; base < p1; base += (int64_t)nw * 32) {
-      const int64_t p = base + lane;
+    // Chunks of 32 nonzeros, software-pipelined: the column, value and row of chunk n + 2
+    // are loaded, and the U lines of chunk n + 1 prefetched into L1, while chunk n is added.
+    constexpr int64_t step = (int64_t)nw * 32;
+    auto load = [&](int64_t b, int& j, float& x, int& i) {
+      const int64_t p = b + lane;
       const bool v = p < p1;
-      const int jj = v ? __ldg(X.col + p) : 0;
-      const float xx = v ? load_valf(X, p) : 0.f;
-      const int ii = v ? __ldg(nzrow + p) : 0;
+      j = v ? __ldg(X.col + p) : 0;
+      x = v ? load_valf(X, p) : 0.f;
+      i = v ? __ldg(nzrow + p) : 0;
+    };
+    const int64_t first = p0 + (int64_t)warp * 32;
+    int jj, ii, j1, i1;
+    float xx, x1;
+    load(first, jj, xx, ii);
+    load(first + step, j1, x1, i1);
+    for (int64_t base = first; base < p1; base += step) {
+      int j2, i2;
+      float x2;
+      load(base + 2 * step, j2, x2, i2);
+      if (base + step + lane < p1 && c0 < R)   // this lane's nonzero of the next chunk: its U line
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(U + (int64_t)i1 * R + c0));
       const int cnt = (int)min((int64_t)32, p1 - base);
 #pragma unroll 4
       for (int q = 0; q < 32; q += per_step) {
@@ -1032,6 +1047,8 @@ __global__ void __launch_bounds__(kSRT, 1) k_spmm_rows(TensorView X, int R, cons
         const int i = __shfl_sync(kFull, ii, src);
         if (src < cnt && c < w) atomicAdd(&Fs[j * 32 + c], x * __ldg(U + (int64_t)i * R + c0 + c));
       }
+      jj = j1; xx = x1; ii = i1;
+      j1 = j2; x1 = x2; i1 = i2;
     }
     __syncthreads();
     float* pp = part + ((size_t)blockIdx.x * npass + pass) * (size_t)X.J * 32;

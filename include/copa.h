@@ -131,6 +131,17 @@ copa_status_t copa_procrustes(copa_handle_t handle, const copa_tensor_t* X, int3
  * figure of the benchmark). Synchronises; writes 0 before the first launch. */
 copa_status_t copa_procrustes_work(copa_handle_t handle, double* fma_host);
 
+/* Test hook (no counterpart in the paper). COPA_DEBUG_TC_FORCE_TIMEOUT_NS = value > 0 makes
+ * the first bounded wait of every later launch of the tensor-core V-mode kernel (FP32
+ * handles, copa_mttkrp(COPA_MODE_V) and copa_fit) wait on an mbarrier that nothing arrives
+ * at, for `value` ns, instead of on its first MMA batch: the kernel then takes its timeout
+ * path (status COPA_ERR_TIMEOUT, reported by the next synchronising call; it waits for the
+ * MMAs it issued, frees its tensor memory and returns), so that this path can be tested
+ * without a fault. 0 switches it off. value must be in [0, 1e9]; other keys return
+ * COPA_ERR_INVALID_ARG. The results of an affected call are undefined. */
+enum { COPA_DEBUG_TC_FORCE_TIMEOUT_NS = 1 };
+copa_status_t copa_debug_set(copa_handle_t handle, int32_t key, int64_t value);
+
 /* Diagnostic (no counterpart in the paper): the number of kernels the last copa_fit call
  * on this handle launched (the kernel nodes of the captured iteration graph times n_outer,
  * plus set-up kernels), or -1 if unknown (use_graph = 0). */
@@ -167,7 +178,10 @@ copa_status_t copa_gram(copa_handle_t handle, const void* A, int64_t rows, int32
  * Runs on the calling thread's current device. R > 90 returns COPA_ERR_UNSUPPORTED,
  * other bad sizes or NULL pointers COPA_ERR_INVALID_ARG. The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress, no allocation); make that first
- * call before any stream capture. All calls share the one array, which keeps the last
+ * call before any stream capture. That address is cached for the life of the process,
+ * which assumes the device's primary context is never reset (no cudaDeviceReset while
+ * the library is loaded). A CUDA error already pending on the calling thread when the
+ * call starts is left in place and the call returns COPA_ERR_CUDA without launching. All calls share the one array, which keeps the last
  * call's contents: calls that may overlap on the GPU (other streams, other host threads)
  * race and must be serialised by the caller. Asynchronous: launch errors are returned at
  * once, execution errors surface at the caller's next synchronisation. */

@@ -32,7 +32,7 @@ EXPORTED = ["copa_create", "copa_destroy", "copa_last_error", "copa_sync", "copa
             "copa_procrustes", "copa_mttkrp", "copa_gram", "copa_admm_step", "copa_admm_w_fused",
             "copa_fit_value", "copa_fit", "copa_fit_host", "copa_smooth_plan",
             "copa_smooth_project", "copa_loss_grad", "copa_procrustes_work", "copa_gram_noalloc",
-            "copa_fit_launches"]
+            "copa_fit_launches", "copa_debug_set"]
 
 
 class CopaError(RuntimeError):
@@ -82,6 +82,7 @@ _sig = {
     "copa_procrustes_work": [_V, POINTER(c_double)],
     "copa_gram_noalloc": [_V, c_int32, _V, c_int64, c_int32, _V],
     "copa_fit_launches": [_V, POINTER(c_int64)],
+    "copa_debug_set": [_V, c_int32, c_int64],
 }
 for _n, _a in _sig.items():
     getattr(_lib, _n).argtypes = _a
@@ -302,6 +303,11 @@ class Copa:
                                              _ptr(C))
         return Xp, C
 
+    def debug_set(self, key: int, value: int):
+        """Test hook of copa_debug_set (key 1: force the tensor-core V-mode kernel's first
+        wait to run out after `value` ns; 0 switches it off)."""
+        self._check(_lib.copa_debug_set(self.h, key, value))
+
     def fit_launches(self) -> int:
         """Kernels launched by the last fit() (graph nodes x iterations + set-up), -1 if unknown."""
         v = c_int64()
@@ -325,10 +331,29 @@ class Copa:
 def gram_noalloc(A, G, stream):
     """G = A^T A through copa_gram_noalloc, which allocates nothing (see include/copa.h).
     A: rows x R float32/float64 CUDA tensor; G: R x R float64 CUDA tensor (written);
-    stream: a torch.cuda.Stream to enqueue on. Raises CopaError on a bad argument."""
+    stream: a torch.cuda.Stream to enqueue on. The call receives raw pointers, so every
+    property the kernel relies on (dtype, shape, contiguity, device) is checked here
+    first; a mismatch raises CopaError(ERR_INVALID_ARG) before anything is launched."""
     import torch
+
+    def bad(why):
+        raise CopaError(ERR_INVALID_ARG, "gram_noalloc: " + why)
+
+    if not (isinstance(A, torch.Tensor) and isinstance(G, torch.Tensor)):
+        bad("A and G must be torch tensors")
+    if A.dtype not in (torch.float32, torch.float64):
+        bad(f"A must be float32 or float64, not {A.dtype}")
+    if A.dim() != 2 or not A.is_contiguous():
+        bad("A must be a contiguous rows x R matrix")
+    R = A.shape[1]
+    if G.dtype != torch.float64 or tuple(G.shape) != (R, R) or not G.is_contiguous():
+        bad(f"G must be a contiguous {R} x {R} float64 matrix")
+    cur = torch.cuda.current_device()
+    for name, t in (("A", A), ("G", G)):
+        if t.device.type != "cuda" or t.device.index != cur:
+            bad(f"{name} must be on the current CUDA device (cuda:{cur}), not {t.device}")
     code = _lib.copa_gram_noalloc(c_void_p(stream.cuda_stream), 1 if A.dtype == torch.float64 else 0,
-                                  _ptr(A), A.shape[0], A.shape[1], _ptr(G))
+                                  _ptr(A), A.shape[0], R, _ptr(G))
     if code != OK:
         raise CopaError(code, "copa_gram_noalloc failed")
 

@@ -266,7 +266,11 @@ static copa_status_t sync_status(copa_ctx* h) {
   const int code = hs[0];
   if (code == COPA_ERR_NUMERIC)
     return fail(h, COPA_ERR_NUMERIC, "G + rho I is not positive definite or not finite");
-  if (code == COPA_ERR_TIMEOUT) return fail(h, COPA_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (code == COPA_ERR_TIMEOUT)
+    return fail(h, COPA_ERR_TIMEOUT,
+                std::string("a bounded device wait gave up (site ") + std::to_string(hs[1]) + ")" +
+                    (hs[2] == 3 ? "; the work in flight did not finish either: do not use this handle further"
+                                : ""));
   static const char* what[] = {"subj_ptr[0] != 0 or subj_ptr[K] != S", "row_ptr[0] != 0 or row_ptr[S] != nnz",
                                "subj_ptr decreases at subject", "row_ptr decreases at row",
                                "column index out of [0, J) in row", "columns not strictly increasing in row",
@@ -370,6 +374,17 @@ copa_status_t copa_procrustes(copa_handle_t h, const copa_tensor_t* X, int32_t R
   return launch_procrustes<double>(h, v, R, (const double*)H, (const double*)V, (const double*)W, tau,
                                    (double*)out->Q, (double*)out->T, (double*)out->Pi, out->rank,
                                    (double*)F_H);
+}
+
+copa_status_t copa_debug_set(copa_handle_t h, int32_t key, int64_t value) {
+  CHECK_H(h);
+  if (key == COPA_DEBUG_TC_FORCE_TIMEOUT_NS) {
+    if (value < 0 || value > 1000000000LL)
+      return fail(h, COPA_ERR_INVALID_ARG, "copa_debug_set: timeout must be in [0, 1e9] ns");
+    h->dbg_tc_force_ns = value;
+    return COPA_OK;
+  }
+  return fail(h, COPA_ERR_INVALID_ARG, "copa_debug_set: unknown key");
 }
 
 copa_status_t copa_fit_launches(copa_handle_t h, int64_t* launches_host) {

@@ -134,6 +134,9 @@ struct copa_ctx {
   const int32_t* csc_key = nullptr;
   int64_t csc_nnz = -1, csc_S = -1;
   int csc_J = 0, csc_prec = -1;
+  // test hook: > 0 makes the first mbarrier wait of the tensor-core V-mode kernel run out
+  // after this many ns on an mbarrier that nothing arrives at (copa_debug_set)
+  int64_t dbg_tc_force_ns = 0;
   // cached nonzero -> row and row -> subject maps (row-order F_V path)
   const int32_t* rmap_key = nullptr;
   int64_t rmap_nnz = -1, rmap_S = -1, rmap_K = -1;

@@ -1374,6 +1374,9 @@ extern "C" copa_status_t copa_gram_noalloc(void* stream, int32_t a_is_double, co
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   double* part = reinterpret_cast<double*>(scratch);
   // every block writes its whole R x R partial, so nothing has to be cleared first
+  // An error left pending by earlier, unrelated work is not this call's failure: refuse to
+  // launch (and leave the error for its owner to collect) instead of clearing it.
+  if (cudaPeekAtLastError() != cudaSuccess) return COPA_ERR_CUDA;
   if (a_is_double) {
     k_gram<double><<<(unsigned)blocks, threads, sizeof(double) * 64 * (size_t)R, st>>>(
         reinterpret_cast<const double*>(A), rows, R, part);
@@ -1381,6 +1384,8 @@ extern "C" copa_status_t copa_gram_noalloc(void* stream, int32_t a_is_double, co
     k_gram<float><<<(unsigned)blocks, threads, sizeof(float) * 64 * (size_t)R, st>>>(
         reinterpret_cast<const float*>(A), rows, R, part);
   }
+  // the reduction must not run over the previous call's partials if the Gram did not launch
+  if (cudaGetLastError() != cudaSuccess) return COPA_ERR_CUDA;
   k_reduce_rows<double><<<(R * R + 255) / 256, 256, 0, st>>>(part, (int)blocks, R * R, G);
   if (cudaGetLastError() != cudaSuccess) return COPA_ERR_CUDA;
   return COPA_OK;

@@ -26,8 +26,12 @@
 //   5. the threads owning lanes r < R and 64 + r read columns c and 64 + c and add them to
 //      their compensated sums.
 // Every wait on an mbarrier is bounded (1 s of wall time); a timeout records
-// COPA_ERR_TIMEOUT in the status word, waits once more for the MMAs in flight, frees the
-// tensor memory and ends the kernel.
+// COPA_ERR_TIMEOUT in the status word, waits once more (bounded) for the MMAs in flight,
+// frees the tensor memory and ends the kernel. If that second wait gives up as well, detail
+// word 2 of the status is set to 3: the tensor memory was released while MMAs may still have
+// been writing it, and the handle should not be used further. For tests of this path a
+// launch can make its first wait run out on purpose: it then waits on an mbarrier that
+// nothing arrives at (force_ns of wall time) instead of the first MMA commit.
 #include "copa_internal.cuh"
 #include "tc_sm100.cuh"
 
@@ -94,7 +98,8 @@ __device__ __forceinline__ float4 split4(float4 x, float4& lo) {
 __global__ void __launch_bounds__(kTM, 2) k_uvec_tc(int64_t S, int R, const float* __restrict__ Q,
                                                     const float* __restrict__ H, const float* __restrict__ W,
                                                     const int32_t* __restrict__ row_subj, float* __restrict__ U,
-                                                    double* __restrict__ utu_part, int* __restrict__ status) {
+                                                    double* __restrict__ utu_part, int* __restrict__ status,
+                                                    uint64_t force_ns) {
   const TcLay L = tc_lay(R);
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* opg = smem;                  // the Gram's A operand (128 rows), aliasing the Q tile
@@ -103,9 +108,10 @@ __global__ void __launch_bounds__(kTM, 2) k_uvec_tc(int64_t S, int R, const floa
   unsigned char* ohh = smem + kGBytes;        // H^T, hi
   unsigned char* ohl = ohh + L.hbytes;        // H^T, lo
   uint64_t* bars = reinterpret_cast<uint64_t*>(ohl + L.hbytes);
-  uint32_t* taddr_s = reinterpret_cast<uint32_t*>(bars + 2);
+  uint32_t* taddr_s = reinterpret_cast<uint32_t*>(bars + 3);
   const int tid = threadIdx.x, warp = tid >> 5;
   const uint32_t bar1 = tc::smem_u32(bars), bar2 = tc::smem_u32(bars + 1);
+  const uint32_t bar_never = tc::smem_u32(bars + 2);   // nothing arrives here (timeout tests)
 
   for (int e = tid; e < L.NP * L.KP; e += kTM) {   // H^T: element (n, k) = H(k, n), zero-padded
     const int n = e / L.KP, k = e - n * L.KP;
@@ -117,6 +123,7 @@ __global__ void __launch_bounds__(kTM, 2) k_uvec_tc(int64_t S, int R, const floa
   if (tid == 0) {
     tc::mbar_init(bar1, 1);
     tc::mbar_init(bar2, 1);
+    tc::mbar_init(bar_never, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -204,10 +211,12 @@ __global__ void __launch_bounds__(kTM, 2) k_uvec_tc(int64_t S, int R, const floa
       }
       tc::mma_commit(bar1);
     }
-    bool ok = tc::mbar_wait(bar1, ph, kWaitNs);
+    bool ok = force_ns ? tc::mbar_wait(bar_never, 0, force_ns) : tc::mbar_wait(bar1, ph, kWaitNs);
     if (__syncthreads_or(!ok)) {
       if (tid == 0) set_status(status, COPA_ERR_TIMEOUT, 1);
-      tc::mbar_wait(bar1, ph, kWaitNs);   // the MMAs in flight, before the memory is released
+      // the MMAs in flight, before the memory is released
+      const bool drained = tc::mbar_wait(bar1, ph, kWaitNs);
+      if (__syncthreads_or(!drained) && tid == 0) status[2] = 3;
       failed = true;
       break;
     }
@@ -253,7 +262,8 @@ __global__ void __launch_bounds__(kTM, 2) k_uvec_tc(int64_t S, int R, const floa
     ok = tc::mbar_wait(bar2, ph, kWaitNs);
     if (__syncthreads_or(!ok)) {
       if (tid == 0) set_status(status, COPA_ERR_TIMEOUT, 2);
-      tc::mbar_wait(bar2, ph, kWaitNs);
+      const bool drained = tc::mbar_wait(bar2, ph, kWaitNs);
+      if (__syncthreads_or(!drained) && tid == 0) status[2] = 3;
       failed = true;
       break;
     }
@@ -314,7 +324,8 @@ copa_status_t launch_uvec_tc(copa_ctx* h, int64_t S, int R, const float* Q, cons
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)h->num_sms * per_sm, ntiles));
   *nparts = blocks * 2;
   if (size_only) return COPA_OK;
-  k_uvec_tc<<<(unsigned)blocks, kTM, L.total, h->stream>>>(S, R, Q, H, W, rsubj, U, utu_part, h->d_status);
+  k_uvec_tc<<<(unsigned)blocks, kTM, L.total, h->stream>>>(S, R, Q, H, W, rsubj, U, utu_part, h->d_status,
+                                                          (uint64_t)h->dbg_tc_force_ns);
   return cuda_check(h, cudaGetLastError(), "k_uvec_tc");
 }
 

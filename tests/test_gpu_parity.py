@@ -1,10 +1,16 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle, step by step.
 
 Each step of the GPU path is fed the same state as the oracle step (step-isolated) and
-compared element-wise. Tolerances: the FP64 handle must agree to 1e-10 relative
-(Frobenius, per step); the mixed handle (FP32 bulk, FP64 Gram/eigen/Cholesky) to 1e-5
-relative per step. Subjects whose Procrustes spectrum has an eigenvalue ratio within a
-factor 100 of the rank cut tau are excluded from element-wise checks (counted)."""
+compared element by element. Tolerances: the FP64 handle must agree to 1e-10 relative
+per step; the mixed handle (FP32 bulk, FP64 Gram/Cholesky/FIT) to 1e-5 relative per
+step. "Relative" for an element is relative to the sum of the magnitudes of the terms
+that make it up (computed by the same formula on absolute values): an FP32 sum of many
+terms is accurate to a multiple of u times that sum, not times its possibly much smaller
+value, so this is the bound floating point gives element by element. The Procrustes step
+of the mixed handle is FP32 one-sided Jacobi, whose error grows with the condition number
+kappa_k of A_k; it is held to 1e-5 (aggregate) over subjects with kappa_k <= 100 and
+reported in kappa bins. Subjects whose Procrustes spectrum has an eigenvalue ratio within
+a factor 100 of the rank cut tau are excluded from element-wise checks (counted, capped)."""
 import numpy as np
 import pytest
 
@@ -14,6 +20,7 @@ from oracle import copa_oracle as O
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-10, "mixed": 1e-5}
+U32 = 2.0 ** -24
 
 
 @pytest.fixture(scope="module")
@@ -31,6 +38,31 @@ def rel(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def assert_elementwise(got, ref, mag, tol, what=""):
+    """|got - ref| <= tol * mag element by element, mag being the sum of the magnitudes
+    of the terms of each element (>= |ref|). Reports the worst element on failure."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    mag = np.maximum(np.asarray(mag, dtype=np.float64), np.abs(ref))
+    assert got.shape == ref.shape, (what, got.shape, ref.shape)
+    err = np.abs(got - ref)
+    bound = tol * mag + 1e-300
+    ratio = err / bound
+    if ratio.size and ratio.max() > 1.0:
+        i = np.unravel_index(np.argmax(ratio), ratio.shape)
+        raise AssertionError(f"{what}: element {i}: got {got[i]!r} ref {ref[i]!r} "
+                             f"|err| {err[i]:.3e} > {tol:g} x {mag[i]:.3e}")
+
+
+def rowscale(ref):
+    """Per-row magnitude scale max_j |ref_ij| (for iterated results such as the ADMM
+    state, where no term sum exists): entries are compared to tol (|ref| + row max)."""
+    ref = np.asarray(ref, dtype=np.float64)
+    if ref.ndim == 1:
+        return np.abs(ref) + np.abs(ref).max(initial=0.0)
+    return np.abs(ref) + np.abs(ref).max(axis=-1, keepdims=True)
 
 
 def T(h, a):
@@ -75,10 +107,20 @@ CASES = [
     (40, 60, 56, 30, 1, 90),   # R = 56: the block kernel in both precisions
 ]
 
+# Tall subjects of the sizes the K = 500k workload reaches (I_k up to 2000): the QR folds
+# 16 to 63 blocks of 32 rows into R_A before the Jacobi, in FP32 on the mixed handle.
+TALL_SIZES = [2000, 500, 1000, 37, 3, 64, 1200]
+
 
 def make_case(K, J, R, med, lo, hi, seed=0):
     X = synth.ehr_custom(K, J, median=med, lo=lo, hi=hi, lam=3.0, cmax=20, seed=seed)
     X = synth.with_edge_cases(X)
+    H, V, W = synth.random_state(X.K, X.J, R, seed=seed + 11)
+    return X, H, V, W
+
+
+def make_tall_case(J=300, R=40, seed=21):
+    X = synth.ehr_tensor(len(TALL_SIZES), J, np.array(TALL_SIZES, dtype=np.int64), 4.0, 50, seed)
     H, V, W = synth.random_state(X.K, X.J, R, seed=seed + 11)
     return X, H, V, W
 
@@ -99,16 +141,12 @@ def kappa_kept(A, tau=O.TAU):
     return float(kept[0] / kept[-1])
 
 
-@pytest.mark.parametrize("case", CASES)
-def test_procrustes_step(h, P, case):
-    """Q_k, T_k = Q_k^T X_k V, Pi_k = Q_k^T Q_k, rank and F_H against the oracle.
-    FP64 handle: 1e-10 relative (aggregate Frobenius). Mixed handle: the FP32 arithmetic
-    in P_k = X_k V, A_k = P_k S_k H^T and the QR/Jacobi steps has a backward error of
-    about R u (u = 2^-24) and the polar factor amplifies it by up to the condition number
-    kappa_k of the kept part of A_k, so each subject must satisfy
-    err_k <= 1e-5 + 4 R u kappa_k (Q_k and T_k) and the aggregate must stay <= 1e-4."""
-    K, J, R, med, lo, hi = case
-    X, H, V, W = make_case(K, J, R, med, lo, hi)
+KAPPA_BINS = [(1.0, 10.0), (10.0, 100.0), (100.0, 1e3), (1e3, np.inf)]
+
+
+def _check_procrustes(h, P, X, H, V, W, R):
+    """Q_k, T_k = Q_k^T X_k V, Pi_k = Q_k^T Q_k, rank and F_H against the oracle (see
+    test_procrustes_step). Returns the aggregate errors (for printing)."""
     H, V, W = inputs_for(h, H, V, W)
     Xd = dev_tensor(h, P, X)
     st = h.procrustes(Xd, R, T(h, H), T(h, V), T(h, W), want_pi=True, want_rank=True)
@@ -116,43 +154,80 @@ def test_procrustes_step(h, P, case):
     Qg, Tg, Pig = N(st["Q"]), N(st["T"]), N(st["Pi"])
     rank = st["rank"].cpu().numpy()
     skip = band_subjects(X, H, V, W, width=2.0 if h.precision == "fp64" else 100.0)
+    # the band is where the rank decision sits on a singular value; it must stay rare
+    assert len(skip) <= max(1, X.K // 10), ("too many band subjects", len(skip), X.K)
     tol = TOL[h.precision]
-    num = {"q": 0.0, "t": 0.0, "q100": 0.0, "t100": 0.0}
-    den = {"q": 0.0, "t": 0.0, "q100": 0.0, "t100": 0.0}
-    FH = np.zeros((R, R))
+    keys = ["q", "t", "q100", "t100"] + [f"{w}{i}" for w in "qt" for i in range(len(KAPPA_BINS))]
+    num = dict.fromkeys(keys, 0.0)
+    den = dict.fromkeys(keys, 0.0)
+    nbin = [0] * len(KAPPA_BINS)
+    FH, FHmag = np.zeros((R, R)), np.zeros((R, R))
     worst = []
     for k in range(X.K):
         Xk = X.dense(k)
+        Sk = np.diag(W[k])
+        if k in skip:      # both rank decisions are valid here: take the GPU's T_k
+            FH += Tg[k] @ Sk
+            FHmag += np.abs(Tg[k]) @ np.abs(Sk)
+            continue
         Qo = O.procrustes(Xk, V, W[k], H)
         To = Qo.T @ Xk @ V
-        FH += To @ np.diag(W[k])
-        if k in skip:
-            continue
+        FH += To @ Sk
+        FHmag += (np.abs(Qo).T @ np.abs(Xk) @ np.abs(V)) @ np.abs(Sk)
         rows = slice(X.subj_ptr[k], X.subj_ptr[k + 1])
-        kap = kappa_kept(Xk @ V @ np.diag(W[k]) @ H.T)
+        kap = kappa_kept(Xk @ V @ Sk @ H.T)
         dq, dt = np.sum((Qg[rows] - Qo) ** 2), np.sum((Tg[k] - To) ** 2)
         nq, nt = np.sum(Qo ** 2), np.sum(To ** 2)
+        b = next(i for i, (lo, hi) in enumerate(KAPPA_BINS) if lo <= kap < hi)
+        nbin[b] += 1
         for key, d, n in (("q", dq, nq), ("t", dt, nt)):
-            num[key] += d
-            den[key] += n
-            if kap <= 100:
-                num[key + "100"] += d
-                den[key + "100"] += n
+            for kk in (key, f"{key}{b}") + ((key + "100",) if kap <= 100 else ()):
+                num[kk] += d
+                den[kk] += n
         ek = max(np.sqrt(dq / max(nq, 1e-300)), np.sqrt(dt / max(nt, 1e-300)))
-        worst.append((ek / (1e-5 + 4 * R * 2.0 ** -24 * kap), k, ek, kap))
+        worst.append((ek / (1e-5 + 4 * R * U32 * kap), k, ek, kap))
         assert rank[k] == (np.linalg.matrix_rank(Qo, tol=0.5) if Qo.size else 0), k
         np.testing.assert_allclose(Pig[k], Qo.T @ Qo, atol=100 * tol)
-    agg = {key: np.sqrt(num[key] / max(den[key], 1e-300)) for key in num}
+    agg = {key: np.sqrt(num[key] / den[key]) if den[key] > 0 else 0.0 for key in num}
+    bins = ", ".join(f"kappa [{lo:g},{hi:g}): n={nbin[i]} Q {agg[f'q{i}']:.1e} T {agg[f't{i}']:.1e}"
+                     for i, (lo, hi) in enumerate(KAPPA_BINS))
+    print(f"\n{h.precision} R={R} K={X.K}: aggregate rel err Q {agg['q']:.2e} T {agg['t']:.2e} "
+          f"(kappa<=100: Q {agg['q100']:.2e} T {agg['t100']:.2e}); {bins}; "
+          f"excluded {len(skip)} band subjects")
     if h.precision == "fp64":
         assert agg["q"] <= tol and agg["t"] <= tol, agg
     else:
-        # FP32: backward error ~R u (u = 2^-24) amplified by kappa_k
-        w = max(worst)
+        # the per-step bar where FP32 can meet it: well-conditioned subjects
+        assert agg["q100"] <= 1e-5 and agg["t100"] <= 1e-5, agg
+        # every non-band subject: aggregate 1e-4, and each subject within its own
+        # FP32 bound (backward error ~R u, u = 2^-24, amplified by kappa_k)
+        assert agg["q"] <= 1e-4 and agg["t"] <= 1e-4, agg
+        w = max(worst) if worst else (0.0,)
         assert w[0] <= 1.0, ("per-subject bound 1e-5 + 4 R u kappa", w)
-    print(f"\n{h.precision} R={R}: aggregate rel err Q {agg['q']:.2e} T {agg['t']:.2e} "
-          f"(kappa<=100: {agg['q100']:.2e}); excluded {len(skip)} band subjects")
-    if not skip:
-        assert rel(N(st["F_H"]), FH) <= (tol if h.precision == "fp64" else 1e-4)
+    assert_elementwise(N(st["F_H"]), FH, FHmag, tol, "F_H")
+    return agg
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_procrustes_step(h, P, case):
+    """Q_k, T_k = Q_k^T X_k V, Pi_k = Q_k^T Q_k, rank and F_H against the oracle.
+    FP64 handle: 1e-10 relative (aggregate Frobenius over subjects). Mixed handle: the
+    FP32 arithmetic in P_k = X_k V, A_k = P_k S_k H^T and the QR/Jacobi steps has a
+    backward error of about R u (u = 2^-24) and the polar factor amplifies it by up to the
+    condition number kappa_k of the kept part of A_k. So: aggregate <= 1e-5 over the
+    subjects with kappa_k <= 100 (the per-step bar), aggregate <= 1e-4 over all non-band
+    subjects, and err_k <= 1e-5 + 4 R u kappa_k for each subject; errors are printed in
+    kappa bins. F_H is compared element by element (band subjects contribute the GPU's
+    own T_k, both rank decisions being valid there)."""
+    K, J, R, med, lo, hi = case
+    X, H, V, W = make_case(K, J, R, med, lo, hi)
+    _check_procrustes(h, P, X, H, V, W, R)
+
+
+def test_procrustes_tall_subjects(h, P):
+    """Subjects of 500 to 2000 visits at R = 40 (the QR over up to 63 row blocks)."""
+    X, H, V, W = make_tall_case()
+    _check_procrustes(h, P, X, H, V, W, 40)
 
 
 def _state_after_procrustes(X, H, V, W):
@@ -170,10 +245,12 @@ def oracle_state(h, X, H, V, W):
 
 
 # (30, 1700, ...): J x 32 floats exceed the shared memory of the row-order F_V kernel, so
-# FP32 takes the column-sorted path as well
-@pytest.mark.parametrize("case", CASES[:3] + [(30, 70, 48, 20, 1, 80), (30, 1700, 40, 20, 1, 80)])
+# FP32 takes the column-sorted path as well; R = 56 takes the CUDA-core V tile kernel
+@pytest.mark.parametrize("case", CASES[:3] + [(30, 70, 48, 20, 1, 80), (30, 1700, 40, 20, 1, 80), CASES[6]])
 def test_mttkrp_steps(h, P, case):
-    """The three MTTKRPs and U^T U, fed the oracle's Q_k and T_k (step-isolated)."""
+    """The three MTTKRPs and U^T U, fed the oracle's Q_k and T_k (step-isolated), element
+    by element against the oracle, each element within tol of the magnitude sum of its
+    terms."""
     K, J, R, med, lo, hi = case
     X, H, V, W = make_case(K, J, R, med, lo, hi, seed=1)
     H, V, W = inputs_for(h, H, V, W)
@@ -181,6 +258,7 @@ def test_mttkrp_steps(h, P, case):
     Q, st = oracle_state(h, X, H, V, W)
     Qr = Q if h.precision == "fp64" else [q.astype(np.float32).astype(np.float64) for q in Q]
     sl = O.project_all(X, Qr)
+    sl_abs = O.project_all(X, [np.abs(q) for q in Qr])     # counts are >= 0: |X_k| = X_k
     H2, _, W2 = inputs_for(h, *synth.random_state(X.K, X.J, R, seed=99))   # "updated" H, W
     tol = TOL[h.precision]
     FH = h.mttkrp("H", Xd, R, st, W=T(h, W))
@@ -188,57 +266,98 @@ def test_mttkrp_steps(h, P, case):
     FV, UtU = h.mttkrp("V", Xd, R, st, H=T(h, H2), W=T(h, W2), want_utu=True)
     h.sync()
     Tr = N(st["T"])
-    assert rel(N(FH), sum(Tr[k] @ np.diag(W[k]) for k in range(X.K))) <= tol
-    assert rel(N(FW), np.stack([np.sum(H2 * Tr[k], axis=0) for k in range(X.K)])) <= tol
-    assert rel(N(FV), O.mttkrp_V(sl, H2, W2, X.J)) <= tol
+    assert_elementwise(N(FH), sum(Tr[k] @ np.diag(W[k]) for k in range(X.K)),
+                       sum(np.abs(Tr[k]) @ np.diag(np.abs(W[k])) for k in range(X.K)), tol, "F_H")
+    assert_elementwise(N(FW), np.stack([np.sum(H2 * Tr[k], axis=0) for k in range(X.K)]),
+                       np.stack([np.sum(np.abs(H2 * Tr[k]), axis=0) for k in range(X.K)]), tol, "F_W")
+    assert_elementwise(N(FV), O.mttkrp_V(sl, H2, W2, X.J), O.mttkrp_V(sl_abs, np.abs(H2), np.abs(W2), X.J),
+                       tol, "F_V")
     Uo = sum(np.diag(W2[k]) @ H2.T @ Qr[k].T @ Qr[k] @ H2 @ np.diag(W2[k]) for k in range(X.K))
-    assert rel(N(UtU), Uo) <= tol
+    Um = 0.0
+    for k in range(X.K):
+        Ua = np.abs(Qr[k]) @ np.abs(H2) @ np.diag(np.abs(W2[k]))
+        Um = Um + Ua.T @ Ua
+    assert_elementwise(N(UtU), Uo, Um, tol, "U^T U")
     # and the same formulas hold for the oracle's own T_k, Q_k in FP64
     if h.precision == "fp64":
         assert rel(N(FH), O.mttkrp_H(sl, V, W)) <= tol
         assert rel(N(FW), O.mttkrp_W(sl, H2, V)) <= tol
 
 
+def _admm_margins(F, G, Zb0, D0, n_inner, kind, lam):
+    """The oracle's ADMM run one inner iteration at a time, returning the final state and,
+    per element, the smallest relative distance |v^2 - 2 lam/rho| / (2 lam/rho) of the prox
+    argument v = z - d to the jump of the l0 prox over the iterations. An element that came
+    that close to the jump may legitimately round to the other branch in another precision.
+    The other proxes are continuous with Lipschitz constant 1 (margin infinite)."""
+    Zb, D = Zb0.copy(), D0.copy()
+    margin = np.full(F.shape, np.inf)
+    rho = None
+    for _ in range(n_inner):
+        Dprev = D
+        Z, Zb, D, rho, _ = O.admm(F, G, Zb, D, 1, kind, lam)
+        v = Z - Dprev
+        if kind == O.L0:
+            t = 2.0 * lam / rho
+            m = np.abs(v * v - t) / t
+        else:
+            m = np.full(F.shape, np.inf)
+        margin = np.minimum(margin, m)
+    return Zb, D, rho, margin
+
+
+@pytest.mark.parametrize("R", [9, 40, 56])
 @pytest.mark.parametrize("constraint,lam", [("none", 0.0), ("nonneg", 0.0), ("l1", 0.8), ("l0", 0.5)])
-def test_admm_step_rows(h, P, constraint, lam):
-    rng = np.random.default_rng(5)
-    rows, R = 133, 9
-    A, B = rng.random((50, R)), rng.random((70, R))
+def test_admm_step_rows(h, P, constraint, lam, R):
+    """The row ADMM (H and V updates) against the oracle's, element by element. For l0,
+    rows in which some element's prox argument came within 1e-4 (relative) of the jump are
+    left out (at most 5% of the rows)."""
+    rng = np.random.default_rng(5 + R)
+    rows = 133 if R == 9 else 1037
+    A, B = rng.random((50 + R, R)), rng.random((70 + R, R))
     Ga, Gb = A.T @ A, B.T @ B
-    F = rng.standard_normal((rows, R)) * 20
+    F = rng.standard_normal((rows, R)) * 20 * R
     Zb0, D0 = rng.standard_normal((rows, R)), rng.standard_normal((rows, R)) * 0.1
-    _, Zo, Do, rho_o, _ = O.admm(F, Ga * Gb, Zb0, D0, 15, constraint, lam)
+    Zo, Do, rho_o, margin = _admm_margins(F, Ga * Gb, Zb0, D0, 15, constraint, lam)
     Zb, D = T(h, Zb0), T(h, D0)
     rho = h.admm_step(T(h, F), h.torch.as_tensor(Ga, device=h.device),
                       h.torch.as_tensor(Gb, device=h.device), 15, constraint, lam, Zb, D)
     h.sync()
     tol = TOL[h.precision]
     assert abs(float(rho.cpu()[0]) - rho_o) <= 1e-12 * rho_o
-    if constraint in ("none", "nonneg", "l1"):
-        assert rel(N(Zb), Zo) <= 10 * tol
-        assert rel(N(D), Do) <= 10 * tol
-    else:   # l0 is discontinuous: compare away from the threshold
-        v = Zo - Do
-        ok = np.abs(N(Zb) - Zo) <= 10 * tol * (1 + np.abs(Zo))
-        assert ok.mean() > 0.97
+    keep = margin.min(axis=1) > 1e-4
+    assert keep.mean() >= 0.95, keep.mean()
+    assert_elementwise(N(Zb)[keep], Zo[keep], rowscale(Zo)[keep], 10 * tol, "Zbar")
+    assert_elementwise(N(D)[keep], Do[keep], rowscale(Do)[keep] + rowscale(Zo)[keep], 10 * tol, "D")
 
 
-def test_admm_w_fused(h, P):
-    X, H, V, W = make_case(100, 30, 6, 8, 1, 25, seed=2)
-    R = 6
+@pytest.mark.parametrize("R", [6, 40, 56])
+def test_admm_w_fused(h, P, R):
+    """F_W fused with the W ADMM (non-negativity), against the oracle: R = 6 and 40 take
+    the tiled kernel (64 subjects per block, 300 subjects: a ragged last tile), R = 56 the
+    warp-per-subject kernel."""
+    X, H, V, W = make_case(300, 30 + R, R, 8, 1, 25, seed=2)
     H, V, W = inputs_for(h, H, V, W)
     Q, st = oracle_state(h, X, H, V, W)
-    sl = O.project_all(X, Q)
+    sl = O.project_all(X, Q if h.precision == "fp64" else
+                       [q.astype(np.float32).astype(np.float64) for q in Q])
+    Tr = N(st["T"])
     H2 = inputs_for(h, np.abs(synth.random_state(X.K, X.J, R, seed=4)[0]))[0]
     Ga, Gb = H2.T @ H2, V.T @ V
     D0 = np.random.default_rng(0).standard_normal((X.K, R)) * 0.01
-    _, Wo, Do, _, _ = O.admm(O.mttkrp_W(sl, H2, V), Ga * Gb, W, D0, 10, O.NONNEG)
+    FWo = np.stack([np.sum(H2 * Tr[k], axis=0) for k in range(X.K)])   # = mttkrp_W on the GPU's T
+    if h.precision == "fp64":
+        np.testing.assert_allclose(FWo, O.mttkrp_W(sl, H2, V), rtol=1e-10, atol=1e-10 * np.abs(FWo).max())
+    Wo, Do, _, margin = _admm_margins(FWo, Ga * Gb, W, D0, 10, O.NONNEG, 0.0)
     Wb, DW = T(h, W), T(h, D0)
     h.admm_w_fused(st, T(h, H2), h.torch.as_tensor(Ga, device=h.device), h.torch.as_tensor(Gb, device=h.device),
                    10, "nonneg", 0.0, Wb, DW)
     h.sync()
-    assert rel(N(Wb), Wo) <= 10 * TOL[h.precision]
-    assert rel(N(DW), Do) <= 10 * TOL[h.precision]
+    tol = TOL[h.precision]
+    keep = margin.min(axis=1) > 1e-4
+    assert keep.all()
+    assert_elementwise(N(Wb)[keep], Wo[keep], rowscale(Wo)[keep], 10 * tol, "Wbar")
+    assert_elementwise(N(DW)[keep], Do[keep], rowscale(Do)[keep] + rowscale(Wo)[keep], 10 * tol, "D_W")
 
 
 def test_gram(h, P):
@@ -338,63 +457,127 @@ def test_warm_start_does_not_drift(h, P):
         assert med < 5e-6 and p99 < 3e-5, (med, p99)
 
 
+def _well_conditioned(X, H, V, W, n, kmax=100.0):
+    """The first n non-empty subjects whose A_k = X_k V S_k H^T has kappa_k <= kmax (the
+    gradient is linear in Q_k, whose FP32 error grows with kappa_k)."""
+    ks = [k for k in range(X.K) if X.subj_ptr[k + 1] > X.subj_ptr[k]
+          and kappa_kept(X.dense(k) @ V @ np.diag(W[k]) @ H.T) <= kmax][:n]
+    assert len(ks) == n, len(ks)
+    return X.subset(ks), W[ks]
+
+
+def _loss_terms(X, Q, H, V, W):
+    """Magnitude sums of the data and model terms of the loss and of each gradient element
+    (the same formulas on absolute values): the scale FP32 rounding errors follow."""
+    aH, aV, aW = np.abs(H), np.abs(V), np.abs(W)
+    Phi = aV.T @ aV
+    mH, mV, mW = np.zeros_like(H), np.zeros_like(V), np.zeros_like(W)
+    UtU = np.zeros((H.shape[0], H.shape[0]))
+    mL = 0.0
+    for k in range(X.K):
+        Xk, Qk, Sk = X.dense(k), np.abs(Q[k]), np.diag(aW[k])
+        Pk = np.abs(Q[k].T @ Q[k])
+        mH += Qk.T @ Xk @ aV @ Sk + Pk @ aH @ Sk @ Phi @ Sk
+        mV += Xk.T @ Qk @ aH @ Sk
+        UtU += Sk @ aH.T @ Pk @ aH @ Sk
+        mW[k] = np.diag(aH.T @ Qk.T @ Xk @ aV) + np.diag(aH.T @ Pk @ aH @ Sk @ Phi)
+        M = Q[k] @ H @ np.diag(W[k]) @ V.T
+        mL += np.sum(Xk * Xk) + 2 * np.abs(np.sum(Xk * M)) + np.sum(M * M)
+    mV += aV @ UtU
+    return mL, 2 * mH, 2 * mV, 2 * mW
+
+
 def test_loss_and_gradient(h, P):
-    X = synth.ehr_custom(50, 30, median=10, lo=2, hi=30, lam=3.0, cmax=10, seed=9)
+    """Loss and the three gradients (hand-written backward kernels) against the oracle's
+    analytic gradient, step-isolated: the kernels are fed the oracle's Q_k (and T_k, Pi_k
+    from it), so the comparison holds them to the per-step bar, element by element:
+    1e-9 (FP64 handle) and 1e-5 (mixed handle) of each element's magnitude sum."""
+    X = synth.with_edge_cases(synth.ehr_custom(150, 30, median=10, lo=2, hi=30, lam=3.0, cmax=10, seed=9))
     R = 4
     H, V, W = inputs_for(h, *synth.random_state(X.K, X.J, R, seed=10))
     Xd = dev_tensor(h, P, X)
-    st = h.procrustes(Xd, R, T(h, H), T(h, V), T(h, W), want_pi=True)
+    Q, st = oracle_state(h, X, H, V, W)
+    Qr = Q if h.precision == "fp64" else [q.astype(np.float32).astype(np.float64) for q in Q]
+    st["Pi"] = T(h, np.stack([q.T @ q for q in Qr]))
     loss, gH, gV, gW = h.loss_grad(Xd, R, st, T(h, H), T(h, V), T(h, W))
     h.sync()
-    Q = [O.procrustes(X.dense(k), V, W[k], H) for k in range(X.K)]
+    # the oracle on the Q_k the kernels were given (rounded to float32 on the mixed handle)
+    Q = Qr
     Lo, gHo, gVo, gWo = O.loss_and_grad(X, Q, H, V, W)
-    if h.precision == "fp64":
-        tol = {"L": 1e-9, "H": 1e-9, "V": 1e-9, "W": 1e-9}
-    else:
-        # Each gradient is the difference of a data term and a model term (e.g. for W:
-        # diag(H^T Q_k^T X_k V) - diag(H^T Q_k^T Q_k H S_k V^T V)); the FP32 path computes
-        # both to the 1e-5 relative step accuracy, so the difference is good to 1e-5 times
-        # (|data term| + |model term|) / |difference|, relative. Q_k itself carries the
-        # Procrustes bound 1e-5 + 4 R u kappa_k (test_procrustes_step), which the worst
-        # conditioned subject passes on to the sums.
-        kmax = max(kappa_kept(X.dense(k) @ V @ np.diag(W[k]) @ H.T) for k in range(X.K))
-        Phi = V.T @ V
-        parts = {"H": [np.zeros_like(H), np.zeros_like(H)], "V": [np.zeros_like(V), np.zeros_like(V)],
-                 "W": [np.zeros_like(W), np.zeros_like(W)]}
-        for k in range(X.K):
-            Xk, Sk = X.dense(k), np.diag(W[k])
-            parts["H"][0] += Q[k].T @ Xk @ V @ Sk
-            parts["H"][1] += Q[k].T @ Q[k] @ H @ Sk @ Phi @ Sk
-            parts["V"][0] += Xk.T @ Q[k] @ H @ Sk
-            parts["V"][1] += V @ Sk @ H.T @ Q[k].T @ Q[k] @ H @ Sk
-            parts["W"][0][k] = np.diag(H.T @ Q[k].T @ Xk @ V)
-            parts["W"][1][k] = np.diag(H.T @ Q[k].T @ Q[k] @ H @ Sk @ Phi)
-        tol = {"L": 1e-4}
-        for g, (a, b), go in (("H", parts["H"], gHo), ("V", parts["V"], gVo), ("W", parts["W"], gWo)):
-            amp = (np.linalg.norm(a) + np.linalg.norm(b)) / max(np.linalg.norm(go / 2.0), 1e-300)
-            tol[g] = max(1e-4, 1e-5 * amp, 4 * R * 2.0 ** -24 * kmax)
-    assert abs(float(loss.cpu()[0]) - Lo) <= tol["L"] * Lo
-    assert rel(N(gH), gHo) <= tol["H"], tol
-    assert rel(N(gV), gVo) <= tol["V"], tol
-    assert rel(N(gW), gWo) <= tol["W"], tol
+    mL, mH, mV, mW = _loss_terms(X, Q, H, V, W)
+    tol = 1e-9 if h.precision == "fp64" else 1e-5
+    assert abs(float(loss.cpu()[0]) - Lo) <= tol * mL, (float(loss.cpu()[0]), Lo, mL)
+    assert_elementwise(N(gH), gHo, mH, tol, "dL/dH")
+    assert_elementwise(N(gV), gVo, mV, tol, "dL/dV")
+    assert_elementwise(N(gW), gWo, mW, tol, "dL/dW")
 
 
-def test_autograd_function(P):
+def test_gradient_matches_fp64_finite_differences(h, P):
+    """The GPU gradient (FP32 on the mixed handle) against FP64 central finite differences
+    of the oracle's loss with Q_k held fixed, h = 1e-6 max(1, |theta|), on up to 200
+    coordinates of each of H, V, W over a 50-subject subset of well-conditioned subjects:
+    relative error (over the sampled coordinates) <= 1e-4 mixed, <= 1e-6 FP64."""
+    X0 = synth.ehr_custom(200, 40, median=10, lo=2, hi=30, lam=3.0, cmax=10, seed=15)
+    R = 6
+    H, V, W0 = inputs_for(h, *synth.random_state(X0.K, X0.J, R, seed=16))
+    X, W = _well_conditioned(X0, H, V, W0, 50)
+    Xd = dev_tensor(h, P, X)
+    st = h.procrustes(Xd, R, T(h, H), T(h, V), T(h, W), want_pi=True)
+    _, gH, gV, gW = h.loss_grad(Xd, R, st, T(h, H), T(h, V), T(h, W))
+    h.sync()
+    Xs = [X.dense(k) for k in range(X.K)]
+    Q = [O.procrustes(Xs[k], V, W[k], H) for k in range(X.K)]
+
+    def loss(Hx, Vx, Wx):
+        return sum(float(np.sum((Xs[k] - Q[k] @ Hx @ np.diag(Wx[k]) @ Vx.T) ** 2)) for k in range(X.K))
+
+    rng = np.random.default_rng(3)
+    tol = 1e-6 if h.precision == "fp64" else 1e-4
+    for name, A, g in (("H", H, N(gH)), ("V", V, N(gV)), ("W", W, N(gW))):
+        flat = rng.permutation(A.size)[:200]
+        fd, got = [], []
+        for f in flat:
+            idx = np.unravel_index(f, A.shape)
+            step = 1e-6 * max(1.0, abs(A[idx]))
+            args = {"H": H, "V": V, "W": W}
+            Ap, Am = A.copy(), A.copy()
+            Ap[idx] += step
+            Am[idx] -= step
+            args[name] = Ap
+            lp = loss(args["H"], args["V"], args["W"])
+            args[name] = Am
+            lm = loss(args["H"], args["V"], args["W"])
+            fd.append((lp - lm) / (2 * step))
+            got.append(g[idx])
+        fd, got = np.array(fd), np.array(got)
+        err = np.linalg.norm(got - fd) / np.linalg.norm(fd)
+        assert err <= tol, (name, err)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_autograd_function(P, precision):
+    """reconstruction_loss (torch.autograd.Function over the backward kernels) on both
+    handles: loss and .grad against the oracle (50 well-conditioned subjects)."""
     import torch
-    hd = P.Copa(0, "fp64")
-    X = synth.ehr_custom(30, 20, median=8, lo=2, hi=20, lam=2.0, cmax=10, seed=12)
+    hd = P.Copa(0, precision)
+    X0 = synth.ehr_custom(120, 20, median=8, lo=2, hi=20, lam=2.0, cmax=10, seed=12)
     R = 3
-    H, V, W = synth.random_state(X.K, X.J, R, seed=13)
-    Xd = P.DeviceTensor.from_host(X, hd.device, "f64")
-    Ht, Vt, Wt = (torch.tensor(a, device=hd.device, requires_grad=True) for a in (H, V, W))
+    H, V, W0 = inputs_for(hd, *synth.random_state(X0.K, X0.J, R, seed=13))
+    X, W = _well_conditioned(X0, H, V, W0, 50)
+    Xd = dev_tensor(hd, P, X)
+    Ht, Vt, Wt = (torch.tensor(a, dtype=hd.dtype, device=hd.device, requires_grad=True) for a in (H, V, W))
     L = P.reconstruction_loss(hd, Xd, Ht, Vt, Wt)
     L.backward()
     Q = [O.procrustes(X.dense(k), V, W[k], H) for k in range(X.K)]
     Lo, gHo, gVo, gWo = O.loss_and_grad(X, Q, H, V, W)
-    assert abs(L.item() - Lo) <= 1e-9 * Lo
-    assert rel(Ht.grad.cpu().numpy(), gHo) <= 1e-9
-    assert rel(Vt.grad.cpu().numpy(), gVo) <= 1e-9
-    assert rel(Wt.grad.cpu().numpy(), gWo) <= 1e-9
+    mL, mH, mV, mW = _loss_terms(X, Q, H, V, W)
+    # the whole path: the GPU's own Procrustes step (FP32 on the mixed handle) feeds the
+    # backward kernels, so the mixed tolerance is that of the FP32 Q_k on kappa <= 100
+    tol = 1e-9 if precision == "fp64" else 1e-4
+    assert abs(L.item() - Lo) <= tol * mL
+    assert_elementwise(Ht.grad.double().cpu().numpy(), gHo, mH, tol, "H.grad")
+    assert_elementwise(Vt.grad.double().cpu().numpy(), gVo, mV, tol, "V.grad")
+    assert_elementwise(Wt.grad.double().cpu().numpy(), gWo, mW, tol, "W.grad")
 
 
 def test_smoothing_projection(h, P):
@@ -489,3 +672,30 @@ def test_host_entry_point_matches_device_fit(P):
     np.testing.assert_allclose(hist_h, hist_d, atol=1e-6)
     # two FP32 runs differ in the order of the F_V atomics; the l1 prox amplifies that
     np.testing.assert_allclose(Vh, Vt.cpu().numpy(), atol=1e-3 * np.abs(Vh).max())
+
+
+def test_tensor_core_wait_timeout_is_reported(P):
+    """The bounded mbarrier waits of the tensor-core V-mode kernel: a test hook makes the
+    first wait of every CTA run out (an mbarrier that nothing arrives at, 2 ms). The kernel
+    must record COPA_ERR_TIMEOUT, wait for the MMAs it issued, free its tensor memory and
+    return; the handle then reports the timeout at the next sync and keeps working."""
+    h = P.Copa(0, "mixed")
+    R = 40
+    X, H, V, W = make_case(60, 90, R, 25, 1, 120)
+    H, V, W = inputs_for(h, H, V, W)
+    Xd = dev_tensor(h, P, X)
+    _, st = oracle_state(h, X, H, V, W)
+    F_ok = h.mttkrp("V", Xd, R, st, H=T(h, H), W=T(h, W))
+    h.sync()
+    h.debug_set(1, 2_000_000)
+    try:
+        h.mttkrp("V", Xd, R, st, H=T(h, H), W=T(h, W))
+        with pytest.raises(P.CopaError) as e:
+            h.sync()
+    finally:
+        h.debug_set(1, 0)
+    assert e.value.code == P.ERR_TIMEOUT
+    assert "did not finish" not in str(e.value), str(e.value)   # the MMAs in flight drained
+    F2 = h.mttkrp("V", Xd, R, st, H=T(h, H), W=T(h, W))
+    h.sync()
+    assert rel(N(F2), N(F_ok)) <= 1e-6

@@ -363,3 +363,23 @@ def test_loss_gradient_matches_finite_differences():
             lm = O.loss_and_grad(X, Q, args["H"], args["V"], args["W"])[0]
             fd = (lp - lm) / (2 * h)
             assert abs(fd - g[idx]) <= 1e-6 * max(1.0, abs(g[idx])), (name, idx, fd, g[idx])
+
+
+def test_fit_on_projected_slices_equals_fit_of_original_data():
+    """The smoothed-data branch of fit_value (x_norm2 given) against a dense reconstruction
+    of the ORIGINAL slices: with U_k = C_k Q_k H (Sec. 3.3.1), FIT = 1 - sum_k
+    ||X_k - C_k Q_k H S_k V^T||^2 / sum_k ||X_k||^2, where Q_k comes from the projected
+    slice X'_k = C_k^T X_k. A dropped or mis-signed add-back term fails here."""
+    X = synth.ehr_custom(K=15, J=20, median=9, lo=2, hi=25, lam=2.0, cmax=5, seed=8, with_days=True)
+    Cs, Xp = O.smooth_project(X)
+    Xo = O.slices_to_tensor(Xp, X.J)
+    R = 3
+    H, V, W = synth.random_state(X.K, X.J, R, seed=2)
+    Q = [O.procrustes(Xo.dense(k), V, W[k], H) for k in range(X.K)]
+    f = O.fit_value(Xo, Q, H, V, W, x_norm2=O.data_norm2(X))
+    res = sum(float(np.sum((X.dense(k) - Cs[k] @ Q[k] @ H @ np.diag(W[k]) @ V.T) ** 2))
+              for k in range(X.K))
+    direct = 1.0 - res / float(np.sum(X.val ** 2))
+    assert abs(f - direct) < 1e-12, (f, direct)
+    # and the projection loses something here, so the add-back term is exercised
+    assert O.data_norm2(Xo) < O.data_norm2(X) * (1 - 1e-3)

@@ -43,7 +43,8 @@ typedef enum {
   COPA_ERR_CUDA = 3,        /* a CUDA runtime call failed */
   COPA_ERR_NUMERIC = 4,     /* a non-positive Cholesky pivot or a non-finite value */
   COPA_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
-  COPA_ERR_UNSUPPORTED = 6  /* the request is valid but not implemented (e.g. R > 128) */
+  COPA_ERR_UNSUPPORTED = 6, /* the request is valid but not implemented (e.g. R > 128) */
+  COPA_ERR_COMM = 7         /* the caller's all-reduce callback reported a failure */
 } copa_status_t;
 
 typedef enum { COPA_PREC_MIXED = 0, COPA_PREC_FP64 = 1 } copa_precision_t;
@@ -226,6 +227,40 @@ copa_status_t copa_fit_value(copa_handle_t handle, const copa_tensor_t* X, int32
 copa_status_t copa_fit(copa_handle_t handle, const copa_tensor_t* X, const copa_options_t* opt,
                        void* H, void* V, void* W, void* DH, void* DV, void* DW,
                        double* fit_history_host, copa_procrustes_out_t* st);
+
+/* Subject sharding (Sec. 3.2: the Procrustes loop runs over subjects independently; every
+ * other step touches the subjects only through sums). A fit over K subjects can be split
+ * into shards of contiguous subjects, one per GPU: a shard holds its subjects' slices X_k
+ * and rows of W and D_W; H, V, D_H, D_V are replicated. Each shard runs copa_fit on its own
+ * subjects; the partial sums F_H, W^T W, F_V, U^T U and ||X||^2 are completed by an
+ * all-reduce (sum over shards) that the caller supplies, after which the H and V updates
+ * see identical inputs on every shard and the FIT is that of the whole tensor.
+ *
+ * copa_partition (host only, no GPU needed): contiguous shards balanced by nonzeros.
+ * subj_ptr_host (K+1) and row_ptr_host (S+1) are X's HOST pointer arrays; bounds_host
+ * (nshards+1) receives the first subject of every shard, bounds[0] = 0, bounds[nshards] = K,
+ * non-decreasing: shard p holds subjects bounds[p] .. bounds[p+1]-1, and bounds[p] is the
+ * subject boundary whose nonzero prefix is closest to p * nnz / nshards. Returns
+ * COPA_ERR_INVALID_ARG for NULL arrays, K < 0 or nshards < 1. */
+copa_status_t copa_partition(const int64_t* subj_ptr_host, const int64_t* row_ptr_host, int64_t K,
+                             int32_t nshards, int64_t* bounds_host);
+
+/* The all-reduce of a sharded fit. Called by copa_fit on the calling thread with `count`
+ * doubles at buf (the device buffer registered below); it must leave in buf[0..count) the
+ * elementwise sum of buf over all shards, either before it returns or enqueued on `stream`
+ * (the handle's cudaStream_t; work the library enqueues after the call waits for it). It
+ * returns 0 on success; anything else fails the fit with COPA_ERR_COMM. Every shard makes
+ * the same sequence of calls with the same counts. */
+typedef int32_t (*copa_allreduce_fn)(double* buf, int64_t count, void* stream, void* user);
+
+/* Registers (fn != NULL) or clears (fn == NULL) the all-reduce of this handle. While one is
+ * registered, copa_fit and copa_fit_host run as one shard of a sharded fit: X holds the
+ * shard's subjects, W and D_W their rows, the FIT history is the whole tensor's. Outer
+ * iterations are then launched eagerly (use_graph is ignored: the callback runs on the
+ * host between steps). buf (device, caller-owned) must hold at least
+ * J * R + 2 * R * R doubles for the fits that follow (checked at copa_fit). */
+copa_status_t copa_set_allreduce(copa_handle_t handle, copa_allreduce_fn fn, void* user, double* buf,
+                                 int64_t capacity);
 
 /* copa_fit on HOST buffers: copies X (arrays given as host pointers in X_host) and the
  * state to the device, runs copa_fit, copies H, V, W, the duals and the FIT history

@@ -22,7 +22,7 @@ if not os.path.exists(LIB_PATH):
     raise ImportError(f"libcopa.so is not built ({LIB_PATH}); run paper_1803_04572_gb300/build.py")
 _lib = ctypes.CDLL(LIB_PATH)
 
-OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NUMERIC, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NUMERIC, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_COMM = range(8)
 PREC = {"mixed": 0, "fp64": 1}
 CONSTRAINT = {"none": 0, "nonneg": 1, "l1": 2, "l0": 3}
 VAL_DTYPE = {"f32": 0, "f64": 1, "bf16": 2}
@@ -32,7 +32,7 @@ EXPORTED = ["copa_create", "copa_destroy", "copa_last_error", "copa_sync", "copa
             "copa_procrustes", "copa_mttkrp", "copa_gram", "copa_admm_step", "copa_admm_w_fused",
             "copa_fit_value", "copa_fit", "copa_fit_host", "copa_smooth_plan",
             "copa_smooth_project", "copa_loss_grad", "copa_procrustes_work", "copa_gram_noalloc",
-            "copa_fit_launches", "copa_debug_set"]
+            "copa_fit_launches", "copa_debug_set", "copa_partition", "copa_set_allreduce"]
 
 
 class CopaError(RuntimeError):
@@ -59,6 +59,8 @@ class OptionsC(Structure):
 
 
 _V = c_void_p
+# int32 (*)(double* buf, int64 count, void* stream, void* user)
+ALLREDUCE_FN = ctypes.CFUNCTYPE(c_int32, c_void_p, c_int64, c_void_p, c_void_p)
 _sig = {
     "copa_create": [POINTER(c_void_p), c_int32, _V, c_int32],
     "copa_destroy": [_V],
@@ -83,6 +85,8 @@ _sig = {
     "copa_gram_noalloc": [_V, c_int32, _V, c_int64, c_int32, _V],
     "copa_fit_launches": [_V, POINTER(c_int64)],
     "copa_debug_set": [_V, c_int32, c_int64],
+    "copa_partition": [_V, _V, c_int64, c_int32, _V],
+    "copa_set_allreduce": [_V, ALLREDUCE_FN, _V, _V, c_int64],
 }
 for _n, _a in _sig.items():
     getattr(_lib, _n).argtypes = _a
@@ -139,6 +143,18 @@ def host_tensor_c(X, val_dtype="f32"):
     tc = TensorC(X.K, X.J, len(arrs[1]) - 1, len(arrs[2]), *(a.ctypes.data for a in arrs),
                  VAL_DTYPE[val_dtype])
     return tc, arrs
+
+
+def partition(subj_ptr, row_ptr, nshards: int) -> np.ndarray:
+    """copa_partition on host arrays: the first subject of each of nshards contiguous
+    shards balanced by nonzeros (nshards + 1 bounds). Needs no GPU."""
+    sp = np.ascontiguousarray(subj_ptr, dtype=np.int64)
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    out = np.zeros(nshards + 1, dtype=np.int64)
+    code = _lib.copa_partition(sp.ctypes.data, rp.ctypes.data, len(sp) - 1, nshards, out.ctypes.data)
+    if code != OK:
+        raise CopaError(code, "copa_partition: bad arguments")
+    return out
 
 
 class Options:
@@ -307,6 +323,31 @@ class Copa:
         """Test hook of copa_debug_set (key 1: force the tensor-core V-mode kernel's first
         wait to run out after `value` ns; 0 switches it off)."""
         self._check(_lib.copa_debug_set(self.h, key, value))
+
+    def set_allreduce(self, reduce_fn, J: int = 0, R: int = 0):
+        """Makes this handle one shard of a sharded fit (copa_set_allreduce), or a whole fit
+        again with reduce_fn=None. reduce_fn(t, stream) must replace the float64 CUDA tensor
+        t by its sum over all shards, on `stream` (this handle's torch stream) or before it
+        returns. The buffer is sized for J x R factors."""
+        if reduce_fn is None:
+            self._check(_lib.copa_set_allreduce(self.h, ALLREDUCE_FN(), None, None, 0))
+            self._red = None
+            return
+        cap = max(1, J * R + 2 * R * R)
+        buf = self.torch.zeros(cap, dtype=self.torch.float64, device=self.device)
+        stream = self.stream
+
+        def cb(ptr, n, _stream, _user):
+            try:
+                reduce_fn(buf[:n], stream)
+                return 0
+            except Exception as e:   # reported as COPA_ERR_COMM by the fit
+                self._red_exc = e
+                return 1
+
+        fn = ALLREDUCE_FN(cb)
+        self._red = (fn, buf)          # keeps the callback and the buffer alive
+        self._check(_lib.copa_set_allreduce(self.h, fn, None, buf.data_ptr(), cap))
 
     def fit_launches(self) -> int:
         """Kernels launched by the last fit() (graph nodes x iterations + set-up), -1 if unknown."""

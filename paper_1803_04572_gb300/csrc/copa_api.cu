@@ -159,6 +159,27 @@ __global__ void k_scan_inplace(int64_t* __restrict__ v, int64_t n) {
   for (int64_t i = a; i < b; ++i) { const int64_t x = v[i]; v[i] = s; s += x; }
 }
 
+// Packs the partial sums of a shard into one FP64 buffer for the all-reduce:
+// out = [a (na reals, widened) | b (nb doubles) | c (nc doubles)], and back.
+template <typename Real>
+__global__ void k_pack_sums(const Real* __restrict__ a, int64_t na, const double* __restrict__ b, int64_t nb,
+                            const double* __restrict__ c, int64_t nc, double* __restrict__ out) {
+  const int64_t n = na + nb + nc;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += gridDim.x * (int64_t)blockDim.x)
+    out[e] = e < na ? (double)a[e] : (e < na + nb ? b[e - na] : c[e - na - nb]);
+}
+
+template <typename Real>
+__global__ void k_unpack_sums(const double* __restrict__ in, Real* __restrict__ a, int64_t na, double* __restrict__ b,
+                              int64_t nb, double* __restrict__ c, int64_t nc) {
+  const int64_t n = na + nb + nc;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += gridDim.x * (int64_t)blockDim.x) {
+    if (e < na) a[e] = (Real)in[e];
+    else if (e < na + nb) b[e - na] = in[e];
+    else c[e - na - nb] = in[e];
+  }
+}
+
 __global__ void k_store_fit(const double* __restrict__ fit, double* __restrict__ hist, int* __restrict__ it,
                             int* __restrict__ epoch) {
   hist[*it] = *fit;
@@ -246,6 +267,24 @@ copa_status_t launch_xnorm2(copa_ctx* h, const TensorView& X, double* out) {
   k_xnorm2<<<blocks, 256, 0, h->stream>>>(X, out);
   h->setup_launches += 1;
   return cuda_check(h, cudaGetLastError(), "k_xnorm2");
+}
+
+// Sum over the shards of a sharded fit (no-op without a registered all-reduce):
+// [a (na reals) | b (nb doubles) | c (nc doubles)] are packed into the caller's buffer,
+// reduced by the caller's callback and unpacked in place.
+template <typename Real>
+copa_status_t shard_allreduce(copa_ctx* h, Real* a, int64_t na, double* b, int64_t nb, double* c, int64_t nc) {
+  if (!h->red_fn) return COPA_OK;
+  const int64_t n = na + nb + nc;
+  if (n > h->red_cap) return fail(h, COPA_ERR_INVALID_ARG, "all-reduce buffer too small");
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 1024));
+  k_pack_sums<Real><<<blocks, 256, 0, h->stream>>>(a, na, b, nb, c, nc, h->red_buf);
+  copa_status_t st;
+  if ((st = cuda_check(h, cudaGetLastError(), "k_pack_sums")) != COPA_OK) return st;
+  const int32_t rc = h->red_fn(h->red_buf, n, reinterpret_cast<void*>(h->stream), h->red_user);
+  if (rc != 0) return fail(h, COPA_ERR_COMM, "all-reduce callback returned " + std::to_string(rc));
+  k_unpack_sums<Real><<<blocks, 256, 0, h->stream>>>(h->red_buf, a, na, b, nb, c, nc);
+  return cuda_check(h, cudaGetLastError(), "k_unpack_sums");
 }
 
 }  // namespace copa
@@ -558,6 +597,8 @@ copa_status_t one_iteration(copa_ctx* h, const TensorView& X, const copa_options
   // within one copa_fit call)
   TRY(launch_gram<Real>(h, W, X.K, R, b.gW));
   if (first) TRY(launch_gram<Real>(h, V, X.J, R, b.gV));
+  // sharded fit: F_H and W^T W summed over the shards (H is then updated identically)
+  TRY(shard_allreduce<Real>(h, b.FH, (int64_t)R * R, b.gW, (int64_t)R * R, nullptr, 0));
   TRY(launch_chol<Real>(h, b.gW, b.gV, R, b.Ginv, b.rho + 0));
   TRY(launch_admm_rows<Real>(h, b.FH, b.Ginv, b.rho + 0, o->n_inner, o->c_H, o->lam_H, H, DH, R, R));
   // W: G = H^T H .* V^T V, F_W fused into the ADMM
@@ -567,6 +608,8 @@ copa_status_t one_iteration(copa_ctx* h, const TensorView& X, const copa_options
   // V: G = H^T H .* W^T W; F_V = sum_k X_k^T Q_k H S_k
   TRY(launch_gram<Real>(h, W, X.K, R, b.gW));
   TRY(launch_mttkrp_v<Real>(h, X, R, b.Q, H, W, b.FV, b.UtU, /*reuse_csc=*/!first));
+  // sharded fit: F_V, W^T W and U^T U summed over the shards (V is then updated identically)
+  TRY(shard_allreduce<Real>(h, b.FV, (int64_t)X.J * R, b.gW, (int64_t)R * R, b.UtU, (int64_t)R * R));
   TRY(launch_chol<Real>(h, b.gH, b.gW, R, b.Ginv, b.rho + 2));
   TRY(launch_admm_rows<Real>(h, b.FV, b.Ginv, b.rho + 2, o->n_inner, o->c_V, o->lam_V, V, DV, X.J, R));
   // FIT of (Q_k, H, W, V) after the iteration
@@ -620,6 +663,11 @@ copa_status_t fit_impl(copa_ctx* h, const copa_tensor_t* Xc, const copa_options_
   int64_t per_iter = -1;
   TRY(cuda_check(h, cudaMemsetAsync(b.it, 0, sizeof(int), h->stream), "memset"));
   TRY(launch_xnorm2(h, X, b.xn2));
+  if (h->red_fn) {
+    if (h->red_cap < (int64_t)X.J * R + 2 * (int64_t)R * R)
+      return fail(h, COPA_ERR_INVALID_ARG, "all-reduce buffer smaller than J * R + 2 R^2 doubles");
+    TRY(shard_allreduce<Real>(h, (Real*)nullptr, 0, b.xn2, 1, nullptr, 0));
+  }
   {
     int64_t wtot = 0;
     TRY(get_warm_offsets(h, X, R, &b.woff, &wtot));
@@ -636,7 +684,7 @@ copa_status_t fit_impl(copa_ctx* h, const copa_tensor_t* Xc, const copa_options_
     h->warm_prec = h->precision;
   }
   if (o->n_outer > 1) {
-    if (o->use_graph) {
+    if (o->use_graph && !h->red_fn) {
       // Capture on a private stream (the caller's may be the legacy default stream, which
       // cannot be captured); capturing enqueues nothing, the replays go to h->stream.
       cudaGraph_t graph = nullptr;
@@ -716,6 +764,42 @@ copa_status_t copa_fit(copa_handle_t h, const copa_tensor_t* X, const copa_optio
                            fit_history_host, st);
   return fit_impl<double>(h, X, opt, (double*)H, (double*)V, (double*)W, (double*)DH, (double*)DV, (double*)DW,
                           fit_history_host, st);
+}
+
+copa_status_t copa_partition(const int64_t* subj_ptr, const int64_t* row_ptr, int64_t K, int32_t nshards,
+                             int64_t* bounds) {
+  if (!subj_ptr || !row_ptr || !bounds || K < 0 || nshards < 1) return COPA_ERR_INVALID_ARG;
+  // nonzero prefix at subject boundary k: row_ptr[subj_ptr[k]] (non-decreasing in k)
+  auto pre = [&](int64_t k) { return row_ptr[subj_ptr[k]]; };
+  const int64_t N = pre(K);
+  bounds[0] = 0;
+  bounds[nshards] = K;
+  int64_t lo = 0;
+  for (int32_t p = 1; p < nshards; ++p) {
+    // target p * N / nshards without overflow
+    const long double target = (long double)N * p / nshards;
+    int64_t a = lo, b = K;   // smallest k in [lo, K] with pre(k) >= target
+    while (a < b) {
+      const int64_t m = a + (b - a) / 2;
+      if ((long double)pre(m) >= target) b = m;
+      else a = m + 1;
+    }
+    int64_t k = a;
+    if (k > lo && target - (long double)pre(k - 1) < (long double)pre(k) - target) k -= 1;
+    bounds[p] = k;
+    lo = k;
+  }
+  return COPA_OK;
+}
+
+copa_status_t copa_set_allreduce(copa_handle_t h, copa_allreduce_fn fn, void* user, double* buf, int64_t capacity) {
+  CHECK_H(h);
+  if (fn && (!buf || capacity < 1)) return fail(h, COPA_ERR_INVALID_ARG, "copa_set_allreduce: NULL buffer");
+  h->red_fn = fn;
+  h->red_user = fn ? user : nullptr;
+  h->red_buf = fn ? buf : nullptr;
+  h->red_cap = fn ? capacity : 0;
+  return COPA_OK;
 }
 
 copa_status_t copa_fit_host(copa_handle_t h, const copa_tensor_t* Xh, const copa_options_t* opt, void* H_host,

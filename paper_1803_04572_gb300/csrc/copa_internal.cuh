@@ -134,6 +134,11 @@ struct copa_ctx {
   const int32_t* csc_key = nullptr;
   int64_t csc_nnz = -1, csc_S = -1;
   int csc_J = 0, csc_prec = -1;
+  // sharded fit: the caller's all-reduce (copa_set_allreduce), NULL when not sharded
+  copa_allreduce_fn red_fn = nullptr;
+  void* red_user = nullptr;
+  double* red_buf = nullptr;
+  int64_t red_cap = 0;
   // test hook: > 0 makes the first mbarrier wait of the tensor-core V-mode kernel run out
   // after this many ns on an mbarrier that nothing arrives at (copa_debug_set)
   int64_t dbg_tc_force_ns = 0;

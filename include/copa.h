@@ -270,24 +270,44 @@ copa_status_t copa_fit_host(copa_handle_t handle, const copa_tensor_t* X_host,
                             void* W_host, void* DH_host, void* DV_host, void* DW_host,
                             double* fit_history_host);
 
-/* Smoothness on U_k (Sec. 3.3.1), set-up step. For every subject, the cubic (degree)
- * B-spline basis with n_basis functions on [t_1, t_{I_k}] (interior knots equally spaced
- * in days, boundary knots repeated degree+1 times; Cox-de Boor recursion) is evaluated
- * at the visit days (double[S], device), M_k = C_k D P^T, and C_k keeps the left
- * singular vectors with sigma^2 > 1e-10 sigma_max^2 (r_k of them; if t_1 = t_{I_k} the
- * basis is the constant function). The projected slices X'_k = C_k^T X_k are r_k x J,
- * stored as CSR over the columns X_k uses.
+/* Smoothness on U_k (Sec. 3.3.1), set-up step. For every subject, the B-spline basis of
+ * the given degree with n_basis functions on [t_1, t_{I_k}] (the first and last visit day;
+ * days (double[S], device) must be non-decreasing within a subject; boundary knots
+ * repeated degree+1 times; Cox-de Boor recursion) is evaluated at the visit days,
+ * M_k = C_k D P^T, and C_k keeps the left singular vectors with sigma^2 > 1e-10
+ * sigma_max^2 (r_k of them; if t_1 = t_{I_k} the basis is the constant function). The
+ * n_basis - degree - 1 interior knots follow knot_rule: COPA_KNOTS_UNIFORM spaces them
+ * equally in days, COPA_KNOTS_QUANTILE puts them at the quantiles j / (n_basis - degree)
+ * of the subject's visit days (linear interpolation between order statistics), i.e.
+ * where the visits are (the paper estimates the knots from the data and builds the
+ * functions on days so that uneven gaps are respected). The projected slices
+ * X'_k = C_k^T X_k are r_k x J, stored as CSR over the columns X_k uses.
  * copa_smooth_plan returns the sizes of X' (S' rows, nnz' nonzeros) and synchronises;
  * copa_smooth_project fills X' (caller-allocated device arrays in Xp: subj_ptr K+1,
  * row_ptr S'+1, col_idx nnz', vals nnz' of type Xp->val_dtype = F32 or F64). The
  * optional C (double[S * n_basis], device, may be NULL) receives C_k padded with zero
  * columns to n_basis. */
+enum { COPA_KNOTS_UNIFORM = 0, COPA_KNOTS_QUANTILE = 1 };
 copa_status_t copa_smooth_plan(copa_handle_t handle, const copa_tensor_t* X,
                                const double* days, int32_t n_basis, int32_t degree,
-                               int64_t* S_out_host, int64_t* nnz_out_host);
+                               int32_t knot_rule, int64_t* S_out_host, int64_t* nnz_out_host);
 copa_status_t copa_smooth_project(copa_handle_t handle, const copa_tensor_t* X,
                                   const double* days, int32_t n_basis, int32_t degree,
-                                  copa_tensor_t* Xp, double* C);
+                                  int32_t knot_rule, copa_tensor_t* Xp, double* C);
+
+/* The output factor of Algorithm 1 (Sec. 3.3.1): U_k = Q_k H, or U_k = C_k Q_k H when the
+ * fit ran on the smoothed projection. Q (S_fit x R, real) holds Q_k of every subject
+ * stacked by rows with offsets subj_ptr_fit (K+1, device: those of the tensor the fit ran
+ * on), as copa_procrustes or copa_fit's state returns it; H is R x R.
+ *   C == NULL: U (S_fit x R, real) gets u_i = q_i H.
+ *   C != NULL: C (S x n_basis double, device) as copa_smooth_project returns it (C_k padded
+ *     with zero columns to n_basis), subj_ptr (K+1, device) the ORIGINAL X's row offsets;
+ *     U (S x R, real) gets, for visit row i of subject k,
+ *     u_i = sum_{q < r_k} C[i, q] (Q_k H)(q, :) with r_k = subj_ptr_fit[k+1] - subj_ptr_fit[k].
+ * With C it uses S_fit x R reals of the handle's workspace. Asynchronous. */
+copa_status_t copa_factor_U(copa_handle_t handle, int64_t K, int32_t R, const int64_t* subj_ptr_fit,
+                            int64_t S_fit, const void* Q, const void* H, const int64_t* subj_ptr,
+                            const double* C, int32_t n_basis, int64_t S, void* U);
 
 /* Reconstruction loss L = sum_k ||X_k - Q_k H S_k V^T||_F^2 (no 1/2) with Q_k fixed (from
  * `st`, which must include Pi and come from copa_procrustes at the same H, V, W) and its

@@ -26,9 +26,10 @@ Readings of the paper used here (the paper is silent or ambiguous at these point
     (a tie goes to 0); non-negativity: max(0, v) (Sec. 3.3.2, 3.3.3).
   * Fixed inner and outer iteration counts; Zbar and D carried across outer iterations.
   * Smoothing basis (Sec. 3.3.1): cubic B-splines by the Cox-de Boor recursion, l = 7
-    functions, 3 interior knots equally spaced in days on [t_1, t_n], boundary knots
-    repeated; C_k = left singular vectors of M_k with sigma^2 > 1e-10 sigma_max^2.
-    If t_1 = t_n the basis is the constant function.
+    functions on [t_1, t_n] (the first and last visit day), boundary knots repeated, 3
+    interior knots either equally spaced in days or at the quantiles of the visit days
+    (the paper leaves their estimation open); C_k = left singular vectors of M_k with
+    sigma^2 > 1e-10 sigma_max^2. If t_1 = t_n the basis is the constant function.
 """
 from __future__ import annotations
 
@@ -304,10 +305,27 @@ def fit(X, H0, V0, W0, opt: Options, n_outer: int, x_norm2: Optional[float] = No
 # Smoothness on U_k through a per-subject spline basis (Sec. 3.3.1)
 # ------------------------------------------------------------------------------------
 
-def spline_knots(t1: float, tn: float, l: int = 7, d: int = 3) -> np.ndarray:
-    """Boundary knots repeated d+1 times, l-d-1 interior knots equally spaced."""
+KNOTS_UNIFORM, KNOTS_QUANTILE = "uniform", "quantile"
+
+
+def spline_knots(t1: float, tn: float, l: int = 7, d: int = 3, days=None,
+                 rule: str = KNOTS_UNIFORM) -> np.ndarray:
+    """Boundary knots t_1 and t_n repeated d+1 times and l-d-1 interior knots, placed
+    (Sec. 3.3.1: the knots' number and positions are estimated; reading used here)
+      uniform:  equally spaced in days on [t_1, t_n];
+      quantile: at the quantiles j/(l-d) of the subject's visit days (linear interpolation
+                between order statistics), so that the knots follow the visits: many where
+                visits cluster, few across long gaps."""
     n_int = l - d - 1
-    interior = t1 + (tn - t1) * np.arange(1, n_int + 1) / (n_int + 1)
+    p = np.arange(1, n_int + 1) / (n_int + 1)
+    if rule == KNOTS_QUANTILE:
+        t = np.sort(np.asarray(days, dtype=np.float64))
+        h = (len(t) - 1) * p
+        j = np.floor(h).astype(int)
+        j1 = np.minimum(j + 1, len(t) - 1)
+        interior = t[j] + (h - j) * (t[j1] - t[j])
+    else:
+        interior = t1 + (tn - t1) * p
     return np.concatenate([np.full(d + 1, t1), interior, np.full(d + 1, tn)])
 
 
@@ -330,14 +348,14 @@ def bspline(i: int, d: int, t: float, knots: np.ndarray) -> float:
     return a + b
 
 
-def subject_basis(days: np.ndarray, l: int = 7, d: int = 3) -> np.ndarray:
+def subject_basis(days: np.ndarray, l: int = 7, d: int = 3, rule: str = KNOTS_UNIFORM) -> np.ndarray:
     """M_k (I_k x l): the l basis functions evaluated at the visit days."""
     if len(days) == 0:
         return np.zeros((0, l))
     t1, tn = float(days[0]), float(days[-1])
     if tn == t1:
         return np.ones((len(days), 1))
-    knots = spline_knots(t1, tn, l, d)
+    knots = spline_knots(t1, tn, l, d, days, rule)
     return np.array([[bspline(i, d, float(t), knots) for i in range(l)] for t in days])
 
 
@@ -350,16 +368,24 @@ def basis_C(M: np.ndarray, tau: float = TAU_BASIS) -> np.ndarray:
     return B[:, keep]
 
 
-def smooth_project(X, l: int = 7, d: int = 3):
+def smooth_project(X, l: int = 7, d: int = 3, rule: str = KNOTS_UNIFORM):
     """X'_k = C_k^T X_k for every subject (Sec. 3.3.1); returns the list of C_k and the
     projected slices as a list of dense r_k x J matrices."""
     Cs, Xp = [], []
     for k in range(X.K):
         rows = X.rows_of(k)
-        C = basis_C(subject_basis(X.days[rows.start:rows.stop], l, d))
+        C = basis_C(subject_basis(X.days[rows.start:rows.stop], l, d, rule))
         Cs.append(C)
         Xp.append(C.T @ X.dense(k))
     return Cs, Xp
+
+
+def factor_U(Q: list, H: np.ndarray, Cs: Optional[list] = None) -> list:
+    """The paper's output U_k = Q_k H, or U_k = C_k Q_k H when the fit ran on the smoothed
+    projection X'_k = C_k^T X_k (Sec. 3.3.1, Algorithm 1 output)."""
+    if Cs is None:
+        return [q @ H for q in Q]
+    return [C @ q @ H for C, q in zip(Cs, Q)]
 
 
 # ------------------------------------------------------------------------------------

@@ -32,7 +32,8 @@ EXPORTED = ["copa_create", "copa_destroy", "copa_last_error", "copa_sync", "copa
             "copa_procrustes", "copa_mttkrp", "copa_gram", "copa_admm_step", "copa_admm_w_fused",
             "copa_fit_value", "copa_fit", "copa_fit_host", "copa_smooth_plan",
             "copa_smooth_project", "copa_loss_grad", "copa_procrustes_work", "copa_gram_noalloc",
-            "copa_fit_launches", "copa_debug_set", "copa_partition", "copa_set_allreduce"]
+            "copa_fit_launches", "copa_debug_set", "copa_partition", "copa_set_allreduce", "copa_factor_U"]
+KNOTS = {"uniform": 0, "quantile": 1}
 
 
 class CopaError(RuntimeError):
@@ -76,9 +77,10 @@ _sig = {
     "copa_fit": [_V, POINTER(TensorC), POINTER(OptionsC), _V, _V, _V, _V, _V, _V, _V,
                  POINTER(ProcOutC)],
     "copa_fit_host": [_V, POINTER(TensorC), POINTER(OptionsC), _V, _V, _V, _V, _V, _V, _V],
-    "copa_smooth_plan": [_V, POINTER(TensorC), _V, c_int32, c_int32, POINTER(c_int64),
+    "copa_smooth_plan": [_V, POINTER(TensorC), _V, c_int32, c_int32, c_int32, POINTER(c_int64),
                          POINTER(c_int64)],
-    "copa_smooth_project": [_V, POINTER(TensorC), _V, c_int32, c_int32, POINTER(TensorC), _V],
+    "copa_smooth_project": [_V, POINTER(TensorC), _V, c_int32, c_int32, c_int32, POINTER(TensorC), _V],
+    "copa_factor_U": [_V, c_int64, c_int32, _V, c_int64, _V, _V, _V, _V, c_int32, c_int64, _V],
     "copa_loss_grad": [_V, POINTER(TensorC), c_int32, POINTER(ProcOutC), _V, _V, _V, _V, _V, _V,
                        _V],
     "copa_procrustes_work": [_V, POINTER(c_double)],
@@ -302,10 +304,14 @@ class Copa:
         del keep
         return hist[:opt.n_outer]
 
-    def smooth(self, X: DeviceTensor, days, n_basis=7, degree=3, out_dtype="f32", want_C=False):
-        """Smoothing set-up of Sec. 3.3.1: returns (X' as DeviceTensor, C or None)."""
+    def smooth(self, X: DeviceTensor, days, n_basis=7, degree=3, out_dtype="f32", want_C=False,
+               knots="quantile"):
+        """Smoothing set-up of Sec. 3.3.1: returns (X' as DeviceTensor, C or None). knots:
+        "quantile" (interior knots at the quantiles of each subject's visit days) or
+        "uniform" (equally spaced in days)."""
         S_out, nnz_out = c_int64(), c_int64()
-        self._call(_lib.copa_smooth_plan, self.h, byref(X.c()), _ptr(days), n_basis, degree, byref(S_out),
+        kr = KNOTS[knots]
+        self._call(_lib.copa_smooth_plan, self.h, byref(X.c()), _ptr(days), n_basis, degree, kr, byref(S_out),
                                           byref(nnz_out))
         torch = self.torch
         tdt = torch.float32 if out_dtype == "f32" else torch.float64
@@ -315,9 +321,19 @@ class Copa:
                           self.empty(max(nnz_out.value, 1), dtype=tdt)[:nnz_out.value], out_dtype)
         C = self.empty(X.S, n_basis, dtype=torch.float64) if want_C else None
         xc = Xp.c()
-        self._call(_lib.copa_smooth_project, self.h, byref(X.c()), _ptr(days), n_basis, degree, byref(xc),
+        self._call(_lib.copa_smooth_project, self.h, byref(X.c()), _ptr(days), n_basis, degree, kr, byref(xc),
                                              _ptr(C))
         return Xp, C
+
+    def factor_U(self, X_fit: DeviceTensor, R, Q, H, X: Optional[DeviceTensor] = None, C=None):
+        """U_k = Q_k H stacked by rows (S_fit x R), or, with the smoothing basis C of the
+        original tensor X, U_k = C_k Q_k H (S x R) (copa_factor_U)."""
+        rows = X.S if C is not None else X_fit.S
+        U = self.empty(max(rows, 1), R)[:rows]
+        self._call(_lib.copa_factor_U, self.h, X_fit.K, R, _ptr(X_fit.subj_ptr), X_fit.S, _ptr(Q), _ptr(H),
+                   _ptr(X.subj_ptr) if X is not None else None, _ptr(C),
+                   int(C.shape[1]) if C is not None else 0, X.S if X is not None else 0, _ptr(U))
+        return U
 
     def debug_set(self, key: int, value: int):
         """Test hook of copa_debug_set (key 1: force the tensor-core V-mode kernel's first

@@ -3,10 +3,15 @@
 // and the projected slice X'_k = C_k^T X_k, run once before the fit. PARAFAC2 on X'
 // gives the same H, S_k, V; U_k = C_k Q_k H afterwards (proof in Sec. 3.3.1).
 //
-// Basis: clamped B-splines of degree d with l functions on [t_1, t_n]: knots t_1 repeated
-// d+1 times, l-d-1 interior knots equally spaced in days, t_n repeated d+1 times. The
-// values of the recursion of Sec. 3.3.1 at a day t are computed with the triangular
-// scheme on the knot span holding t (half-open spans, the last one closed at t_n).
+// Basis: clamped B-splines of degree d with l functions on [t_1, t_n] (the first and last
+// visit day; days are non-decreasing within a subject): knots t_1 repeated d+1 times,
+// l-d-1 interior knots, t_n repeated d+1 times. The interior knots are either equally
+// spaced in days (COPA_KNOTS_UNIFORM) or placed at the quantiles j/(l-d) of the subject's
+// visit days, interpolating linearly between order statistics (COPA_KNOTS_QUANTILE: many
+// knots where visits cluster, few across long gaps; Sec. 3.3.1 leaves the knots to be
+// estimated). The values of the recursion of Sec. 3.3.1 at a day t are computed with the
+// triangular scheme on the last non-empty knot span that starts at or before t (half-open
+// spans; the last non-empty one is closed at t_n).
 // C_k = M_k Z Lambda^{-1/2} from the FP64 Jacobi eigendecomposition M_k^T M_k = Z Lambda Z^T.
 #include "copa_internal.cuh"
 
@@ -20,30 +25,46 @@ constexpr int kMaxJWords = 8192;   // column bitmap of X_k in shared memory: J <
 struct SmoothArgs {
   TensorView X;
   const double* days;
-  int l, d;
+  int l, d, rule;
   int* r_out;          // K: rank r_k
   int64_t* c_out;      // K: distinct columns c_k
   double* Zs;          // K x l x l: Z Lambda^{-1/2} on the kept eigenpairs (columns >= r_k zero)
 };
 
-// knots of the clamped basis (length l + d + 1)
-__device__ inline double knot(int i, int l, int d, double t1, double tn) {
-  if (i <= d) return t1;
-  if (i >= l) return tn;
+// knots of the clamped basis of the subject with visit rows r0 .. r1-1 (l + d + 1 of them)
+__device__ inline void make_knots(const double* days, int64_t r0, int64_t r1, int l, int d, int rule, double* kn) {
+  const double t1 = days[r0], tn = days[r1 - 1];
   const int nint = l - d - 1;
-  return t1 + (tn - t1) * (double)(i - d) / (double)(nint + 1);
+  for (int i = 0; i < l + d + 1; ++i) {
+    if (i <= d) {
+      kn[i] = t1;
+    } else if (i >= l) {
+      kn[i] = tn;
+    } else {
+      const double p = (double)(i - d) / (double)(nint + 1);
+      if (rule == COPA_KNOTS_QUANTILE) {
+        const double hq = (double)(r1 - r0 - 1) * p;
+        const int64_t j = (int64_t)floor(hq);
+        const int64_t j1 = min(j + 1, r1 - r0 - 1);
+        kn[i] = days[r0 + j] + (hq - (double)j) * (days[r0 + j1] - days[r0 + j]);
+      } else {
+        kn[i] = t1 + (tn - t1) * p;
+      }
+    }
+  }
 }
 
-// all l basis values at t (out[0..l-1]); t in [t1, tn], t1 < tn
-__device__ inline void basis_at(double t, int l, int d, double t1, double tn, double* out) {
+// all l basis values at t (out[0..l-1]); t in [kn[0], kn[l+d]], kn[0] < kn[l+d]
+__device__ inline void basis_at(double t, int l, int d, const double* kn, double* out) {
   for (int b = 0; b < l; ++b) out[b] = 0.0;
-  int mu = d;
-  while (mu < l - 1 && knot(mu + 1, l, d, t1, tn) <= t) ++mu;
+  int mu = d;   // the last non-empty span [kn[m], kn[m+1]) with kn[m] <= t
+  for (int m = d; m < l; ++m)
+    if (kn[m] <= t && kn[m] < kn[m + 1]) mu = m;
   double N[kMaxBasis], left[kMaxBasis], right[kMaxBasis];
   N[0] = 1.0;
   for (int j = 1; j <= d; ++j) {
-    left[j] = t - knot(mu + 1 - j, l, d, t1, tn);
-    right[j] = knot(mu + j, l, d, t1, tn) - t;
+    left[j] = t - kn[mu + 1 - j];
+    right[j] = kn[mu + j] - t;
     double saved = 0.0;
     for (int r = 0; r < j; ++r) {
       const double den = right[r + 1] + left[j - r];
@@ -57,7 +78,7 @@ __device__ inline void basis_at(double t, int l, int d, double t1, double tn, do
 }
 
 // Basis row of visit i of a subject (handles the constant-basis special case).
-__device__ inline void basis_row(const double* days, int64_t r0, int64_t r1, int64_t i, int l, int d,
+__device__ inline void basis_row(const double* days, int64_t r0, int64_t r1, int64_t i, int l, int d, int rule,
                                  double* out, int* lb) {
   const double t1 = days[r0], tn = days[r1 - 1];
   if (!(tn > t1)) {
@@ -66,7 +87,9 @@ __device__ inline void basis_row(const double* days, int64_t r0, int64_t r1, int
     return;
   }
   *lb = l;
-  basis_at(days[i], l, d, t1, tn, out);
+  double kn[2 * kMaxBasis + 1];
+  make_knots(days, r0, r1, l, d, rule, kn);
+  basis_at(days[i], l, d, kn, out);
 }
 
 // Cyclic Jacobi on a small symmetric matrix (n <= kMaxBasis), single thread, FP64.
@@ -147,7 +170,7 @@ __global__ void k_smooth_plan(SmoothArgs a) {
         int lb = l;
         for (int e = 0; e < l * l; ++e) B[e] = 0.0;
         for (int64_t i = r0; i < r1; ++i) {
-          basis_row(a.days, r0, r1, i, l, a.d, row, &lb);
+          basis_row(a.days, r0, r1, i, l, a.d, a.rule, row, &lb);
           for (int p = 0; p < lb; ++p)
             for (int q = 0; q < lb; ++q) B[p * lb + q] += row[p] * row[q];
         }
@@ -247,7 +270,7 @@ __global__ void k_smooth_project(SmoothArgs a, const int64_t* __restrict__ row_o
     for (int64_t i = r0; i < r1; ++i) {
       int lb = l;
       if (lane == 0) {
-        basis_row(a.days, r0, r1, i, l, a.d, brow, &lb);
+        basis_row(a.days, r0, r1, i, l, a.d, a.rule, brow, &lb);
         for (int q = 0; q < kMaxBasis; ++q) crow[q] = 0.0;
         for (int q = 0; q < rk; ++q) {
           double acc = 0.0;
@@ -272,10 +295,12 @@ __global__ void k_smooth_project(SmoothArgs a, const int64_t* __restrict__ row_o
   }
 }
 
-copa_status_t run_plan(copa_ctx* h, const copa_tensor_t* X, const double* days, int l, int d, SmoothArgs* a,
-                       int64_t** row_off, int64_t** nz_off, size_t* smem_plan) {
+copa_status_t run_plan(copa_ctx* h, const copa_tensor_t* X, const double* days, int l, int d, int rule,
+                       SmoothArgs* a, int64_t** row_off, int64_t** nz_off, size_t* smem_plan) {
   if (l < 1 || l > kMaxBasis || d < 0 || d >= l)
     return fail(h, COPA_ERR_INVALID_ARG, "smoothing: need 1 <= n_basis <= 16 and 0 <= degree < n_basis");
+  if (rule != COPA_KNOTS_UNIFORM && rule != COPA_KNOTS_QUANTILE)
+    return fail(h, COPA_ERR_INVALID_ARG, "smoothing: unknown knot rule");
   if (!days) return fail(h, COPA_ERR_INVALID_ARG, "smoothing: days is NULL");
   const int nw = (X->J + 31) / 32;
   if (nw > kMaxJWords) return fail(h, COPA_ERR_UNSUPPORTED, "smoothing: J too large");
@@ -288,6 +313,7 @@ copa_status_t run_plan(copa_ctx* h, const copa_tensor_t* X, const double* days, 
   a->days = days;
   a->l = l;
   a->d = d;
+  a->rule = rule;
   a->c_out = reinterpret_cast<int64_t*>(p);
   *row_off = a->c_out + (K + 1);
   *nz_off = *row_off + (K + 1);
@@ -310,7 +336,8 @@ copa_status_t run_plan(copa_ctx* h, const copa_tensor_t* X, const double* days, 
 using namespace copa;
 
 extern "C" copa_status_t copa_smooth_plan(copa_handle_t h, const copa_tensor_t* X, const double* days,
-                                          int32_t n_basis, int32_t degree, int64_t* S_out, int64_t* nnz_out) {
+                                          int32_t n_basis, int32_t degree, int32_t knot_rule, int64_t* S_out,
+                                          int64_t* nnz_out) {
   if (!h) return COPA_ERR_INVALID_ARG;
   copa_status_t st;
   if ((st = cuda_check(h, cudaSetDevice(h->device), "cudaSetDevice")) != COPA_OK) return st;
@@ -319,7 +346,7 @@ extern "C" copa_status_t copa_smooth_plan(copa_handle_t h, const copa_tensor_t* 
   SmoothArgs a;
   int64_t *ro, *no;
   size_t smem;
-  if ((st = run_plan(h, X, days, n_basis, degree, &a, &ro, &no, &smem)) != COPA_OK) return st;
+  if ((st = run_plan(h, X, days, n_basis, degree, knot_rule, &a, &ro, &no, &smem)) != COPA_OK) return st;
   if ((st = cuda_check(h, cudaMemcpyAsync(S_out, ro + X->K, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream),
                        "D2H")) != COPA_OK)
     return st;
@@ -330,7 +357,8 @@ extern "C" copa_status_t copa_smooth_plan(copa_handle_t h, const copa_tensor_t* 
 }
 
 extern "C" copa_status_t copa_smooth_project(copa_handle_t h, const copa_tensor_t* X, const double* days,
-                                             int32_t n_basis, int32_t degree, copa_tensor_t* Xp, double* C) {
+                                             int32_t n_basis, int32_t degree, int32_t knot_rule, copa_tensor_t* Xp,
+                                             double* C) {
   if (!h) return COPA_ERR_INVALID_ARG;
   copa_status_t st;
   if ((st = cuda_check(h, cudaSetDevice(h->device), "cudaSetDevice")) != COPA_OK) return st;
@@ -342,7 +370,7 @@ extern "C" copa_status_t copa_smooth_project(copa_handle_t h, const copa_tensor_
   SmoothArgs a;
   int64_t *ro, *no;
   size_t smem;
-  if ((st = run_plan(h, X, days, n_basis, degree, &a, &ro, &no, &smem)) != COPA_OK) return st;
+  if ((st = run_plan(h, X, days, n_basis, degree, knot_rule, &a, &ro, &no, &smem)) != COPA_OK) return st;
   const int warps = 4;
   const int nw = (X->J + 31) / 32;
   const size_t smem2 = (size_t)warps * (2 * nw + 2) * 4 + (size_t)warps * 2 * kMaxBasis * sizeof(double) + 64;
@@ -364,4 +392,108 @@ extern "C" copa_status_t copa_smooth_project(copa_handle_t h, const copa_tensor_
   }
   if ((st = cuda_check(h, cudaGetLastError(), "k_smooth_project")) != COPA_OK) return st;
   return copa_sync(h);
+}
+
+// =====================================================================================
+// The paper's output factor U_k = Q_k H, or C_k Q_k H after a fit on the smoothed
+// projection (Algorithm 1 output; Sec. 3.3.1).
+// =====================================================================================
+
+namespace copa {
+namespace {
+
+constexpr int kUThreads = 256;
+
+// Y[i, :] = Q[i, :] H for rows, a warp per row, H in shared memory (R x R)
+template <typename Real>
+__global__ void __launch_bounds__(kUThreads) k_times_H(int64_t rows, int R, const Real* __restrict__ Q,
+                                                       const Real* __restrict__ H, Real* __restrict__ Y) {
+  extern __shared__ unsigned char smem_raw[];
+  Real* Hs = reinterpret_cast<Real*>(smem_raw);
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) Hs[e] = H[e];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = wid; i < rows; i += nw) {
+    const Real* q = Q + i * R;
+    for (int c = lane; c < R; c += 32) {
+      Real acc = Real(0);
+      for (int r = 0; r < R; ++r) acc += q[r] * Hs[r * R + c];
+      Y[i * R + c] = acc;
+    }
+  }
+}
+
+// U[i, :] = sum_{q < r_k} C[i, q] Y[sp_fit[k] + q, :] for every original visit row i of
+// subject k (r_k = sp_fit[k+1] - sp_fit[k]), a warp per row
+template <typename Real>
+__global__ void __launch_bounds__(kUThreads) k_basis_combine(int64_t K, int64_t S, int R, int nb,
+                                                             const int64_t* __restrict__ sp,
+                                                             const int64_t* __restrict__ sp_fit,
+                                                             const double* __restrict__ C,
+                                                             const Real* __restrict__ Y, Real* __restrict__ U) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = wid; i < S; i += nw) {
+    int64_t lo = 0, hi = K;   // the subject k with sp[k] <= i < sp[k+1]
+    while (hi - lo > 1) {
+      const int64_t m = (lo + hi) >> 1;
+      if (sp[m] <= i) lo = m;
+      else hi = m;
+    }
+    const int64_t k = lo;
+    const int64_t f0 = sp_fit[k];
+    const int rk = (int)min(sp_fit[k + 1] - f0, (int64_t)nb);
+    for (int c = lane; c < R; c += 32) {
+      double acc = 0.0;
+      for (int q = 0; q < rk; ++q) acc += C[i * nb + q] * (double)Y[(f0 + q) * R + c];
+      U[i * R + c] = (Real)acc;
+    }
+  }
+}
+
+template <typename Real>
+copa_status_t launch_factor_U(copa_ctx* h, int64_t K, int R, const int64_t* sp_fit, int64_t S_fit, const Real* Q,
+                              const Real* H, const int64_t* sp, const double* C, int nb, int64_t S, Real* U) {
+  copa_status_t st;
+  const size_t smem = sizeof(Real) * (size_t)R * R;
+  if ((st = cuda_check(h, cudaFuncSetAttribute(k_times_H<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem), "attr")) != COPA_OK)
+    return st;
+  auto grid = [&](int64_t rows) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((rows + 7) / 8, (int64_t)h->num_sms * 8));
+  };
+  if (!C) {
+    if (S_fit > 0) k_times_H<Real><<<grid(S_fit), kUThreads, smem, h->stream>>>(S_fit, R, Q, H, U);
+    return cuda_check(h, cudaGetLastError(), "k_times_H");
+  }
+  Real* Y = nullptr;
+  if ((st = ws_get(h, SLOT_MISC, sizeof(Real) * (size_t)std::max<int64_t>(S_fit, 1) * R, (void**)&Y)) != COPA_OK)
+    return st;
+  if (S_fit > 0) k_times_H<Real><<<grid(S_fit), kUThreads, smem, h->stream>>>(S_fit, R, Q, H, Y);
+  if (S > 0) k_basis_combine<Real><<<grid(S), kUThreads, 0, h->stream>>>(K, S, R, nb, sp, sp_fit, C, Y, U);
+  return cuda_check(h, cudaGetLastError(), "k_basis_combine");
+}
+
+}  // namespace
+}  // namespace copa
+
+extern "C" copa_status_t copa_factor_U(copa_handle_t h, int64_t K, int32_t R, const int64_t* subj_ptr_fit,
+                                       int64_t S_fit, const void* Q, const void* H, const int64_t* subj_ptr,
+                                       const double* C, int32_t n_basis, int64_t S, void* U) {
+  if (!h) return COPA_ERR_INVALID_ARG;
+  copa_status_t st;
+  if ((st = cuda_check(h, cudaSetDevice(h->device), "cudaSetDevice")) != COPA_OK) return st;
+  if (R < 1 || R > kMaxR) return fail(h, R < 1 ? COPA_ERR_INVALID_ARG : COPA_ERR_UNSUPPORTED, "copa_factor_U: R");
+  if (K < 0 || S_fit < 0 || !Q || !H || !U || !subj_ptr_fit)
+    return fail(h, COPA_ERR_INVALID_ARG, "copa_factor_U: bad arguments");
+  if (C && (!subj_ptr || S < 0 || n_basis < 1 || n_basis > kMaxBasis))
+    return fail(h, COPA_ERR_INVALID_ARG, "copa_factor_U: C needs subj_ptr, S >= 0 and 1 <= n_basis <= 16");
+  if (h->precision == COPA_PREC_MIXED)
+    return launch_factor_U<float>(h, K, R, subj_ptr_fit, S_fit, (const float*)Q, (const float*)H, subj_ptr, C,
+                                  n_basis, S, (float*)U);
+  return launch_factor_U<double>(h, K, R, subj_ptr_fit, S_fit, (const double*)Q, (const double*)H, subj_ptr, C,
+                                 n_basis, S, (double*)U);
 }

@@ -603,13 +603,15 @@ def test_autograd_function(P, precision):
     assert_elementwise(Wt.grad.double().cpu().numpy(), gWo, mW, tol, "W.grad")
 
 
-def test_smoothing_projection(h, P):
+@pytest.mark.parametrize("knots", ["uniform", "quantile"])
+def test_smoothing_projection(h, P, knots):
     X = synth.ehr_custom(90, 40, median=9, lo=1, hi=40, lam=2.0, cmax=8, seed=5, with_days=True)
     X = synth.with_edge_cases(X)
-    Cs, Xp_o = O.smooth_project(X)
+    Cs, Xp_o = O.smooth_project(X, rule=knots)
     Xd = dev_tensor(h, P, X)
     days = h.torch.as_tensor(X.days, dtype=h.torch.float64, device=h.device)
-    Xp, C = h.smooth(Xd, days, 7, 3, out_dtype="f64" if h.precision == "fp64" else "f32", want_C=True)
+    Xp, C = h.smooth(Xd, days, 7, 3, out_dtype="f64" if h.precision == "fp64" else "f32", want_C=True,
+                     knots=knots)
     h.sync()
     sp = Xp.subj_ptr.cpu().numpy()
     rp, col, val = Xp.row_ptr.cpu().numpy(), Xp.col.cpu().numpy(), Xp.vals.double().cpu().numpy()
@@ -631,9 +633,10 @@ def test_smoothing_projection(h, P):
         np.testing.assert_allclose(Ck @ Ck.T, Cs[k] @ Cs[k].T, atol=1e-8)
 
 
-def test_fit_on_smoothed_projection_matches_oracle(h, P):
+@pytest.mark.parametrize("knots", ["uniform", "quantile"])
+def test_fit_on_smoothed_projection_matches_oracle(h, P, knots):
     X = synth.ehr_custom(120, 40, median=10, lo=2, hi=40, lam=3.0, cmax=10, seed=14, with_days=True)
-    Cs, Xp_o = O.smooth_project(X)
+    Cs, Xp_o = O.smooth_project(X, rule=knots)
     Xo = O.slices_to_tensor(Xp_o, X.J)
     R = 4
     init = synth.init_factors(X.K, X.J, R)
@@ -642,11 +645,53 @@ def test_fit_on_smoothed_projection_matches_oracle(h, P):
     st_o, hist_o, _ = O.fit(Xo, *init, opt_o, 5, x_norm2=xn2)
     Xd = dev_tensor(h, P, X)
     days = h.torch.as_tensor(X.days, dtype=h.torch.float64, device=h.device)
-    Xp, _ = h.smooth(Xd, days, 7, 3, out_dtype="f64" if h.precision == "fp64" else "f32")
+    Xp, _ = h.smooth(Xd, days, 7, 3, out_dtype="f64" if h.precision == "fp64" else "f32", knots=knots)
     H, V, W = (T(h, a) for a in init)
     opt = P.Options(R, n_outer=5, n_inner=10, c_V="l1", lam_V=0.5, x_norm2=xn2)
     hist = h.fit(Xp, opt, H, V, W)
     np.testing.assert_allclose(hist, hist_o, atol=1e-8 if h.precision == "fp64" else 1e-4)
+
+
+@pytest.mark.parametrize("smoothed", [False, True])
+def test_output_factor_U(h, P, smoothed):
+    """copa_factor_U, the fit's output U_k = Q_k H (or C_k Q_k H on the smoothed projection,
+    Sec. 3.3.1), step-isolated: the GPU's Procrustes step at a given state, then U, against
+    the oracle's U_k from its own basis and Q_k (U_k does not depend on which orthonormal
+    basis C_k of span(M_k) is used). Per subject within the Procrustes bound
+    1e-5 + 4 R u kappa_k (mixed) or 1e-10 (FP64); band subjects left out."""
+    X = synth.ehr_custom(80, 30, median=9, lo=1, hi=40, lam=2.0, cmax=8, seed=18, with_days=True)
+    R = 4
+    H, V, W = inputs_for(h, *synth.random_state(X.K, X.J, R, seed=19))
+    H = conditioned(H)
+    Xd = dev_tensor(h, P, X)
+    if smoothed:
+        Cs, Xp_o = O.smooth_project(X, rule="quantile")
+        Xo = O.slices_to_tensor(Xp_o, X.J)
+        days = h.torch.as_tensor(X.days, dtype=h.torch.float64, device=h.device)
+        Xf, C = h.smooth(Xd, days, 7, 3, out_dtype="f64" if h.precision == "fp64" else "f32", want_C=True,
+                         knots="quantile")
+    else:
+        Cs, Xo, Xf, C = None, X, Xd, None
+    st = h.procrustes(Xf, R, T(h, H), T(h, V), T(h, W), want_fh=False)
+    U = N(h.factor_U(Xf, R, st["Q"], T(h, H), X=Xd if smoothed else None, C=C))
+    h.sync()
+    Qo = [O.procrustes(Xo.dense(k), V, W[k], H) for k in range(X.K)]
+    Uo = O.factor_U(Qo, H, Cs)
+    skip = band_subjects(Xo, H, V, W, R, h.precision)
+    assert len(skip) <= max(1, X.K // 10)
+    sp = X.subj_ptr if smoothed else Xo.subj_ptr
+    for k in range(X.K):
+        if k in skip:
+            continue
+        Uk = U[sp[k]:sp[k + 1]]
+        kap = kappa_kept(Xo.dense(k) @ V @ np.diag(W[k]) @ H.T)
+        # with smoothing, C_k comes from an FP64 eigendecomposition of M_k^T M_k with the
+        # rank cut at 1e-10 of the largest eigenvalue, which fixes span(C_k) to ~1e-8
+        # (test_smoothing_projection); that floor adds to both handles' bounds
+        floor = 1e-8 if smoothed else 1e-10
+        bound = floor if h.precision == "fp64" else floor + 1e-5 + 4 * R * U32 * kap
+        err = np.linalg.norm(Uk - Uo[k]) / max(np.linalg.norm(Uo[k]), 1e-300)
+        assert err <= bound, (k, err, kap)
 
 
 def test_validation_and_argument_errors(h, P):

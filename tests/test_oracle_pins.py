@@ -383,3 +383,46 @@ def test_fit_on_projected_slices_equals_fit_of_original_data():
     assert abs(f - direct) < 1e-12, (f, direct)
     # and the projection loses something here, so the add-back term is exercised
     assert O.data_norm2(Xo) < O.data_norm2(X) * (1 - 1e-3)
+
+
+def test_quantile_knots_on_an_even_grid_are_the_uniform_knots():
+    """On equally spaced visit days the quantiles of the days are equally spaced, so the
+    quantile rule reduces to the uniform rule exactly; on clustered days it does not."""
+    days = np.arange(0.0, 41.0)
+    np.testing.assert_allclose(O.spline_knots(0.0, 40.0, 7, 3, days, O.KNOTS_QUANTILE),
+                               O.spline_knots(0.0, 40.0, 7, 3), atol=1e-12)
+    np.testing.assert_allclose(O.subject_basis(days, 7, 3, O.KNOTS_QUANTILE), O.subject_basis(days, 7, 3),
+                               atol=1e-14)
+    clustered = np.array([0.0, 1.0, 2.0, 3.0, 4.0, 300.0, 301.0, 302.0, 900.0])
+    kq = O.spline_knots(0.0, 900.0, 7, 3, clustered, O.KNOTS_QUANTILE)
+    np.testing.assert_allclose(kq[4:7], [2.0, 4.0, 301.0])       # order statistics 2, 4, 6 of 9
+    assert np.all(np.diff(kq) >= 0)
+
+
+@pytest.mark.parametrize("rule", ["uniform", "quantile"])
+def test_spline_basis_partition_of_unity_support_and_span(rule):
+    """Clamped B-splines of either knot rule: non-negative, sum to one at every visit day,
+    basis function i vanishes outside [beta_i, beta_{i+d+1}]; and the factor
+    U_k = C_k Q_k H is a combination of the basis functions (U_k = M_k W_k, Sec. 3.3.1)."""
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        n = int(rng.integers(2, 40))
+        gaps = np.where(rng.random(n - 1) < 0.8, rng.integers(1, 4, n - 1), rng.integers(60, 900, n - 1))
+        days = np.concatenate([[0.0], np.cumsum(gaps)]).astype(float)
+        if rng.random() < 0.3:
+            days[1:4] = days[1]          # repeated visit days: repeated quantile knots
+            days = np.sort(days)
+        M = O.subject_basis(days, 7, 3, rule)
+        if days[-1] == days[0]:
+            continue
+        kn = O.spline_knots(days[0], days[-1], 7, 3, days, rule)
+        assert (M >= 0).all()
+        np.testing.assert_allclose(M.sum(axis=1), 1.0, atol=1e-13)
+        for i in range(7):
+            out = (days < kn[i]) | (days > kn[i + 4])
+            assert np.all(M[out, i] == 0.0)
+        C = O.basis_C(M)
+        Q = rng.standard_normal((C.shape[1], 3))
+        U = O.factor_U([Q], rng.random((3, 3)), [C])[0]
+        Wk = np.linalg.lstsq(M, U, rcond=None)[0]
+        np.testing.assert_allclose(M @ Wk, U, atol=1e-10)

@@ -95,6 +95,14 @@ typedef struct {
   double x_norm2;          /* sum_k ||X_k||^2 of the ORIGINAL data when X is a smoothed
                               projection (Sec. 3.3.1); <= 0 means: use ||X||^2 */
   int32_t use_graph;       /* 1: capture one outer iteration in a CUDA graph and replay */
+  /* Convergence tests of Algorithm 1 (the paper names them without defining them; <= 0
+   * keeps the fixed counts above). eps_inner > 0: each factor's ADMM stops after the first
+   * iteration with ||Zbar - Z||_F <= eps ||Zbar||_F and ||Zbar - Zbar_prev||_F <= eps ||Zbar||_F
+   * (norms over the whole factor; n_inner is then the cap). eps_fit > 0: the outer loop
+   * stops after the first iteration t >= 2 with |FIT_t - FIT_{t-1}| <= eps_fit (n_outer is
+   * the cap). copa_fit_stats reports the counts that ran. */
+  double eps_inner;
+  double eps_fit;
 } copa_options_t;
 
 typedef struct copa_ctx* copa_handle_t;
@@ -261,6 +269,13 @@ typedef int32_t (*copa_allreduce_fn)(double* buf, int64_t count, void* stream, v
  * J * R + 2 * R * R doubles for the fits that follow (checked at copa_fit). */
 copa_status_t copa_set_allreduce(copa_handle_t handle, copa_allreduce_fn fn, void* user, double* buf,
                                  int64_t capacity);
+
+/* The iteration counts of the last copa_fit / copa_fit_host call on this handle:
+ * n_outer_run_host (int32[1]) the outer iterations run (< n_outer if eps_fit stopped the
+ * loop; FIT history entries past it are NaN), inner_host (int32[3 * n_outer], may be NULL)
+ * the ADMM iterations of H, W, V (update order) in each outer iteration (n_inner each with
+ * fixed counts, 0 past n_outer_run). */
+copa_status_t copa_fit_stats(copa_handle_t handle, int32_t* n_outer_run_host, int32_t* inner_host);
 
 /* copa_fit on HOST buffers: copies X (arrays given as host pointers in X_host) and the
  * state to the device, runs copa_fit, copies H, V, W, the duals and the FIT history

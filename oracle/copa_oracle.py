@@ -24,7 +24,10 @@ Readings of the paper used here (the paper is silent or ambiguous at these point
     d = d + zbar - z (Eq. 8 update rules, Algorithm 1).
   * l1 prox: sign(v) max(|v| - lambda/rho, 0); l0 prox: v if v^2 > 2 lambda/rho else 0
     (a tie goes to 0); non-negativity: max(0, v) (Sec. 3.3.2, 3.3.3).
-  * Fixed inner and outer iteration counts; Zbar and D carried across outer iterations.
+  * Fixed inner and outer iteration counts by default; optionally the inner ADMM stops on
+    its primal and dual residuals and the outer loop on the change of the FIT (Algorithm 1
+    names both convergence tests without defining them). Zbar and D carried across outer
+    iterations.
   * Smoothing basis (Sec. 3.3.1): cubic B-splines by the Cox-de Boor recursion, l = 7
     functions on [t_1, t_n] (the first and last visit day), boundary knots repeated, 3
     interior knots either equally spaced in days or at the quantiles of the visit days
@@ -163,19 +166,44 @@ def rho_of(G: np.ndarray) -> float:
     return float(np.trace(G)) / G.shape[0]
 
 
-def admm(F, G, Zbar, D, n_inner: int, kind: str, lam: float = 0.0):
-    """Inner ADMM for one factor with G, F, rho and L = chol(G + rho I) fixed.
-    Returns (Z, Zbar, D, rho, L); rows of Z, Zbar, D are the factor's rows."""
+def admm_counted(F, G, Zbar, D, n_inner: int, kind: str, lam: float = 0.0, eps: float = 0.0,
+                 trace: Optional[list] = None):
+    """Inner ADMM for one factor with G, F, rho and L = chol(G + rho I) fixed; at most
+    n_inner iterations. With eps > 0 the loop stops after the first iteration whose primal
+    and dual residuals are both small relative to the factor (the convergence test that
+    Algorithm 1 leaves unspecified; reading used here, norms over the whole factor matrix):
+        ||Zbar - Z||_F <= eps ||Zbar||_F   and   ||Zbar - Zbar_prev||_F <= eps ||Zbar||_F
+    (Zbar after the iteration's update). Both are measured against the factor: the scaled
+    dual D of an unconstrained factor is zero after the first iteration, so a test against
+    ||D|| would never pass there. Returns (Z, Zbar, D, rho, L, iterations). `trace`, if a
+    list, receives max(primal, dual) / ||Zbar|| of every iteration (the quantity compared
+    with eps)."""
     R = G.shape[0]
     rho = rho_of(G)
     L = np.linalg.cholesky(G + rho * np.eye(R))
     Z = np.zeros_like(Zbar)
-    for _ in range(n_inner):
+    it = 0
+    for it in range(1, n_inner + 1):
+        Zbar_prev = Zbar
         rhs = (F + rho * (Zbar + D)).T
         Z = solve_triangular(L.T, solve_triangular(L, rhs, lower=True), lower=False).T
         Zbar = prox(Z - D, kind, lam, rho)
         D = D + Zbar - Z
-    return Z, Zbar, D, rho, L
+        if eps > 0.0:
+            nz2 = np.sum(Zbar ** 2)
+            p2, d2 = np.sum((Zbar - Z) ** 2), np.sum((Zbar - Zbar_prev) ** 2)
+            if trace is not None:
+                trace.append(np.sqrt(max(p2, d2) / nz2) if nz2 > 0 else np.inf)
+            if p2 <= eps * eps * nz2 and d2 <= eps * eps * nz2:
+                break
+    return Z, Zbar, D, rho, L, it
+
+
+def admm(F, G, Zbar, D, n_inner: int, kind: str, lam: float = 0.0):
+    """Inner ADMM for one factor with G, F, rho and L = chol(G + rho I) fixed, exactly
+    n_inner iterations. Returns (Z, Zbar, D, rho, L); rows of Z, Zbar, D are the factor's
+    rows."""
+    return admm_counted(F, G, Zbar, D, n_inner, kind, lam)[:5]
 
 
 def grams(H, V, W):
@@ -231,6 +259,7 @@ class Options:
     lam_W: float = 0.0
     lam_V: float = 1.0
     tau: float = TAU
+    eps_inner: float = 0.0    # > 0: stop each inner ADMM early (admm_counted); n_inner is the cap
 
 
 @dataclasses.dataclass
@@ -266,6 +295,8 @@ class StepRecord:
     G_V: np.ndarray
     rho_V: float
     state: State
+    inner: tuple = (0, 0, 0)    # ADMM iterations run for H, W, V
+    traces: tuple = ((), (), ())  # with eps_inner > 0: the residual ratio of every iteration
 
 
 def outer_iteration(X, st: State, opt: Options) -> StepRecord:
@@ -276,21 +307,31 @@ def outer_iteration(X, st: State, opt: Options) -> StepRecord:
     # H: G = W^T W * V^T V, F = Y_(1)(W (.) V)
     G_H = (st.W.T @ st.W) * (st.V.T @ st.V)
     F_H = mttkrp_H(Ys, st.V, st.W)
-    _, st.H, st.DH, rho_H, _ = admm(F_H, G_H, st.H, st.DH, opt.n_inner, opt.c_H, opt.lam_H)
+    tr = ([], [], [])
+    _, st.H, st.DH, rho_H, _, nH = admm_counted(F_H, G_H, st.H, st.DH, opt.n_inner, opt.c_H, opt.lam_H,
+                                                opt.eps_inner, tr[0])
     # W: G = H^T H * V^T V, F = Y_(3)(V (.) H)
     G_W = (st.H.T @ st.H) * (st.V.T @ st.V)
     F_W = mttkrp_W(Ys, st.H, st.V)
-    _, st.W, st.DW, rho_W, _ = admm(F_W, G_W, st.W, st.DW, opt.n_inner, opt.c_W, opt.lam_W)
+    _, st.W, st.DW, rho_W, _, nW = admm_counted(F_W, G_W, st.W, st.DW, opt.n_inner, opt.c_W, opt.lam_W,
+                                                opt.eps_inner, tr[1])
     # V: G = H^T H * W^T W, F = Y_(2)(W (.) H)
     G_V = (st.H.T @ st.H) * (st.W.T @ st.W)
     F_V = mttkrp_V(Ys, st.H, st.W, X.J)
-    _, st.V, st.DV, rho_V, _ = admm(F_V, G_V, st.V, st.DV, opt.n_inner, opt.c_V, opt.lam_V)
-    return StepRecord(Q, F_H, G_H, rho_H, F_W, G_W, rho_W, F_V, G_V, rho_V, st)
+    _, st.V, st.DV, rho_V, _, nV = admm_counted(F_V, G_V, st.V, st.DV, opt.n_inner, opt.c_V, opt.lam_V,
+                                                opt.eps_inner, tr[2])
+    return StepRecord(Q, F_H, G_H, rho_H, F_W, G_W, rho_W, F_V, G_V, rho_V, st, (nH, nW, nV),
+                      tuple(tuple(t) for t in tr))
 
 
-def fit(X, H0, V0, W0, opt: Options, n_outer: int, x_norm2: Optional[float] = None):
-    """Run n_outer outer iterations from the given init; returns (state, FIT history,
-    last step record). FIT uses the Q_k of each iteration and its final factors."""
+def fit(X, H0, V0, W0, opt: Options, n_outer: int, x_norm2: Optional[float] = None, eps_fit: float = 0.0,
+        records: Optional[list] = None):
+    """Run up to n_outer outer iterations from the given init; returns (state, FIT history,
+    last step record). FIT uses the Q_k of each iteration and its final factors. With
+    eps_fit > 0 the loop stops after the first iteration t >= 2 (1-based) whose FIT differs
+    from the previous one by at most eps_fit (Algorithm 1's outer convergence test, which
+    the paper leaves unspecified; reading used here). `records`, if a list, receives every
+    iteration's StepRecord."""
     st = State.from_init(H0, V0, W0)
     hist = []
     rec = None
@@ -298,6 +339,10 @@ def fit(X, H0, V0, W0, opt: Options, n_outer: int, x_norm2: Optional[float] = No
         rec = outer_iteration(X, st, opt)
         st = rec.state
         hist.append(fit_value(X, rec.Q, st.H, st.V, st.W, x_norm2))
+        if records is not None:
+            records.append(rec)
+        if eps_fit > 0.0 and len(hist) >= 2 and abs(hist[-1] - hist[-2]) <= eps_fit:
+            break
     return st, np.array(hist), rec
 
 

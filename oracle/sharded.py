@@ -51,6 +51,7 @@ def outer_iteration(Xs, st: ShardState, opt: O.Options, allreduce: Callable[[np.
                     x_norm2: Optional[float] = None):
     """One outer iteration of Algorithm 1 on the shard Xs (its subjects only). Returns the
     new shard state and the FIT of the whole tensor after the iteration."""
+    assert opt.eps_inner <= 0.0, "sharded iteration: fixed inner counts only"
     st = st.copy()
     Q = [O.procrustes(Xs.dense(k), st.V, st.W[k], st.H, opt.tau) for k in range(Xs.K)]
     Ys = O.project_all(Xs, Q)

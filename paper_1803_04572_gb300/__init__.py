@@ -32,7 +32,8 @@ EXPORTED = ["copa_create", "copa_destroy", "copa_last_error", "copa_sync", "copa
             "copa_procrustes", "copa_mttkrp", "copa_gram", "copa_admm_step", "copa_admm_w_fused",
             "copa_fit_value", "copa_fit", "copa_fit_host", "copa_smooth_plan",
             "copa_smooth_project", "copa_loss_grad", "copa_procrustes_work", "copa_gram_noalloc",
-            "copa_fit_launches", "copa_debug_set", "copa_partition", "copa_set_allreduce", "copa_factor_U"]
+            "copa_fit_launches", "copa_debug_set", "copa_partition", "copa_set_allreduce", "copa_factor_U",
+            "copa_fit_stats"]
 KNOTS = {"uniform": 0, "quantile": 1}
 
 
@@ -56,7 +57,7 @@ class OptionsC(Structure):
     _fields_ = [("R", c_int32), ("n_outer", c_int32), ("n_inner", c_int32), ("c_H", c_int32),
                 ("c_W", c_int32), ("c_V", c_int32), ("lam_H", c_double), ("lam_W", c_double),
                 ("lam_V", c_double), ("tau", c_double), ("x_norm2", c_double),
-                ("use_graph", c_int32)]
+                ("use_graph", c_int32), ("eps_inner", c_double), ("eps_fit", c_double)]
 
 
 _V = c_void_p
@@ -81,6 +82,7 @@ _sig = {
                          POINTER(c_int64)],
     "copa_smooth_project": [_V, POINTER(TensorC), _V, c_int32, c_int32, c_int32, POINTER(TensorC), _V],
     "copa_factor_U": [_V, c_int64, c_int32, _V, c_int64, _V, _V, _V, _V, c_int32, c_int64, _V],
+    "copa_fit_stats": [_V, POINTER(c_int32), _V],
     "copa_loss_grad": [_V, POINTER(TensorC), c_int32, POINTER(ProcOutC), _V, _V, _V, _V, _V, _V,
                        _V],
     "copa_procrustes_work": [_V, POINTER(c_double)],
@@ -161,14 +163,14 @@ def partition(subj_ptr, row_ptr, nshards: int) -> np.ndarray:
 
 class Options:
     def __init__(self, R, n_outer=10, n_inner=10, c_H="none", c_W="nonneg", c_V="l1", lam_H=0.0,
-                 lam_W=0.0, lam_V=1.0, tau=1e-8, x_norm2=0.0, use_graph=True):
+                 lam_W=0.0, lam_V=1.0, tau=1e-8, x_norm2=0.0, use_graph=True, eps_inner=0.0, eps_fit=0.0):
         self.__dict__.update(locals())
         del self.__dict__["self"]
 
     def c(self) -> OptionsC:
         return OptionsC(self.R, self.n_outer, self.n_inner, CONSTRAINT[self.c_H], CONSTRAINT[self.c_W],
                         CONSTRAINT[self.c_V], self.lam_H, self.lam_W, self.lam_V, self.tau, self.x_norm2,
-                        1 if self.use_graph else 0)
+                        1 if self.use_graph else 0, self.eps_inner, self.eps_fit)
 
 
 class Copa:
@@ -286,7 +288,15 @@ class Copa:
         po = byref(self.proc_c(state)) if state is not None else None
         self._call(_lib.copa_fit, self.h, byref(X.c()), byref(opt.c()), _ptr(H), _ptr(V), _ptr(W), _ptr(DH),
                                   _ptr(DV), _ptr(DW), hist.ctypes.data, po)
-        return hist[:opt.n_outer]
+        return hist[:self.fit_stats(opt.n_outer)[0]]
+
+    def fit_stats(self, n_outer: int):
+        """(outer iterations run, inner ADMM iterations as an n_outer x 3 array (H, W, V))
+        of the last fit (copa_fit_stats)."""
+        n = c_int32()
+        inner = np.zeros(3 * max(n_outer, 1), dtype=np.int32)
+        self._check(_lib.copa_fit_stats(self.h, byref(n), inner.ctypes.data))
+        return n.value, inner[:3 * n_outer].reshape(n_outer, 3)
 
     def fit_host(self, Xh, opt: Options, H, V, W, DH=None, DV=None, DW=None, val_dtype="f32"):
         """copa_fit_host on numpy arrays (H, V, W, duals updated in place)."""
@@ -302,7 +312,7 @@ class Copa:
                                        W.ctypes.data, DH.ctypes.data, DV.ctypes.data, DW.ctypes.data,
                                        hist.ctypes.data)
         del keep
-        return hist[:opt.n_outer]
+        return hist[:self.fit_stats(opt.n_outer)[0]]
 
     def smooth(self, X: DeviceTensor, days, n_basis=7, degree=3, out_dtype="f32", want_C=False,
                knots="quantile"):

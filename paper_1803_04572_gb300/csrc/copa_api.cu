@@ -3,6 +3,7 @@
 // on one stream, optionally captured once into a CUDA graph and replayed.
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <string>
 #include <vector>
 
@@ -180,11 +181,22 @@ __global__ void k_unpack_sums(const double* __restrict__ in, Real* __restrict__ 
   }
 }
 
+// Records the FIT of outer iteration *it, advances the counters and, with eps_fit > 0,
+// raises *stop once the FIT changed by at most eps_fit (from the second iteration on).
 __global__ void k_store_fit(const double* __restrict__ fit, double* __restrict__ hist, int* __restrict__ it,
-                            int* __restrict__ epoch) {
-  hist[*it] = *fit;
-  *it += 1;
+                            int* __restrict__ epoch, int* __restrict__ stop, double eps_fit) {
+  const int i = *it;
+  const double f = *fit;
+  hist[i] = f;
+  if (eps_fit > 0.0 && i >= 1 && fabs(f - hist[i - 1]) <= eps_fit) *stop = 1;
+  *it = i + 1;
   *epoch += 1;
+}
+
+// Sets the condition of the conditional node that wraps one outer iteration in the
+// replayed graph: run the iteration unless the outer loop has converged.
+__global__ void k_cond_set(cudaGraphConditionalHandle ch, const int* __restrict__ stop) {
+  cudaGraphSetConditional(ch, *stop ? 0u : 1u);
 }
 
 }  // namespace
@@ -583,6 +595,11 @@ struct FitBufs {
   double* fitv;
   double* hist;
   int* it;
+  int* stop;      // outer loop converged (eps_fit)
+  int* counts;    // int[3 * n_outer]: inner iterations run for H, W, V
+  int* done;      // inner loop converged (eps_inner), per mode
+  double* acc;    // residual sums of the current inner iteration
+  Real* FW;       // F_W (K x R) for the early-stopping W update
 };
 
 template <typename Real>
@@ -599,22 +616,38 @@ copa_status_t one_iteration(copa_ctx* h, const TensorView& X, const copa_options
   if (first) TRY(launch_gram<Real>(h, V, X.J, R, b.gV));
   // sharded fit: F_H and W^T W summed over the shards (H is then updated identically)
   TRY(shard_allreduce<Real>(h, b.FH, (int64_t)R * R, b.gW, (int64_t)R * R, nullptr, 0));
+  const bool adaptive = o->eps_inner > 0.0;
   TRY(launch_chol<Real>(h, b.gW, b.gV, R, b.Ginv, b.rho + 0));
-  TRY(launch_admm_rows<Real>(h, b.FH, b.Ginv, b.rho + 0, o->n_inner, o->c_H, o->lam_H, H, DH, R, R));
-  // W: G = H^T H .* V^T V, F_W fused into the ADMM
+  if (adaptive)
+    TRY(launch_admm_adaptive<Real>(h, b.FH, b.Ginv, b.rho + 0, o->n_inner, o->c_H, o->lam_H, H, DH, R, R,
+                                   o->eps_inner, b.acc, b.done, b.counts, b.it, 0));
+  else
+    TRY(launch_admm_rows<Real>(h, b.FH, b.Ginv, b.rho + 0, o->n_inner, o->c_H, o->lam_H, H, DH, R, R));
+  // W: G = H^T H .* V^T V, F_W fused into the ADMM (or computed first for early stopping,
+  // whose residual test needs every row after each iteration)
   TRY(launch_gram<Real>(h, H, R, R, b.gH));
   TRY(launch_chol<Real>(h, b.gH, b.gV, R, b.Ginv, b.rho + 1));
-  TRY(launch_admm_w<Real>(h, b.T, H, b.Ginv, b.rho + 1, o->n_inner, o->c_W, o->lam_W, W, DW, X.K, R));
+  if (adaptive) {
+    TRY(launch_mttkrp_w<Real>(h, X.K, R, b.T, H, b.FW));
+    TRY(launch_admm_adaptive<Real>(h, b.FW, b.Ginv, b.rho + 1, o->n_inner, o->c_W, o->lam_W, W, DW, X.K, R,
+                                   o->eps_inner, b.acc, b.done, b.counts, b.it, 1));
+  } else {
+    TRY(launch_admm_w<Real>(h, b.T, H, b.Ginv, b.rho + 1, o->n_inner, o->c_W, o->lam_W, W, DW, X.K, R));
+  }
   // V: G = H^T H .* W^T W; F_V = sum_k X_k^T Q_k H S_k
   TRY(launch_gram<Real>(h, W, X.K, R, b.gW));
   TRY(launch_mttkrp_v<Real>(h, X, R, b.Q, H, W, b.FV, b.UtU, /*reuse_csc=*/!first));
   // sharded fit: F_V, W^T W and U^T U summed over the shards (V is then updated identically)
   TRY(shard_allreduce<Real>(h, b.FV, (int64_t)X.J * R, b.gW, (int64_t)R * R, b.UtU, (int64_t)R * R));
   TRY(launch_chol<Real>(h, b.gH, b.gW, R, b.Ginv, b.rho + 2));
-  TRY(launch_admm_rows<Real>(h, b.FV, b.Ginv, b.rho + 2, o->n_inner, o->c_V, o->lam_V, V, DV, X.J, R));
+  if (adaptive)
+    TRY(launch_admm_adaptive<Real>(h, b.FV, b.Ginv, b.rho + 2, o->n_inner, o->c_V, o->lam_V, V, DV, X.J, R,
+                                   o->eps_inner, b.acc, b.done, b.counts, b.it, 2));
+  else
+    TRY(launch_admm_rows<Real>(h, b.FV, b.Ginv, b.rho + 2, o->n_inner, o->c_V, o->lam_V, V, DV, X.J, R));
   // FIT of (Q_k, H, W, V) after the iteration
   TRY(launch_fit_value<Real>(h, X.J, R, V, b.FV, b.UtU, b.xn2, o->x_norm2, b.fitv, b.gV));
-  k_store_fit<<<1, 1, 0, h->stream>>>(b.fitv, b.hist, b.it, b.epoch);
+  k_store_fit<<<1, 1, 0, h->stream>>>(b.fitv, b.hist, b.it, b.epoch, b.stop, o->eps_fit);
   return cuda_check(h, cudaGetLastError(), "k_store_fit");
 }
 
@@ -638,7 +671,8 @@ copa_status_t fit_impl(copa_ctx* h, const copa_tensor_t* Xc, const copa_options_
   const size_t nsmall = 4 * rnd(sizeof(double) * R * R) + rnd(sizeof(double) * 4) + 2 * rnd(sizeof(double)) +
                         rnd(sizeof(double) * std::max(1, o->n_outer)) + rnd(sizeof(int)) +
                         rnd(sizeof(Real) * R * R) + rnd(sizeof(Real) * (size_t)X.J * R) +
-                        rnd(sizeof(Real) * R * (R + 1));
+                        rnd(sizeof(Real) * R * (R + 1)) + 2 * rnd(sizeof(int)) +
+                        rnd(sizeof(int) * 3 * std::max(1, o->n_outer)) + rnd(sizeof(double) * 4);
   char* p = nullptr;
   TRY(ws_get(h, SLOT_FIT_SMALL, nsmall, (void**)&p));
   auto take = [&](size_t bytes) {
@@ -658,6 +692,15 @@ copa_status_t fit_impl(copa_ctx* h, const copa_tensor_t* Xc, const copa_options_
   b.FH = (Real*)take(sizeof(Real) * R * R);
   b.FV = (Real*)take(sizeof(Real) * (size_t)X.J * R);
   b.Ginv = (Real*)take(sizeof(Real) * R * (R + 1));
+  b.stop = (int*)take(sizeof(int));
+  b.done = (int*)take(sizeof(int));
+  b.counts = (int*)take(sizeof(int) * 3 * std::max(1, o->n_outer));
+  b.acc = (double*)take(sizeof(double) * 4);
+  b.FW = nullptr;
+  if (o->eps_inner > 0.0) TRY(ws_get(h, SLOT_FIT_FW, sizeof(Real) * (size_t)std::max<int64_t>(X.K, 1) * R,
+                                     (void**)&b.FW));
+  TRY(cuda_check(h, cudaMemsetAsync(b.stop, 0, sizeof(int), h->stream), "memset"));
+  TRY(cuda_check(h, cudaMemsetAsync(b.counts, 0, sizeof(int) * 3 * std::max(1, o->n_outer), h->stream), "memset"));
   h->fit_launches = -1;
   h->setup_launches = 0;
   int64_t per_iter = -1;
@@ -686,27 +729,70 @@ copa_status_t fit_impl(copa_ctx* h, const copa_tensor_t* Xc, const copa_options_
   if (o->n_outer > 1) {
     if (o->use_graph && !h->red_fn) {
       // Capture on a private stream (the caller's may be the legacy default stream, which
-      // cannot be captured); capturing enqueues nothing, the replays go to h->stream.
-      cudaGraph_t graph = nullptr;
+      // cannot be captured); capturing enqueues nothing, the replays go to h->stream. With
+      // eps_fit > 0 the iteration is the body of a conditional (if) node whose condition a
+      // small kernel sets from the device's stop flag before it, so that the replays after
+      // convergence do nothing and the host never waits.
+      const bool cond = o->eps_fit > 0.0;
+      cudaGraph_t graph = nullptr, body = nullptr;
       cudaStream_t orig = h->stream, cap = nullptr;
       TRY(cuda_check(h, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "cudaStreamCreate"));
-      h->stream = cap;
-      cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
-      copa_status_t cs = ce == cudaSuccess ? one_iteration<Real>(h, X, o, H, V, W, DH, DV, DW, b, true, false) : COPA_OK;
-      if (ce == cudaSuccess) ce = cudaStreamEndCapture(cap, &graph);
-      h->stream = orig;
-      cudaStreamDestroy(cap);
-      if (cs != COPA_OK) {
-        if (graph) cudaGraphDestroy(graph);
-        return cs;
+      cudaError_t ce = cudaSuccess;
+      if (cond) {
+        cudaGraphConditionalHandle ch = 0;
+        ce = cudaGraphCreate(&graph, 0);
+        if (ce == cudaSuccess) ce = cudaGraphConditionalHandleCreate(&ch, graph, 1, 0);
+        if (ce == cudaSuccess) ce = cudaStreamBeginCaptureToGraph(cap, graph, nullptr, nullptr, 0,
+                                                                  cudaStreamCaptureModeRelaxed);
+        if (ce == cudaSuccess) {
+          k_cond_set<<<1, 1, 0, cap>>>(ch, b.stop);
+          ce = cudaGetLastError();
+          cudaGraph_t g2 = nullptr;
+          const cudaError_t ce2 = cudaStreamEndCapture(cap, &g2);
+          if (ce == cudaSuccess) ce = ce2;
+        }
+        cudaGraphNode_t kn = nullptr;
+        size_t nk = 1;
+        if (ce == cudaSuccess) ce = cudaGraphGetNodes(graph, &kn, &nk);
+        if (ce == cudaSuccess && nk != 1) ce = cudaErrorUnknown;
+        if (ce == cudaSuccess) {
+          cudaGraphNodeParams cp = {};
+          cp.type = cudaGraphNodeTypeConditional;
+          cp.conditional.handle = ch;
+          cp.conditional.type = cudaGraphCondTypeIf;
+          cp.conditional.size = 1;
+          cudaGraphNode_t cn = nullptr;
+          ce = cudaGraphAddNode(&cn, graph, &kn, nullptr, 1, &cp);
+          if (ce == cudaSuccess) body = cp.conditional.phGraph_out[0];
+        }
+        if (ce == cudaSuccess)
+          ce = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+      } else {
+        ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
       }
-      TRY(cuda_check(h, ce, "EndCapture"));
+      copa_status_t cs = COPA_OK;
+      if (ce == cudaSuccess) {
+        h->stream = cap;
+        cs = one_iteration<Real>(h, X, o, H, V, W, DH, DV, DW, b, true, false);
+        h->stream = orig;
+        cudaGraph_t got = nullptr;
+        ce = cudaStreamEndCapture(cap, &got);
+        if (!cond) graph = got;
+        else body = got;
+      }
+      cudaStreamDestroy(cap);
+      if (cs != COPA_OK || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        if (cs != COPA_OK) return cs;
+        TRY(cuda_check(h, ce, "graph capture"));
+      }
       {
+        cudaGraph_t counted = cond ? body : graph;
         size_t nn = 0;
-        if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn > 0) {
+        if (cudaGraphGetNodes(counted, nullptr, &nn) == cudaSuccess && nn > 0) {
           std::vector<cudaGraphNode_t> nodes(nn);
-          if (cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess) {
-            per_iter = 0;
+          if (cudaGraphGetNodes(counted, nodes.data(), &nn) == cudaSuccess) {
+            per_iter = cond ? 1 : 0;
             for (size_t q = 0; q < nn; ++q) {
               cudaGraphNodeType ty;
               if (cudaGraphNodeGetType(nodes[q], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++per_iter;
@@ -725,14 +811,34 @@ copa_status_t fit_impl(copa_ctx* h, const copa_tensor_t* Xc, const copa_options_
       cudaGraphExecDestroy(exec);
       TRY(cuda_check(h, ce, "GraphLaunch"));
     } else {
-      for (int it = 1; it < o->n_outer; ++it) TRY(one_iteration<Real>(h, X, o, H, V, W, DH, DV, DW, b, true, false));
+      for (int it = 1; it < o->n_outer; ++it) {
+        if (o->eps_fit > 0.0) {   // the eager loop asks the device whether to go on
+          int stop = 0;
+          TRY(cuda_check(h, cudaMemcpyAsync(&stop, b.stop, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "D2H"));
+          TRY(cuda_check(h, cudaStreamSynchronize(h->stream), "sync"));
+          if (stop) break;
+        }
+        TRY(one_iteration<Real>(h, X, o, H, V, W, DH, DV, DW, b, true, false));
+      }
     }
   }
   TRY(sync_status(h));
+  int32_t n_run = 0;
+  if (o->n_outer > 0) TRY(cuda_check(h, cudaMemcpy(&n_run, b.it, sizeof(int), cudaMemcpyDeviceToHost), "D2H"));
+  h->last_n_run = n_run;
+  h->last_inner.assign(3 * (size_t)std::max(0, o->n_outer), 0);
+  if (o->eps_inner > 0.0 && o->n_outer > 0) {
+    TRY(cuda_check(h, cudaMemcpy(h->last_inner.data(), b.counts, sizeof(int) * 3 * o->n_outer,
+                                 cudaMemcpyDeviceToHost), "D2H"));
+  } else {
+    for (int i = 0; i < 3 * n_run; ++i) h->last_inner[i] = o->n_inner;
+  }
   if (per_iter >= 0) h->fit_launches = h->setup_launches + per_iter * o->n_outer;
-  if (hist_host && o->n_outer > 0)
-    TRY(cuda_check(h, cudaMemcpy(hist_host, b.hist, sizeof(double) * o->n_outer, cudaMemcpyDeviceToHost),
+  if (hist_host && o->n_outer > 0) {
+    TRY(cuda_check(h, cudaMemcpy(hist_host, b.hist, sizeof(double) * n_run, cudaMemcpyDeviceToHost),
                    "history D2H"));
+    for (int i = n_run; i < o->n_outer; ++i) hist_host[i] = std::numeric_limits<double>::quiet_NaN();
+  }
   return COPA_OK;
 }
 
@@ -744,6 +850,11 @@ copa_status_t check_options(copa_ctx* h, const copa_options_t* o) {
     if (c < COPA_C_NONE || c > COPA_C_L0) return fail(h, COPA_ERR_INVALID_ARG, "unknown constraint");
   if (!(o->lam_H >= 0 && o->lam_W >= 0 && o->lam_V >= 0)) return fail(h, COPA_ERR_INVALID_ARG, "negative lambda");
   if (!(o->tau >= 0.0 && o->tau < 1.0)) return fail(h, COPA_ERR_INVALID_ARG, "tau must be in [0, 1)");
+  if (!(o->eps_inner >= 0.0) || !(o->eps_fit >= 0.0))
+    return fail(h, COPA_ERR_INVALID_ARG, "eps_inner and eps_fit must be >= 0");
+  if (h->red_fn && o->eps_inner > 0.0)
+    return fail(h, COPA_ERR_UNSUPPORTED,
+                "eps_inner in a sharded fit (the W residuals would need an all-reduce per inner iteration)");
   return COPA_OK;
 }
 
@@ -764,6 +875,15 @@ copa_status_t copa_fit(copa_handle_t h, const copa_tensor_t* X, const copa_optio
                            fit_history_host, st);
   return fit_impl<double>(h, X, opt, (double*)H, (double*)V, (double*)W, (double*)DH, (double*)DV, (double*)DW,
                           fit_history_host, st);
+}
+
+copa_status_t copa_fit_stats(copa_handle_t h, int32_t* n_outer_run_host, int32_t* inner_host) {
+  CHECK_H(h);
+  if (!n_outer_run_host) return fail(h, COPA_ERR_INVALID_ARG, "copa_fit_stats: NULL output");
+  *n_outer_run_host = h->last_n_run;
+  if (inner_host)
+    for (size_t i = 0; i < h->last_inner.size(); ++i) inner_host[i] = h->last_inner[i];
+  return COPA_OK;
 }
 
 copa_status_t copa_partition(const int64_t* subj_ptr, const int64_t* row_ptr, int64_t K, int32_t nshards,

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "copa.h"
 
@@ -134,6 +135,9 @@ struct copa_ctx {
   const int32_t* csc_key = nullptr;
   int64_t csc_nnz = -1, csc_S = -1;
   int csc_J = 0, csc_prec = -1;
+  // iteration counts of the last copa_fit (copa_fit_stats)
+  int32_t last_n_run = 0;
+  std::vector<int32_t> last_inner;
   // sharded fit: the caller's all-reduce (copa_set_allreduce), NULL when not sharded
   copa_allreduce_fn red_fn = nullptr;
   void* red_user = nullptr;
@@ -167,6 +171,7 @@ enum Slot {
   SLOT_UVEC = 14,      // u_i = q_i H S_k for every visit row (S x R)
   SLOT_ROWMAP = 15,    // int32 nonzero -> row map and int32 row -> subject map
   SLOT_FV_PART = 16,   // per-CTA partial sums of F_V (row-order path)
+  SLOT_FIT_FW = 17,    // copa_fit: F_W (K x R) for the early-stopping W update
 };
 copa_status_t get_warm_offsets(copa_ctx* h, const TensorView& X, int R, const int64_t** woff,
                                int64_t* total);
@@ -216,6 +221,13 @@ template <typename Real>
 copa_status_t launch_admm_rows(copa_ctx* h, const Real* F, const Real* Ginv,
                                const double* rho_dev, int n_inner, int c, double lam,
                                Real* Zbar, Real* D, int64_t rows, int R);
+// Early-stopping form of the row ADMM: at most max_inner launches of one iteration each,
+// with the residual test of the method after each (see k_admm_check); the number of
+// iterations run goes to counts[*it * 3 + mode].
+template <typename Real>
+copa_status_t launch_admm_adaptive(copa_ctx* h, const Real* F, const Real* Ginv, const double* rho_dev,
+                                   int max_inner, int c, double lam, Real* Zbar, Real* D, int64_t rows, int R,
+                                   double eps, double* acc, int* done, int* counts, const int* it, int mode);
 template <typename Real>
 copa_status_t launch_admm_w(copa_ctx* h, const Real* T, const Real* H, const Real* Ginv,
                             const double* rho_dev, int n_inner, int c, double lam, Real* Wbar,

@@ -682,6 +682,87 @@ __global__ void __launch_bounds__(256) k_admm_rows(const Real* __restrict__ F,
   }
 }
 
+// One inner ADMM iteration over all rows (the early-stopping form of the update): a warp
+// per row does z = (G + rho I)^{-1} (f + rho (zbar + d)), zbar' = prox(z - d),
+// d' = d + zbar' - z, and the grid sums ||zbar' - z||^2, ||zbar'||^2, ||zbar' - zbar||^2 into
+// acc[0..2] (FP64 atomics, one per block). Returns at once once *done is set.
+template <typename Real>
+__global__ void __launch_bounds__(256) k_admm_iter(const Real* __restrict__ F, const Real* __restrict__ Ginv,
+                                                   const double* __restrict__ rho_dev, int c, double lam,
+                                                   Real* __restrict__ Zbar, Real* __restrict__ D, int64_t rows,
+                                                   int R, const int* __restrict__ done, double* __restrict__ acc) {
+  if (*done) return;
+  extern __shared__ unsigned char smem_raw[];
+  Real* Gi = reinterpret_cast<Real*>(smem_raw);          // R x (R+1)
+  Real* bvall = Gi + R * (R + 1);
+  __shared__ double red[3][8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Real* bv = bvall + warp * R;
+  for (int e = threadIdx.x; e < R * (R + 1); e += blockDim.x) Gi[e] = Ginv[e];
+  __syncthreads();
+  const double rho = *rho_dev;
+  const Real rr = (Real)rho, lor = (Real)(lam / rho);
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (gridDim.x * (int64_t)blockDim.x) >> 5;
+  for (int64_t i = wid; i < rows; i += nw) {
+    Real zb[kRegs], d[kRegs];
+#pragma unroll
+    for (int q = 0; q < kRegs; ++q) {
+      const int sc = lane + 32 * q;
+      const Real f = sc < R ? F[i * R + sc] : Real(0);
+      zb[q] = sc < R ? Zbar[i * R + sc] : Real(0);
+      d[q] = sc < R ? D[i * R + sc] : Real(0);
+      if (sc < R) bv[sc] = f + rr * (zb[q] + d[q]);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < kRegs; ++q) {
+      const int sc = lane + 32 * q;
+      if (sc < R) {
+        Real z = Real(0);
+        for (int t = 0; t < R; ++t) z += Gi[sc * (R + 1) + t] * bv[t];
+        const Real nz = prox<Real>(z - d[q], c, lor);
+        const Real dn = d[q] + nz - z;
+        s0 += (double)(nz - z) * (double)(nz - z);
+        s1 += (double)nz * (double)nz;
+        s2 += (double)(nz - zb[q]) * (double)(nz - zb[q]);
+        Zbar[i * R + sc] = nz;
+        D[i * R + sc] = dn;
+      }
+    }
+    __syncwarp();
+  }
+  s0 = warp_sum(s0);
+  s1 = warp_sum(s1);
+  s2 = warp_sum(s2);
+  if (lane == 0) { red[0][warp] = s0; red[1][warp] = s1; red[2][warp] = s2; }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[threadIdx.x][w];
+    atomicAdd(acc + threadIdx.x, t);
+  }
+}
+
+// After an inner iteration: counts it for (outer iteration *it, mode) and sets *done when
+// ||zbar - z||^2 <= eps^2 ||zbar||^2 and ||zbar - zbar_prev||^2 <= eps^2 ||zbar||^2; clears
+// the sums for the next iteration.
+__global__ void k_admm_check(double* __restrict__ acc, double eps2, int* __restrict__ done,
+                             int* __restrict__ counts, const int* __restrict__ it, int mode) {
+  if (*done) return;
+  counts[*it * 3 + mode] += 1;
+  if (acc[0] <= eps2 * acc[1] && acc[2] <= eps2 * acc[1]) *done = 1;
+  acc[0] = acc[1] = acc[2] = 0.0;
+}
+
+__global__ void k_admm_reset(double* __restrict__ acc, int* __restrict__ done, int* __restrict__ counts,
+                             const int* __restrict__ it, int mode) {
+  acc[0] = acc[1] = acc[2] = 0.0;
+  *done = 0;
+  counts[*it * 3 + mode] = 0;
+}
+
 // F_W(k,:) = diag(H^T T_k) fused with the W ADMM (all inner iterations in registers).
 template <typename Real>
 __global__ void __launch_bounds__(256) k_admm_w(const Real* __restrict__ T,
@@ -1248,6 +1329,24 @@ copa_status_t launch_admm_rows(copa_ctx* h, const Real* F, const Real* Ginv, con
 }
 
 template <typename Real>
+copa_status_t launch_admm_adaptive(copa_ctx* h, const Real* F, const Real* Ginv, const double* rho_dev,
+                                   int max_inner, int c, double lam, Real* Zbar, Real* D, int64_t rows, int R,
+                                   double eps, double* acc, int* done, int* counts, const int* it, int mode) {
+  const size_t smem = sizeof(Real) * ((size_t)R * (R + 1) + 8 * (size_t)R);
+  copa_status_t st;
+  if ((st = cuda_check(h, cudaFuncSetAttribute(k_admm_iter<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem), "cudaFuncSetAttribute")) != COPA_OK)
+    return st;
+  k_admm_reset<<<1, 1, 0, h->stream>>>(acc, done, counts, it, mode);
+  const int grid = grid_for(h, rows, 8, 8);
+  for (int t = 0; t < max_inner; ++t) {
+    k_admm_iter<Real><<<grid, 256, smem, h->stream>>>(F, Ginv, rho_dev, c, lam, Zbar, D, rows, R, done, acc);
+    k_admm_check<<<1, 1, 0, h->stream>>>(acc, eps * eps, done, counts, it, mode);
+  }
+  return cuda_check(h, cudaGetLastError(), "k_admm_iter");
+}
+
+template <typename Real>
 copa_status_t launch_admm_w(copa_ctx* h, const Real* T, const Real* H, const Real* Ginv,
                             const double* rho_dev, int n_inner, int c, double lam, Real* Wbar,
                             Real* DW, int64_t K, int R) {
@@ -1306,6 +1405,10 @@ copa_status_t launch_fit_value(copa_ctx* h, int64_t J, int R, const Real* V, con
   template copa_status_t launch_admm_rows<Real>(copa_ctx*, const Real*, const Real*,              \
                                                 const double*, int, int, double, Real*, Real*,    \
                                                 int64_t, int);                                    \
+  template copa_status_t launch_admm_adaptive<Real>(copa_ctx*, const Real*, const Real*,          \
+                                                    const double*, int, int, double, Real*, Real*, \
+                                                    int64_t, int, double, double*, int*, int*,     \
+                                                    const int*, int);                              \
   template copa_status_t launch_admm_w<Real>(copa_ctx*, const Real*, const Real*, const Real*,    \
                                              const double*, int, int, double, Real*, Real*,       \
                                              int64_t, int);                                       \

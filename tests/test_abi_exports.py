@@ -10,7 +10,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "copa.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(copa_[a-z_0-9]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(copa_[A-Za-z_0-9]+)\s*\(", src)))
 
 
 def _build():

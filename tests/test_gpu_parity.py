@@ -767,3 +767,46 @@ def test_tensor_core_wait_timeout_is_reported(P):
     F2 = h.mttkrp("V", Xd, R, st, H=T(h, H), W=T(h, W))
     h.sync()
     assert rel(N(F2), N(F_ok)) <= 1e-6
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_adaptive_stopping_matches_oracle(h, P, use_graph):
+    """Algorithm 1's two convergence tests (residual test of each inner ADMM, FIT change of
+    the outer loop): GPU and oracle run the same numbers of inner iterations per factor and
+    outer iteration and stop the outer loop at the same iteration, with the FIT history at
+    the trajectory tolerances. On the mixed handle a decision whose residual ratio lay
+    within 2% of eps in the oracle may go either way (FP32 residuals of a slightly
+    different trajectory); such (iteration, factor) pairs are left out of the count check
+    and must be rare. With graphs the replays after convergence are skipped by a
+    conditional node; without, the host stops launching."""
+    X = synth.ehr_custom(200, 60, median=10, lo=1, hi=40, lam=3.0, cmax=10, seed=41)
+    R = 6
+    init = synth.init_factors(X.K, X.J, R)
+    eps_in, eps_fit, n_out, n_in = 2e-3, 2e-4, 30, 40
+    opt_o = O.Options(n_inner=n_in, c_H=O.NONE, c_W=O.NONNEG, c_V=O.L1, lam_V=0.5, eps_inner=eps_in)
+    recs = []
+    _, hist_o, _ = O.fit(X, *init, opt_o, n_out, eps_fit=eps_fit, records=recs)
+    assert 2 < len(hist_o) < n_out
+    Xd = dev_tensor(h, P, X)
+    H, V, W = (T(h, a) for a in init)
+    opt = P.Options(R, n_outer=n_out, n_inner=n_in, c_V="l1", lam_V=0.5, eps_inner=eps_in, eps_fit=eps_fit,
+                    use_graph=use_graph)
+    hist = h.fit(Xd, opt, H, V, W)
+    n_run, inner = h.fit_stats(n_out)
+    counts_o = np.array([r.inner for r in recs])
+    assert counts_o.min() >= 1 and (counts_o < n_in).mean() > 0.9
+    fit_margin = np.abs(np.abs(np.diff(hist_o)) - eps_fit) / eps_fit
+    if h.precision == "fp64":
+        assert n_run == len(hist_o)
+        np.testing.assert_array_equal(inner[:n_run], counts_o)
+        np.testing.assert_allclose(hist, hist_o, atol=1e-8)
+    else:
+        robust = np.array([[min(abs(t / eps_in - 1.0) for t in tr) > 0.02 for tr in r.traces] for r in recs])
+        assert robust.mean() > 0.6, robust.mean()
+        m = min(n_run, len(hist_o))
+        ok = robust[:m]
+        np.testing.assert_array_equal(inner[:m][ok], counts_o[:m][ok])
+        if fit_margin.min() > 0.02:
+            assert n_run == len(hist_o)
+        np.testing.assert_allclose(hist[:m], hist_o[:m], atol=1e-4)
+    assert np.all(inner[n_run:] == 0)

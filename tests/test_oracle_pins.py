@@ -426,3 +426,50 @@ def test_spline_basis_partition_of_unity_support_and_span(rule):
         U = O.factor_U([Q], rng.random((3, 3)), [C])[0]
         Wk = np.linalg.lstsq(M, U, rcond=None)[0]
         np.testing.assert_allclose(M @ Wk, U, atol=1e-10)
+
+
+# ---------------------------------------------------------------------------------
+# Adaptive stopping (Algorithm 1's two convergence tests; residual reading)
+# ---------------------------------------------------------------------------------
+
+def test_adaptive_inner_stop_is_the_first_crossing_of_a_fixed_run():
+    """The early-stopped ADMM equals the fixed-count ADMM run for exactly the number of
+    iterations at which the residual test first holds, the residuals being recomputed here
+    from the fixed-count runs of t and t - 1 iterations (a separate route to the same
+    quantities); with eps = 0 it runs the full count."""
+    rng = np.random.default_rng(13)
+    G, F = _sys(rng, 40, 5)
+    Zb0, D0 = rng.standard_normal((6, 5)), rng.standard_normal((6, 5)) * 0.1
+    for kind, lam in ((O.NONE, 0.0), (O.NONNEG, 0.0), (O.L1, 1.5)):
+        eps = 1e-3
+        first = None
+        for t in range(1, 400):
+            Z, Zb, D, _, _ = O.admm(F, G, Zb0, D0, t, kind, lam)
+            Zb_prev = O.admm(F, G, Zb0, D0, t - 1, kind, lam)[1] if t > 1 else Zb0
+            r = np.linalg.norm(Zb - Z) / np.linalg.norm(Zb)
+            s = np.linalg.norm(Zb - Zb_prev) / np.linalg.norm(Zb)
+            if r <= eps and s <= eps:
+                first = t
+                break
+        assert first is not None and 1 < first < 400
+        Za, Zba, Da, _, _, n = O.admm_counted(F, G, Zb0, D0, 400, kind, lam, eps)
+        assert n == first, (kind, n, first)
+        Zf, Zbf, Df, _, _ = O.admm(F, G, Zb0, D0, first, kind, lam)
+        np.testing.assert_array_equal(Zba, Zbf)
+        np.testing.assert_array_equal(Da, Df)
+        assert O.admm_counted(F, G, Zb0, D0, 37, kind, lam, 0.0)[5] == 37
+
+
+def test_adaptive_outer_stop_truncates_the_fixed_history():
+    """The outer loop with eps_fit stops at the first iteration whose FIT moved by at most
+    eps_fit, and its history is the fixed-count history up to there."""
+    X, _ = synth.planted_small(K=30, J=25, R=3, seed=6)
+    init = synth.init_factors(X.K, X.J, 3)
+    opt = O.Options(n_inner=8)
+    _, full, _ = O.fit(X, *init, opt, 25)
+    d = np.abs(np.diff(full))
+    eps = float(np.sort(d)[len(d) // 2])          # crossed somewhere in the middle
+    t = int(np.argmax(d <= eps)) + 2             # 1-based count of iterations run
+    _, part, _ = O.fit(X, *init, opt, 25, eps_fit=eps)
+    assert len(part) == t
+    np.testing.assert_array_equal(part, full[:t])

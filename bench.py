@@ -41,6 +41,8 @@ OTHER_WORKLOADS = {
     "ehr_K20k_J500_R10_smooth": dict(gen="ehr_K20k", R=10, n_inner=10, smooth=True),
     "ehr_K50k_J1000_R20_backward": dict(gen="ehr_K50k", R=20, backward=True),
     "ehr_K100k_J1000": dict(gen="ehr_K100k", R=None, n_inner=10),
+    # hyperparameter sweep: 8 fits (l1 weight on V over a grid) of the smoothed K=20k tensor
+    "ehr_K20k_J500_R10_sweep8": dict(gen="ehr_K20k", R=10, n_inner=10, smooth=True, sweep=8),
 }
 
 
@@ -538,6 +540,55 @@ def config_leg(args):
         h.sync()
         extra["loss"] = float(loss.cpu()[0])
         launches = None
+    elif cfg.get("sweep"):
+        G = cfg["sweep"]
+        lams = list(np.geomspace(0.1, 10.0, G))
+        days = torch.as_tensor(X.days, dtype=torch.float64, device=h.device)
+        Xfit, _ = h.smooth(Xd, days, 7, 3, out_dtype="f64" if args.precision == "fp64" else "f32")
+        xn2 = float(np.sum(np.asarray(X.val, dtype=np.float64) ** 2))
+        opts = [P.Options(R, n_outer=args.steps, n_inner=cfg["n_inner"], c_V="l1", lam_V=float(l), x_norm2=xn2)
+                for l in lams]
+        fresh = lambda: [tuple(torch.as_tensor(a, dtype=h.dtype, device=h.device) for a in (H0, V0, W0))
+                         for _ in lams]
+        h.fit_batch(Xfit, [P.Options(**dict(o.__dict__, n_outer=args.warmup)) for o in opts], fresh())   # warm-up
+        for o in opts:
+            st0 = fresh()[0]
+            h.fit(Xfit, P.Options(**dict(o.__dict__, n_outer=args.warmup)), *st0)
+        h.sync()
+        clk = Clocks(0)
+        clk.start()
+        states = fresh()
+        h.sync()
+        e0.record(h.stream)
+        hists = h.fit_batch(Xfit, opts, states)
+        e1.record(h.stream)
+        h.sync()
+        ms_batch = e0.elapsed_time(e1)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        seq_states = fresh()
+        h.sync()
+        t0.record(h.stream)
+        for o, st0 in zip(opts, seq_states):
+            h.fit(Xfit, o, *st0)
+        t1.record(h.stream)
+        h.sync()
+        ms_seq = t0.elapsed_time(t1)
+        work = G * args.steps
+        line = {"metric": f"sweep fit-iterations/sec ({G} fits, l1 weight grid, K={X.K // 1000}k, J={X.J}, R={R}, "
+                          "smoothed)", "unit": "1/s", "higher_is_better": True, "data": "synthetic",
+                "config": {"workload": args.workload, "K": X.K, "J": X.J, "R": R, "fits": G,
+                           "lam_V": [float(l) for l in lams], "precision": args.precision, "parallelism": "1 GPU"},
+                "value": 1000.0 * work / ms_batch, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms_batch / args.steps, "scaling": "weak", "vs_baseline": None,
+                "dtype": DTYPE[args.precision], "clocks": clk.stop(), "gpu_launches": None,
+                "sequential": {"value": 1000.0 * work / ms_seq, "ms_total": ms_seq,
+                               "note": "the same fits as separate copa_fit calls, one after the other"},
+                "batched_ms_total": ms_batch, "fit_last": [float(x[-1]) for x in hists],
+                "sparsity_V": [float((st[1] == 0).double().mean().item()) for st in states],
+                "generation_s": gen_s}
+        print(json.dumps(line))
+        return
     else:
         Xfit, xn2 = Xd, 0.0
         if cfg.get("smooth"):

@@ -270,6 +270,20 @@ typedef int32_t (*copa_allreduce_fn)(double* buf, int64_t count, void* stream, v
 copa_status_t copa_set_allreduce(copa_handle_t handle, copa_allreduce_fn fn, void* user, double* buf,
                                  int64_t capacity);
 
+/* Hyperparameter sweeps (Sec. 4.2 tunes the regularisation weight and the basis over a
+ * grid): G independent fits of the same X (device, resident once) with their own options,
+ * factors and duals, run concurrently on G streams that the library creates and keeps
+ * with the handle (each with its own workspace). opts[g], H[g], V[g], W[g], DH[g], DV[g],
+ * DW[g] are those of copa_fit for fit g; all fits share R and n_outer (constraints,
+ * lambdas, n_inner, tau, eps_* may differ). fit_history_host (HOST, G x n_outer, may be
+ * NULL) receives each fit's FIT history as a row. The fits start after the work already
+ * queued on the handle's stream, and work queued there after the call sees their results.
+ * Synchronises. 1 <= G <= 64; not for a shard of a sharded fit. copa_fit_stats is not
+ * updated by this call. */
+copa_status_t copa_fit_batch(copa_handle_t handle, const copa_tensor_t* X, int32_t G,
+                             const copa_options_t* opts, void* const* H, void* const* V, void* const* W,
+                             void* const* DH, void* const* DV, void* const* DW, double* fit_history_host);
+
 /* The iteration counts of the last copa_fit / copa_fit_host call on this handle:
  * n_outer_run_host (int32[1]) the outer iterations run (< n_outer if eps_fit stopped the
  * loop; FIT history entries past it are NaN), inner_host (int32[3 * n_outer], may be NULL)

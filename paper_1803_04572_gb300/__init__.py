@@ -33,7 +33,7 @@ EXPORTED = ["copa_create", "copa_destroy", "copa_last_error", "copa_sync", "copa
             "copa_fit_value", "copa_fit", "copa_fit_host", "copa_smooth_plan",
             "copa_smooth_project", "copa_loss_grad", "copa_procrustes_work", "copa_gram_noalloc",
             "copa_fit_launches", "copa_debug_set", "copa_partition", "copa_set_allreduce", "copa_factor_U",
-            "copa_fit_stats"]
+            "copa_fit_stats", "copa_fit_batch"]
 KNOTS = {"uniform": 0, "quantile": 1}
 
 
@@ -83,6 +83,7 @@ _sig = {
     "copa_smooth_project": [_V, POINTER(TensorC), _V, c_int32, c_int32, c_int32, POINTER(TensorC), _V],
     "copa_factor_U": [_V, c_int64, c_int32, _V, c_int64, _V, _V, _V, _V, c_int32, c_int64, _V],
     "copa_fit_stats": [_V, POINTER(c_int32), _V],
+    "copa_fit_batch": [_V, POINTER(TensorC), c_int32, _V, _V, _V, _V, _V, _V, _V, _V],
     "copa_loss_grad": [_V, POINTER(TensorC), c_int32, POINTER(ProcOutC), _V, _V, _V, _V, _V, _V,
                        _V],
     "copa_procrustes_work": [_V, POINTER(c_double)],
@@ -289,6 +290,25 @@ class Copa:
         self._call(_lib.copa_fit, self.h, byref(X.c()), byref(opt.c()), _ptr(H), _ptr(V), _ptr(W), _ptr(DH),
                                   _ptr(DV), _ptr(DW), hist.ctypes.data, po)
         return hist[:self.fit_stats(opt.n_outer)[0]]
+
+    def fit_batch(self, X: DeviceTensor, opts, states):
+        """copa_fit_batch: len(opts) fits of X run concurrently; states is a list of
+        (H, V, W) or (H, V, W, DH, DV, DW) tensors per fit, updated in place. Returns the FIT
+        histories (G x n_outer numpy array, NaN past a fit's last iteration)."""
+        G = len(opts)
+        if len(states) != G:
+            raise ValueError("one state per option set")
+        full = []
+        for stt in states:
+            H, V, W = stt[:3]
+            D = stt[3:] if len(stt) == 6 else tuple(self.torch.zeros_like(a) for a in (H, V, W))
+            full.append((H, V, W) + tuple(D))
+        arr = (OptionsC * G)(*[o.c() for o in opts])
+        ptrs = [(c_void_p * G)(*[_ptr(st[i]) for st in full]) for i in range(6)]
+        n_outer = opts[0].n_outer
+        hist = np.zeros((G, max(1, n_outer)), dtype=np.float64)
+        self._call(_lib.copa_fit_batch, self.h, byref(X.c()), G, arr, *ptrs, hist.ctypes.data)
+        return hist[:, :n_outer]
 
     def fit_stats(self, n_outer: int):
         """(outer iterations run, inner ADMM iterations as an n_outer x 3 array (H, W, V))

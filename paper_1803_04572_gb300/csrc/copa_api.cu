@@ -374,17 +374,26 @@ copa_status_t copa_create(copa_handle_t* handle, int device, void* stream, int32
   return COPA_OK;
 }
 
-copa_status_t copa_destroy(copa_handle_t h) {
-  CHECK_H(h);
-  cudaSetDevice(h->device);
+static void release_ctx(copa_ctx* h, bool own_stream) {
   cudaStreamSynchronize(h->stream);
+  for (copa_ctx* c : h->children) release_ctx(c, true);
+  h->children.clear();
+  if (h->batch_ev) cudaEventDestroy(h->batch_ev);
+  if (h->pend_exec) cudaGraphExecDestroy(h->pend_exec);
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
   for (int i = 0; i < 20; ++i)
     if (h->slot_ptr[i]) cudaFree(h->slot_ptr[i]);
   for (int i = 0; i < 16; ++i)
     if (h->host_slot_ptr[i]) cudaFree(h->host_slot_ptr[i]);
   cudaFree(h->d_status);
+  if (own_stream) cudaStreamDestroy(h->stream);
   delete h;
+}
+
+copa_status_t copa_destroy(copa_handle_t h) {
+  CHECK_H(h);
+  cudaSetDevice(h->device);
+  release_ctx(h, false);
   return COPA_OK;
 }
 
@@ -651,9 +660,42 @@ copa_status_t one_iteration(copa_ctx* h, const TensorView& X, const copa_options
   return cuda_check(h, cudaGetLastError(), "k_store_fit");
 }
 
+// Waits for the fit enqueued last on this handle and collects its results: the device
+// status, the iteration counts (copa_fit_stats) and the FIT history.
+copa_status_t finish_fit(copa_ctx* h, double* hist_host) {
+  const copa_status_t sst = sync_status(h);
+  if (h->pend_exec) {
+    cudaGraphExecDestroy(h->pend_exec);
+    h->pend_exec = nullptr;
+  }
+  TRY(sst);
+  const int n_outer = h->pend_n_outer;
+  int32_t n_run = 0;
+  if (n_outer > 0) TRY(cuda_check(h, cudaMemcpy(&n_run, h->pend_it, sizeof(int), cudaMemcpyDeviceToHost), "D2H"));
+  h->last_n_run = n_run;
+  h->last_inner.assign(3 * (size_t)std::max(0, n_outer), 0);
+  if (h->pend_adaptive && n_outer > 0) {
+    TRY(cuda_check(h, cudaMemcpy(h->last_inner.data(), h->pend_counts, sizeof(int) * 3 * n_outer,
+                                 cudaMemcpyDeviceToHost), "D2H"));
+  } else {
+    for (int i = 0; i < 3 * n_run; ++i) h->last_inner[i] = h->pend_n_inner;
+  }
+  if (h->pend_per_iter >= 0) h->fit_launches = h->setup_launches + h->pend_per_iter * n_outer;
+  if (hist_host && n_outer > 0) {
+    TRY(cuda_check(h, cudaMemcpy(hist_host, h->pend_hist, sizeof(double) * n_run, cudaMemcpyDeviceToHost),
+                   "history D2H"));
+    for (int i = n_run; i < n_outer; ++i) hist_host[i] = std::numeric_limits<double>::quiet_NaN();
+  }
+  return COPA_OK;
+}
+
+// Enqueues a whole fit on h->stream (set-up, the first iteration eagerly, the others as
+// graph replays) and, if finish, waits for it (finish_fit). Without finish the results
+// are collected by a later finish_fit on the same handle.
 template <typename Real>
 copa_status_t fit_impl(copa_ctx* h, const copa_tensor_t* Xc, const copa_options_t* o, Real* H, Real* V,
-                       Real* W, Real* DH, Real* DV, Real* DW, double* hist_host, copa_procrustes_out_t* st) {
+                       Real* W, Real* DH, Real* DV, Real* DW, double* hist_host, copa_procrustes_out_t* st,
+                       bool finish = true) {
   const TensorView X = view_of(Xc);
   const int R = o->R;
   const size_t KRR = (size_t)X.K * R * R;
@@ -808,7 +850,9 @@ copa_status_t fit_impl(copa_ctx* h, const copa_tensor_t* Xc, const copa_options_
         ce = cudaGraphLaunch(exec, h->stream);
         if (ce != cudaSuccess) break;
       }
-      cudaGraphExecDestroy(exec);
+      // destroyed by finish_fit once the stream has drained (the launches stay in flight
+      // meanwhile, so that fits on other streams can be enqueued behind them)
+      h->pend_exec = exec;
       TRY(cuda_check(h, ce, "GraphLaunch"));
     } else {
       for (int it = 1; it < o->n_outer; ++it) {
@@ -822,24 +866,15 @@ copa_status_t fit_impl(copa_ctx* h, const copa_tensor_t* Xc, const copa_options_
       }
     }
   }
-  TRY(sync_status(h));
-  int32_t n_run = 0;
-  if (o->n_outer > 0) TRY(cuda_check(h, cudaMemcpy(&n_run, b.it, sizeof(int), cudaMemcpyDeviceToHost), "D2H"));
-  h->last_n_run = n_run;
-  h->last_inner.assign(3 * (size_t)std::max(0, o->n_outer), 0);
-  if (o->eps_inner > 0.0 && o->n_outer > 0) {
-    TRY(cuda_check(h, cudaMemcpy(h->last_inner.data(), b.counts, sizeof(int) * 3 * o->n_outer,
-                                 cudaMemcpyDeviceToHost), "D2H"));
-  } else {
-    for (int i = 0; i < 3 * n_run; ++i) h->last_inner[i] = o->n_inner;
-  }
-  if (per_iter >= 0) h->fit_launches = h->setup_launches + per_iter * o->n_outer;
-  if (hist_host && o->n_outer > 0) {
-    TRY(cuda_check(h, cudaMemcpy(hist_host, b.hist, sizeof(double) * n_run, cudaMemcpyDeviceToHost),
-                   "history D2H"));
-    for (int i = n_run; i < o->n_outer; ++i) hist_host[i] = std::numeric_limits<double>::quiet_NaN();
-  }
-  return COPA_OK;
+  h->pend_it = b.it;
+  h->pend_hist = b.hist;
+  h->pend_counts = b.counts;
+  h->pend_n_outer = o->n_outer;
+  h->pend_n_inner = o->n_inner;
+  h->pend_adaptive = o->eps_inner > 0.0;
+  h->pend_per_iter = per_iter;
+  if (!finish) return COPA_OK;
+  return finish_fit(h, hist_host);
 }
 
 copa_status_t check_options(copa_ctx* h, const copa_options_t* o) {
@@ -875,6 +910,74 @@ copa_status_t copa_fit(copa_handle_t h, const copa_tensor_t* X, const copa_optio
                            fit_history_host, st);
   return fit_impl<double>(h, X, opt, (double*)H, (double*)V, (double*)W, (double*)DH, (double*)DV, (double*)DW,
                           fit_history_host, st);
+}
+
+copa_status_t copa_fit_batch(copa_handle_t h, const copa_tensor_t* X, int32_t G, const copa_options_t* opts,
+                             void* const* H, void* const* V, void* const* W, void* const* DH, void* const* DV,
+                             void* const* DW, double* fit_history_host) {
+  CHECK_H(h);
+  TRY(set_dev(h));
+  TRY(check_tensor_args(h, X));
+  if (G < 1 || G > 64 || !opts || !H || !V || !W || !DH || !DV || !DW)
+    return fail(h, COPA_ERR_INVALID_ARG, "copa_fit_batch: need 1 <= G <= 64 and non-NULL arrays");
+  if (h->red_fn) return fail(h, COPA_ERR_UNSUPPORTED, "copa_fit_batch: not for a shard of a sharded fit");
+  for (int g = 0; g < G; ++g) {
+    TRY(check_options(h, &opts[g]));
+    if (opts[g].R != opts[0].R || opts[g].n_outer != opts[0].n_outer)
+      return fail(h, COPA_ERR_INVALID_ARG, "copa_fit_batch: every fit must have the same R and n_outer");
+    if (!H[g] || !V[g] || !W[g] || !DH[g] || !DV[g] || !DW[g])
+      return fail(h, COPA_ERR_INVALID_ARG, "copa_fit_batch: NULL factor or dual");
+  }
+  while ((int)h->children.size() < G) {
+    copa_ctx* c = new copa_ctx();
+    c->device = h->device;
+    c->precision = h->precision;
+    c->num_sms = h->num_sms;
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMalloc(&c->d_status, sizeof(int) * 4) != cudaSuccess ||
+        cudaMemset(c->d_status, 0, sizeof(int) * 4) != cudaSuccess) {
+      cudaGetLastError();
+      if (c->stream) cudaStreamDestroy(c->stream);
+      if (c->d_status) cudaFree(c->d_status);
+      delete c;
+      return fail(h, COPA_ERR_CUDA, "copa_fit_batch: could not create a stream for a fit");
+    }
+    h->children.push_back(c);
+  }
+  if (!h->batch_ev) TRY(cuda_check(h, cudaEventCreateWithFlags(&h->batch_ev, cudaEventDisableTiming), "event"));
+  for (int g = 0; g < G; ++g) h->children[g]->num_sms = h->num_sms;
+  // every fit starts after the work already queued on the handle's stream
+  TRY(cuda_check(h, cudaEventRecord(h->batch_ev, h->stream), "cudaEventRecord"));
+  for (int g = 0; g < G; ++g)
+    TRY(cuda_check(h, cudaStreamWaitEvent(h->children[g]->stream, h->batch_ev, 0), "cudaStreamWaitEvent"));
+  const bool mixed = h->precision == COPA_PREC_MIXED;
+  copa_status_t first = COPA_OK;
+  int enq = 0;
+  for (; enq < G; ++enq) {
+    copa_ctx* c = h->children[enq];
+    const copa_status_t st =
+        mixed ? fit_impl<float>(c, X, &opts[enq], (float*)H[enq], (float*)V[enq], (float*)W[enq], (float*)DH[enq],
+                                (float*)DV[enq], (float*)DW[enq], nullptr, nullptr, false)
+              : fit_impl<double>(c, X, &opts[enq], (double*)H[enq], (double*)V[enq], (double*)W[enq],
+                                 (double*)DH[enq], (double*)DV[enq], (double*)DW[enq], nullptr, nullptr, false);
+    if (st != COPA_OK) {
+      first = fail(h, st, "copa_fit_batch: fit " + std::to_string(enq) + ": " + c->err);
+      break;
+    }
+  }
+  // collect every enqueued fit (also after an error, so that nothing is left running)
+  for (int g = 0; g < enq; ++g) {
+    copa_ctx* c = h->children[g];
+    const copa_status_t st =
+        finish_fit(c, fit_history_host ? fit_history_host + (size_t)g * std::max(0, opts[0].n_outer) : nullptr);
+    if (st != COPA_OK && first == COPA_OK) first = fail(h, st, "copa_fit_batch: fit " + std::to_string(g) + ": " + c->err);
+  }
+  // later work on the handle's stream sees the fits' results
+  for (int g = 0; g < enq; ++g) {
+    TRY(cuda_check(h, cudaEventRecord(h->batch_ev, h->children[g]->stream), "cudaEventRecord"));
+    TRY(cuda_check(h, cudaStreamWaitEvent(h->stream, h->batch_ev, 0), "cudaStreamWaitEvent"));
+  }
+  return first;
 }
 
 copa_status_t copa_fit_stats(copa_handle_t h, int32_t* n_outer_run_host, int32_t* inner_host) {

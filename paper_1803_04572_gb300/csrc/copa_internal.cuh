@@ -138,6 +138,17 @@ struct copa_ctx {
   // iteration counts of the last copa_fit (copa_fit_stats)
   int32_t last_n_run = 0;
   std::vector<int32_t> last_inner;
+  // the fit enqueued last (results collected by finish_fit)
+  const int* pend_it = nullptr;
+  const double* pend_hist = nullptr;
+  const int* pend_counts = nullptr;
+  int pend_n_outer = 0, pend_n_inner = 0;
+  bool pend_adaptive = false;
+  int64_t pend_per_iter = -1;
+  cudaGraphExec_t pend_exec = nullptr;   // replayed graph of that fit, destroyed by finish_fit
+  // batched fits (copa_fit_batch): one child handle, with its own stream, per fit
+  std::vector<copa_ctx*> children;
+  cudaEvent_t batch_ev = nullptr;
   // sharded fit: the caller's all-reduce (copa_set_allreduce), NULL when not sharded
   copa_allreduce_fn red_fn = nullptr;
   void* red_user = nullptr;

@@ -810,3 +810,31 @@ def test_adaptive_stopping_matches_oracle(h, P, use_graph):
             assert n_run == len(hist_o)
         np.testing.assert_allclose(hist[:m], hist_o[:m], atol=1e-4)
     assert np.all(inner[n_run:] == 0)
+
+
+def test_fit_batch_matches_separate_fits(h, P):
+    """copa_fit_batch (a lambda / constraint sweep run as concurrent fits of one X) gives
+    every fit the FIT history and factors that copa_fit gives it alone, and the first fit
+    matches the oracle."""
+    X = synth.ehr_custom(300, 60, median=10, lo=1, hi=40, lam=3.0, cmax=10, seed=51)
+    R = 6
+    init = synth.init_factors(X.K, X.J, R)
+    grid = [("l1", 0.2), ("l1", 1.0), ("nonneg", 0.0), ("l0", 0.05), ("l1", 0.5)]
+    opts = [P.Options(R, n_outer=6, n_inner=8, c_V=c, lam_V=lam) for c, lam in grid]
+    Xd = dev_tensor(h, P, X)
+    sep = []
+    for o in opts:
+        H, V, W = (T(h, a) for a in init)
+        sep.append((h.fit(Xd, o, H, V, W), N(V), N(W)))
+    states = [tuple(T(h, a) for a in init) for _ in grid]
+    hists = h.fit_batch(Xd, opts, states)
+    h.sync()
+    tol = 1e-10 if h.precision == "fp64" else 1e-5
+    for g, (hist, V1, W1) in enumerate(sep):
+        np.testing.assert_allclose(hists[g], hist, rtol=0, atol=tol)
+        if grid[g][0] != "l0":      # the l0 jump amplifies the order of FP32 atomics
+            np.testing.assert_allclose(N(states[g][1]), V1, rtol=0, atol=100 * tol * max(1.0, np.abs(V1).max()))
+            np.testing.assert_allclose(N(states[g][2]), W1, rtol=0, atol=100 * tol * max(1.0, np.abs(W1).max()))
+    opt_o = O.Options(n_inner=8, c_H=O.NONE, c_W=O.NONNEG, c_V=O.L1, lam_V=0.2)
+    _, hist_o, _ = O.fit(X, *init, opt_o, 6)
+    np.testing.assert_allclose(hists[0], hist_o, atol=1e-8 if h.precision == "fp64" else 1e-4)

@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--gap-oracle-sample", type=int, default=2000,
                     help="subjects of the oracle refit in the fit-gap leg (0: skip)")
     ap.add_argument("--no-fit-gap", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="default launch schedule (no copa_tune)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -419,6 +420,12 @@ def gpu_leg(args, X, init, rank, world):
     DH, DV, DW = torch.zeros_like(H), torch.zeros_like(V), torch.zeros_like(W)
     mk = lambda n: P.Options(R, n_outer=n, n_inner=N_INNER, c_H="none", c_W="nonneg", c_V="l1",
                              lam_V=LAM_V, use_graph=True)
+    # the launch schedule for this tensor's size distribution (timed once, untimed here)
+    tuned = None
+    if not args.no_tune:
+        t0 = time.perf_counter()
+        tuned = h.tune(Xd, R, H, V, W)
+        tuned["tuning_s"] = time.perf_counter() - t0
     # warm-up (W outer iterations, untimed)
     h.fit(Xd, mk(args.warmup), H, V, W, DH, DV, DW)
     torch.cuda.synchronize()
@@ -441,7 +448,7 @@ def gpu_leg(args, X, init, rank, world):
         ms = float(t.item())
         torch.distributed.barrier()
     out = {"ms_total": ms, "fit_last": float(hist[-1]), "fit_hist": [float(x) for x in hist], "clocks": clocks,
-           "launches": launches}
+           "launches": launches, "autotune": tuned}
     if rank == 0 and world == 1:
         out["breakdown_ms"] = kernel_breakdown(h, P, Xd, R, H, V, W)
         out["proc_ms"], out["roofline"] = procrustes_roofline(h, P, Xd, X, R, H, V, W, PEAKS)
@@ -687,7 +694,7 @@ def main():
     line = dict(base, value=value, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms_step, scaling="strong" if world > 1 else "weak", vs_baseline=None,
                 dtype=DTYPE[args.precision], clocks=res["clocks"], gpu_launches=res["launches"],
-                fit_last=res["fit_last"], generation_s=gen_s)
+                fit_last=res["fit_last"], generation_s=gen_s, autotune=res["autotune"])
     if world == 1:
         B = iteration_bytes(X, R_RANK)
         ach = B / (ms_step * 1e-3) / 1e9

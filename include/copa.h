@@ -270,6 +270,41 @@ typedef int32_t (*copa_allreduce_fn)(double* buf, int64_t count, void* stream, v
 copa_status_t copa_set_allreduce(copa_handle_t handle, copa_allreduce_fn fn, void* user, double* buf,
                                  int64_t capacity);
 
+/* Launch-schedule autotuner (no counterpart in the paper). The schedule of one outer
+ * iteration has three knobs that depend on the rank, the precision and the distribution of
+ * subject sizes I_k:
+ *   split          subjects with I_k > split take the tall-subject Procrustes kernels (QR,
+ *                  Jacobi on R_A, second pass), the others the warp-per-subject kernel;
+ *                  1 <= split <= min(R, 32) (default min(R, 32));
+ *   blocks_per_sm  cap on the resident blocks per SM of those persistent kernels (0 = as
+ *                  many as fit, the default);
+ *   fv_path        F_V by the row-order kernel (0, default where it applies) or over the
+ *                  column-sorted copy of X (1).
+ * copa_tune times the candidates (every split in {min(R,32), 24, 16, 8} below min(R,32) with
+ * blocks_per_sm in {0, 2}; then both F_V kernels) on X with the factors H, V, W, with CUDA
+ * events on the handle's stream, and keeps the fastest: in a process-wide table keyed by
+ * copa_tune_key(R, precision, size histogram) and on the handle, whose later calls on the
+ * same X (same subj_ptr, K, S) and R use it. A key already in the table is applied without
+ * timing unless force != 0. out (HOST, may be NULL) receives the choice, ms the measured
+ * time of one Procrustes step plus one V mode with it. Synchronises. */
+typedef struct {
+  int32_t split;
+  int32_t blocks_per_sm;
+  int32_t fv_path;
+  float ms;
+} copa_tune_t;
+copa_status_t copa_tune(copa_handle_t handle, const copa_tensor_t* X, int32_t R, const void* H,
+                        const void* V, const void* W, int32_t force, copa_tune_t* out);
+/* The table's key (host only, no GPU): a hash of R, precision and the share of subjects in
+ * each power-of-two size class of I_k (0, 1, 2-3, 4-7, ...) rounded to 1/64, so that
+ * tensors drawn from the same size distribution share it. subj_ptr_host has K+1 entries. */
+copa_status_t copa_tune_key(const int64_t* subj_ptr_host, int64_t K, int32_t R, int32_t precision,
+                            uint64_t* key);
+/* Table access (host only): lookup sets *found (0/1) and, if found, *out; store inserts or
+ * replaces (split >= 1, blocks_per_sm >= 0, fv_path 0 or 1, else COPA_ERR_INVALID_ARG). */
+copa_status_t copa_tune_lookup(uint64_t key, int32_t* found, copa_tune_t* out);
+copa_status_t copa_tune_store(uint64_t key, const copa_tune_t* choice);
+
 /* Hyperparameter sweeps (Sec. 4.2 tunes the regularisation weight and the basis over a
  * grid): G independent fits of the same X (device, resident once) with their own options,
  * factors and duals, run concurrently on G streams that the library creates and keeps

@@ -33,7 +33,8 @@ EXPORTED = ["copa_create", "copa_destroy", "copa_last_error", "copa_sync", "copa
             "copa_fit_value", "copa_fit", "copa_fit_host", "copa_smooth_plan",
             "copa_smooth_project", "copa_loss_grad", "copa_procrustes_work", "copa_gram_noalloc",
             "copa_fit_launches", "copa_debug_set", "copa_partition", "copa_set_allreduce", "copa_factor_U",
-            "copa_fit_stats", "copa_fit_batch"]
+            "copa_fit_stats", "copa_fit_batch", "copa_tune", "copa_tune_key", "copa_tune_lookup",
+            "copa_tune_store"]
 KNOTS = {"uniform": 0, "quantile": 1}
 
 
@@ -51,6 +52,14 @@ class TensorC(Structure):
 
 class ProcOutC(Structure):
     _fields_ = [("Q", c_void_p), ("T", c_void_p), ("Pi", c_void_p), ("rank", c_void_p)]
+
+
+class TuneC(Structure):
+    _fields_ = [("split", c_int32), ("blocks_per_sm", c_int32), ("fv_path", c_int32), ("ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {"split": self.split, "blocks_per_sm": self.blocks_per_sm, "fv_path": self.fv_path,
+                "ms": float(self.ms)}
 
 
 class OptionsC(Structure):
@@ -84,6 +93,10 @@ _sig = {
     "copa_factor_U": [_V, c_int64, c_int32, _V, c_int64, _V, _V, _V, _V, c_int32, c_int64, _V],
     "copa_fit_stats": [_V, POINTER(c_int32), _V],
     "copa_fit_batch": [_V, POINTER(TensorC), c_int32, _V, _V, _V, _V, _V, _V, _V, _V],
+    "copa_tune": [_V, POINTER(TensorC), c_int32, _V, _V, _V, c_int32, POINTER(TuneC)],
+    "copa_tune_key": [_V, c_int64, c_int32, c_int32, POINTER(ctypes.c_uint64)],
+    "copa_tune_lookup": [ctypes.c_uint64, POINTER(c_int32), POINTER(TuneC)],
+    "copa_tune_store": [ctypes.c_uint64, POINTER(TuneC)],
     "copa_loss_grad": [_V, POINTER(TensorC), c_int32, POINTER(ProcOutC), _V, _V, _V, _V, _V, _V,
                        _V],
     "copa_procrustes_work": [_V, POINTER(c_double)],
@@ -160,6 +173,29 @@ def partition(subj_ptr, row_ptr, nshards: int) -> np.ndarray:
     if code != OK:
         raise CopaError(code, "copa_partition: bad arguments")
     return out
+
+
+def tune_key(subj_ptr, R: int, precision: str) -> int:
+    """copa_tune_key on a host subj_ptr array (no GPU needed)."""
+    sp = np.ascontiguousarray(subj_ptr, dtype=np.int64)
+    key = ctypes.c_uint64()
+    code = _lib.copa_tune_key(sp.ctypes.data, len(sp) - 1, R, PREC[precision], byref(key))
+    if code != OK:
+        raise CopaError(code, "copa_tune_key: bad arguments")
+    return key.value
+
+
+def tune_lookup(key: int):
+    """The table entry of a key as a dict, or None (copa_tune_lookup; no GPU needed)."""
+    found, out = c_int32(), TuneC()
+    _lib.copa_tune_lookup(key, byref(found), byref(out))
+    return out.as_dict() if found.value else None
+
+
+def tune_store(key: int, split: int, blocks_per_sm: int = 0, fv_path: int = 0, ms: float = 0.0):
+    code = _lib.copa_tune_store(key, byref(TuneC(split, blocks_per_sm, fv_path, ms)))
+    if code != OK:
+        raise CopaError(code, "copa_tune_store: bad choice")
 
 
 class Options:
@@ -309,6 +345,14 @@ class Copa:
         hist = np.zeros((G, max(1, n_outer)), dtype=np.float64)
         self._call(_lib.copa_fit_batch, self.h, byref(X.c()), G, arr, *ptrs, hist.ctypes.data)
         return hist[:, :n_outer]
+
+    def tune(self, X: DeviceTensor, R, H, V, W, force=False):
+        """copa_tune: times the schedule candidates on X (or reuses the table's choice) and
+        applies the fastest to this handle's later calls on X at rank R; returns it."""
+        out = TuneC()
+        self._call(_lib.copa_tune, self.h, byref(X.c()), R, _ptr(H), _ptr(V), _ptr(W), 1 if force else 0,
+                   byref(out))
+        return out.as_dict()
 
     def fit_stats(self, n_outer: int):
         """(outer iterations run, inner ADMM iterations as an n_outer x 3 array (H, W, V))

@@ -146,6 +146,13 @@ struct copa_ctx {
   bool pend_adaptive = false;
   int64_t pend_per_iter = -1;
   cudaGraphExec_t pend_exec = nullptr;   // replayed graph of that fit, destroyed by finish_fit
+  // autotuned schedule (copa_tune): used by the calls on the tensor, rank and precision it
+  // was tuned for
+  bool tune_valid = false;
+  const int64_t* tune_ptr = nullptr;
+  int64_t tune_K = -1, tune_S = -1;
+  int tune_R = 0;
+  int tune_split = 0, tune_bps = 0, tune_fv = 0;
   // batched fits (copa_fit_batch): one child handle, with its own stream, per fit
   std::vector<copa_ctx*> children;
   cudaEvent_t batch_ev = nullptr;
@@ -186,6 +193,23 @@ enum Slot {
 };
 copa_status_t get_warm_offsets(copa_ctx* h, const TensorView& X, int R, const int64_t** woff,
                                int64_t* total);
+
+// The schedule knobs of the Procrustes and V-mode launches: subjects with I_k > split take
+// the tall-subject kernels; bps caps the resident blocks per SM of the persistent
+// Procrustes kernels (0: as many as fit); fv = 1 takes the column-sorted F_V kernel where
+// the row-order one would apply. Defaults unless copa_tune chose them for (X, R).
+struct TuneChoice {
+  int split, bps, fv;
+};
+inline TuneChoice active_tune(const copa_ctx* h, const TensorView& X, int R) {
+  TuneChoice c{R < 32 ? R : 32, 0, 0};
+  if (h->tune_valid && h->tune_ptr == X.subj_ptr && h->tune_K == X.K && h->tune_S == X.S && h->tune_R == R) {
+    c.split = h->tune_split;
+    c.bps = h->tune_bps;
+    c.fv = h->tune_fv;
+  }
+  return c;
+}
 
 copa_status_t ws_get(copa_ctx* h, int slot, size_t bytes, void** out);
 copa_status_t fail(copa_ctx* h, copa_status_t code, const std::string& msg);

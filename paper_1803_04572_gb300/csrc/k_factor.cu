@@ -1198,7 +1198,7 @@ copa_status_t launch_mttkrp_v(copa_ctx* h, const TensorView& X, int R, const Rea
   // F_V in row order (FP32, when J x 32 floats fit in shared memory), else over the
   // column-sorted copy of X
   bool rows_fv = false;
-  if constexpr (std::is_same<Real, float>::value) rows_fv = spmm_rows_fits(h, X);
+  if constexpr (std::is_same<Real, float>::value) rows_fv = spmm_rows_fits(h, X) && active_tune(h, X, R).fv != 1;
   if (rows_fv) {
     if ((st = get_rowmaps(h, X, reuse_csc, &nzrow, &rsubj)) != COPA_OK) return st;
   } else if ((st = get_csc<Real>(h, X, reuse_csc, &cptr, &crow, &cval, &rsubj)) != COPA_OK) {

@@ -1837,9 +1837,10 @@ RowKernels<double> row_kernels_for<double>(int kr) {
   }
 }
 
-// grid of a lane-per-row kernel: SMs x resident blocks, no more than the subjects need
+// grid of a lane-per-row kernel: SMs x resident blocks (at most bps if bps > 0), no more
+// than the subjects need
 template <typename Kern>
-copa_status_t row_grid(copa_ctx* h, Kern kern, size_t smem, int64_t K, int64_t* blocks) {
+copa_status_t row_grid(copa_ctx* h, Kern kern, size_t smem, int64_t K, int64_t* blocks, int bps) {
   copa_status_t st;
   if ((st = cuda_check(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                        "cudaFuncSetAttribute")) != COPA_OK)
@@ -1848,6 +1849,7 @@ copa_status_t row_grid(copa_ctx* h, Kern kern, size_t smem, int64_t K, int64_t* 
   if ((st = cuda_check(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWNT, smem), "occupancy")) !=
       COPA_OK)
     return st;
+  if (bps > 0 && per_sm > bps) per_sm = bps;
   *blocks = (int64_t)h->num_sms * std::max(per_sm, 1);
   const int64_t need = (K + kWNT / 32 - 1) / (kWNT / 32);
   if (*blocks > need) *blocks = std::max<int64_t>(need, 1);
@@ -1891,16 +1893,19 @@ copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const R
     blocks = (int64_t)h->num_sms * per_sm;
     if (blocks > X.K) blocks = X.K > 0 ? X.K : 1;
   }
+  const TuneChoice tc = active_tune(h, X, R);
   int64_t sblocks = 0, qblocks = 0, jblocks = 0, pblocks = 0;
   if (rows) {
-    if ((st = row_grid(h, rk.small, rk.small_smem, X.K, &sblocks)) != COPA_OK) return st;
-    if ((st = row_grid(h, rk.qr, rk.qr_smem, X.K, &qblocks)) != COPA_OK) return st;
-    if ((st = row_grid(h, rk.jac, rk.jac_smem, X.K, &jblocks)) != COPA_OK) return st;
-    if ((st = row_grid(h, rk.pass2, rk.tall_smem, X.K, &pblocks)) != COPA_OK) return st;
+    if ((st = row_grid(h, rk.small, rk.small_smem, X.K, &sblocks, tc.bps)) != COPA_OK) return st;
+    if ((st = row_grid(h, rk.qr, rk.qr_smem, X.K, &qblocks, tc.bps)) != COPA_OK) return st;
+    if ((st = row_grid(h, rk.jac, rk.jac_smem, X.K, &jblocks, tc.bps)) != COPA_OK) return st;
+    if ((st = row_grid(h, rk.pass2, rk.tall_smem, X.K, &pblocks, tc.bps)) != COPA_OK) return st;
   }
   const int64_t* order = nullptr;
   if ((st = get_schedule(h, X, &order)) != COPA_OK) return st;
-  const int* n_big = rows ? schedule_count_above(h, std::min(R, 32)) : nullptr;   // I_k > min(R, 32)
+  // I_k > split (min(R, 32) unless tuned lower) take the tall-subject kernels
+  const int split = std::max(1, std::min(tc.split, std::min(R, 32)));
+  const int* n_big = rows ? schedule_count_above(h, split) : nullptr;
   int* counter = nullptr;
   if ((st = ws_get(h, SLOT_COUNTER, 64, (void**)&counter)) != COPA_OK) return st;
   unsigned long long* fma_count = reinterpret_cast<unsigned long long*>(counter + 2);

@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--gap-oracle-sample", type=int, default=2000,
                     help="subjects of the oracle refit in the fit-gap leg (0: skip)")
     ap.add_argument("--no-fit-gap", action="store_true")
+    ap.add_argument("--plain-outer", type=int, default=3,
+                    help="outer iterations of the plain per-subject FP64 form in the fit-gap leg (0: skip)")
     ap.add_argument("--no-tune", action="store_true", help="default launch schedule (no copa_tune)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -497,13 +499,34 @@ def fit_gap_leg(args, X, init, h):
     hist32, ms32 = fit_history(h, P, X, init, n, "bf16")
     h64 = P.Copa(h.device.index, "fp64")
     hist64, ms64 = fit_history(h64, P, X, init, n, "f64")
+    plain = None
+    if args.plain_outer > 0:
+        # the plain per-subject FP64 form (block per subject, FP64 Gram eigendecomposition,
+        # explicit Y, unfused launches, no graph) from the same initialisation
+        import torch
+        npl = min(args.plain_outer, n)
+        Xd = P.DeviceTensor.from_host(X, h64.device, "f64")
+        Hp, Vp, Wp = (torch.as_tensor(a, dtype=torch.float64, device=h64.device) for a in init)
+        h64.sync()
+        t0 = time.perf_counter()
+        hp = h64.fit_plain(Xd, P.Options(R_RANK, n_outer=npl, n_inner=N_INNER, c_H="none", c_W="nonneg", c_V="l1",
+                                         lam_V=LAM_V), Hp, Vp, Wp)
+        h64.sync()
+        sp = time.perf_counter() - t0
+        del Xd, Hp, Vp, Wp
+        plain = {"outer_iterations": npl, "fit": [float(x) for x in hp], "iters_per_s": npl / sp,
+                 "fit_gap_vs_mixed_max": float(np.max(np.abs(np.array(hp) - np.array(hist32[:npl])))),
+                 "mixed_speedup": (1000.0 * n / ms32) / (npl / sp),
+                 "note": "copa_fit_plain: one block per subject, FP64 Gram eigendecomposition, explicit Y, "
+                         "unfused launches, no graph; host-timed including its set-up"}
     h64.close()
     res = {"outer_iterations": n, "n_inner": N_INNER,
            "fit_mixed": hist32, "fit_fp64": hist64,
            "fit_gap_vs_fp64_max": float(np.max(np.abs(np.array(hist32) - np.array(hist64)))),
            "mixed_iters_per_s": 1000.0 * n / ms32, "fp64_iters_per_s": 1000.0 * n / ms64,
            "note": "same kernels, FP64 handle: every step in double (the Procrustes step by the "
-                   "block or lane kernels in FP64)"}
+                   "block or lane kernels in FP64)",
+           "plain_fp64": plain}
     if args.gap_oracle_sample > 0:
         Xs, init_s = sample_subjects(X, init, args.gap_oracle_sample, seed=5)
         hs, _ = fit_history(h, P, Xs, init_s, n, "bf16")

@@ -270,6 +270,21 @@ typedef int32_t (*copa_allreduce_fn)(double* buf, int64_t count, void* stream, v
 copa_status_t copa_set_allreduce(copa_handle_t handle, copa_allreduce_fn fn, void* user, double* buf,
                                  int64_t capacity);
 
+/* The plain per-subject FP64 form of Algorithm 1 (a comparison form: the method as
+ * written, without this library's batching, fusion or precision choices). Same arguments
+ * and results as copa_fit (fixed counts; eps_*, use_graph and the sharding hook are not
+ * used) on an FP64 handle: one block per subject forms A_k = X_k V S_k H^T in global memory,
+ * the FP64 Gram A_k^T A_k (or A_k A_k^T when I_k < R) and its eigendecomposition by cyclic
+ * Jacobi, and Q_k = A_k C Lambda^{-1/2}_+ C^T (or C Lambda^{-1/2}_+ C^T A_k) over the
+ * eigenvalues above tau times the largest (Eq. 5 with the truncated SVD of Algorithm 1);
+ * Y_k = Q_k^T X_k is materialised over the distinct columns of every X_k; the MTTKRPs read Y;
+ * each ADMM inner iteration is its own launch; the host waits for every outer iteration.
+ * R <= 64 and J <= 65536 (COPA_ERR_UNSUPPORTED otherwise, and on a mixed handle). Uses
+ * (2 S + 1) R + (distinct (subject, column) pairs) R doubles of workspace. Synchronises. */
+copa_status_t copa_fit_plain(copa_handle_t handle, const copa_tensor_t* X, const copa_options_t* opt,
+                             void* H, void* V, void* W, void* DH, void* DV, void* DW,
+                             double* fit_history_host);
+
 /* Launch-schedule autotuner (no counterpart in the paper). The schedule of one outer
  * iteration has three knobs that depend on the rank, the precision and the distribution of
  * subject sizes I_k:

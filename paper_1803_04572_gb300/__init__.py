@@ -34,7 +34,7 @@ EXPORTED = ["copa_create", "copa_destroy", "copa_last_error", "copa_sync", "copa
             "copa_smooth_project", "copa_loss_grad", "copa_procrustes_work", "copa_gram_noalloc",
             "copa_fit_launches", "copa_debug_set", "copa_partition", "copa_set_allreduce", "copa_factor_U",
             "copa_fit_stats", "copa_fit_batch", "copa_tune", "copa_tune_key", "copa_tune_lookup",
-            "copa_tune_store"]
+            "copa_tune_store", "copa_fit_plain"]
 KNOTS = {"uniform": 0, "quantile": 1}
 
 
@@ -94,6 +94,7 @@ _sig = {
     "copa_fit_stats": [_V, POINTER(c_int32), _V],
     "copa_fit_batch": [_V, POINTER(TensorC), c_int32, _V, _V, _V, _V, _V, _V, _V, _V],
     "copa_tune": [_V, POINTER(TensorC), c_int32, _V, _V, _V, c_int32, POINTER(TuneC)],
+    "copa_fit_plain": [_V, POINTER(TensorC), POINTER(OptionsC), _V, _V, _V, _V, _V, _V, _V],
     "copa_tune_key": [_V, c_int64, c_int32, c_int32, POINTER(ctypes.c_uint64)],
     "copa_tune_lookup": [ctypes.c_uint64, POINTER(c_int32), POINTER(TuneC)],
     "copa_tune_store": [ctypes.c_uint64, POINTER(TuneC)],
@@ -361,6 +362,17 @@ class Copa:
         inner = np.zeros(3 * max(n_outer, 1), dtype=np.int32)
         self._check(_lib.copa_fit_stats(self.h, byref(n), inner.ctypes.data))
         return n.value, inner[:3 * n_outer].reshape(n_outer, 3)
+
+    def fit_plain(self, X: DeviceTensor, opt: Options, H, V, W, DH=None, DV=None, DW=None):
+        """copa_fit_plain: the plain per-subject FP64 form (FP64 handle); returns the FIT
+        history (numpy) and updates H, V, W (and the duals) in place."""
+        DH = self.torch.zeros_like(H) if DH is None else DH
+        DV = self.torch.zeros_like(V) if DV is None else DV
+        DW = self.torch.zeros_like(W) if DW is None else DW
+        hist = np.zeros(max(1, opt.n_outer), dtype=np.float64)
+        self._call(_lib.copa_fit_plain, self.h, byref(X.c()), byref(opt.c()), _ptr(H), _ptr(V), _ptr(W), _ptr(DH),
+                   _ptr(DV), _ptr(DW), hist.ctypes.data)
+        return hist[:opt.n_outer]
 
     def fit_host(self, Xh, opt: Options, H, V, W, DH=None, DV=None, DW=None, val_dtype="f32"):
         """copa_fit_host on numpy arrays (H, V, W, duals updated in place)."""

@@ -838,3 +838,34 @@ def test_fit_batch_matches_separate_fits(h, P):
     opt_o = O.Options(n_inner=8, c_H=O.NONE, c_W=O.NONNEG, c_V=O.L1, lam_V=0.2)
     _, hist_o, _ = O.fit(X, *init, opt_o, 6)
     np.testing.assert_allclose(hists[0], hist_o, atol=1e-8 if h.precision == "fp64" else 1e-4)
+
+
+@pytest.mark.parametrize("case", ["planted", "ehr_R40"])
+def test_plain_fp64_form_matches_oracle(P, case):
+    """copa_fit_plain (block per subject, FP64 Gram eigendecomposition, explicit Y, unfused
+    launches, no graph) against the oracle's trajectory. Its eigenvalues of A_k^T A_k carry
+    errors of about eps kappa_k^2 relative to the largest, so Q_k of a subject with kappa_k
+    near the cut (1e4) is good to ~1e-8: the FIT is held to 1e-8, the factors to 1e-6."""
+    import torch
+    hd = P.Copa(0, "fp64")
+    if case == "planted":
+        X, _ = synth.planted_small()
+        R, n_out, n_in = 5, 8, 10
+        opt_o = O.Options(n_inner=n_in, c_H=O.NONE, c_W=O.NONNEG, c_V=O.L1, lam_V=1.0)
+    else:
+        X = synth.ehr_tensor(60, 80, np.array([2000, 300, 41, 40, 39, 5, 1, 0] + [12] * 52, dtype=np.int64),
+                             4.0, 50, seed=71)
+        R, n_out, n_in = 40, 4, 6
+        opt_o = O.Options(n_inner=n_in, c_H=O.NONE, c_W=O.NONNEG, c_V=O.L1, lam_V=1.0)
+    init = synth.init_factors(X.K, X.J, R)
+    _, hist_o, rec = O.fit(X, *init, opt_o, n_out)
+    Xd = P.DeviceTensor.from_host(X, hd.device, "f64")
+    H, V, W = (torch.as_tensor(a, device=hd.device) for a in init)
+    hist = hd.fit_plain(Xd, P.Options(R, n_outer=n_out, n_inner=n_in, c_V="l1", lam_V=1.0), H, V, W)
+    np.testing.assert_allclose(hist, hist_o, rtol=0, atol=1e-8)
+    for got, ref in ((H, rec.state.H), (V, rec.state.V), (W, rec.state.W)):
+        assert rel(N(got), ref) <= 1e-6
+    with pytest.raises(P.CopaError) as e:
+        P.Copa(0, "mixed").fit_plain(P.DeviceTensor.from_host(X, hd.device, "f32"), P.Options(R, n_outer=1),
+                                     *(torch.as_tensor(a, dtype=torch.float32, device=hd.device) for a in init))
+    assert e.value.code == P.ERR_UNSUPPORTED

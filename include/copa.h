@@ -121,6 +121,18 @@ copa_status_t copa_sync(copa_handle_t handle);
  * Returns COPA_ERR_INVALID_ARG with a message naming the first violation. */
 copa_status_t copa_validate(copa_handle_t handle, const copa_tensor_t* X);
 
+/* A handle keeps data derived from the tensors it has been called with, keyed by their
+ * device addresses and sizes: the schedule of subjects by I_k, the offsets and the
+ * Jacobi rotations of the warm start (the previous iteration's rotations start the next
+ * one), the column-sorted copy of X and the nonzero -> row maps of the V mode, and the
+ * choice of copa_tune. A tensor whose device arrays were rewritten in place, or a new
+ * tensor at the addresses of a freed one with the same sizes, looks unchanged to those
+ * keys: call copa_forget_tensor before the next call with it. It waits for the handle's
+ * stream, then drops every such datum (they are rebuilt on the next call, and the next
+ * fit starts its Procrustes sweeps cold). copa_fit_host needs no such call: it compares
+ * the uploaded tensor with the previous one itself. */
+copa_status_t copa_forget_tensor(copa_handle_t handle);
+
 /* (a)+(b), Eq. 5 and Algorithm 1's per-subject loop, for every subject at once:
  * A_k = X_k V S_k H^T = B D C^T (thin SVD) and Q_k = B C^T over the singular values with
  * sigma^2 > tau * sigma_max^2 (tau = 1e-8 in the paper's reading used here). Computed by
@@ -343,7 +355,11 @@ copa_status_t copa_fit_stats(copa_handle_t handle, int32_t* n_outer_run_host, in
 
 /* copa_fit on HOST buffers: copies X (arrays given as host pointers in X_host) and the
  * state to the device, runs copa_fit, copies H, V, W, the duals and the FIT history
- * back. Device memory is owned by the handle and reused across calls. Synchronises. */
+ * back. Device memory is owned by the handle and reused across calls. The uploaded X is
+ * compared byte for byte, on the device, with the one the previous call uploaded: if it
+ * is the same, the data derived from it (see copa_forget_tensor) carry over, so that
+ * successive calls continue one fit (warm start included); otherwise they are rebuilt.
+ * Synchronises. */
 copa_status_t copa_fit_host(copa_handle_t handle, const copa_tensor_t* X_host,
                             const copa_options_t* opt, void* H_host, void* V_host,
                             void* W_host, void* DH_host, void* DV_host, void* DW_host,

@@ -9,6 +9,7 @@ is no CPU fallback: importing this package fails if the library has not been bui
 from __future__ import annotations
 
 import ctypes
+import itertools
 import os
 from ctypes import POINTER, Structure, byref, c_double, c_int32, c_int64, c_void_p
 from typing import Optional
@@ -34,7 +35,7 @@ EXPORTED = ["copa_create", "copa_destroy", "copa_last_error", "copa_sync", "copa
             "copa_smooth_project", "copa_loss_grad", "copa_procrustes_work", "copa_gram_noalloc",
             "copa_fit_launches", "copa_debug_set", "copa_partition", "copa_set_allreduce", "copa_factor_U",
             "copa_fit_stats", "copa_fit_batch", "copa_tune", "copa_tune_key", "copa_tune_lookup",
-            "copa_tune_store", "copa_fit_plain"]
+            "copa_tune_store", "copa_fit_plain", "copa_forget_tensor"]
 KNOTS = {"uniform": 0, "quantile": 1}
 
 
@@ -77,6 +78,7 @@ _sig = {
     "copa_destroy": [_V],
     "copa_sync": [_V],
     "copa_validate": [_V, POINTER(TensorC)],
+    "copa_forget_tensor": [_V],
     "copa_procrustes": [_V, POINTER(TensorC), c_int32, _V, _V, _V, c_double, POINTER(ProcOutC), _V],
     "copa_mttkrp": [_V, c_int32, POINTER(TensorC), c_int32, POINTER(ProcOutC), _V, _V, _V, _V],
     "copa_gram": [_V, _V, c_int64, c_int32, _V],
@@ -123,9 +125,17 @@ def _ptr(t) -> Optional[int]:
 
 
 class DeviceTensor:
-    """Segmented per-subject CSR storage of {X_k} on the device (torch-owned arrays)."""
+    """Segmented per-subject CSR storage of {X_k} on the device (torch-owned arrays).
+
+    Each instance has a serial number: a handle called with another instance than the last
+    one first drops what it derived from the last one (copa_forget_tensor), since a new
+    tensor can sit at a freed one's addresses. After rewriting the arrays of an instance in
+    place, call Copa.forget_tensor() before using it again."""
+
+    _serials = itertools.count(1)
 
     def __init__(self, K, J, subj_ptr, row_ptr, col, vals, val_dtype: str):
+        self.serial = next(DeviceTensor._serials)
         self.K, self.J = int(K), int(J)
         self.subj_ptr, self.row_ptr, self.col, self.vals = subj_ptr, row_ptr, col, vals
         self.val_dtype = val_dtype
@@ -230,6 +240,19 @@ class Copa:
         h = c_void_p()
         self._check(_lib.copa_create(byref(h), device, c_void_p(self.stream.cuda_stream), PREC[precision]), None)
         self.h = h
+        self._last_serial = None
+
+    def _xc(self, X: DeviceTensor) -> TensorC:
+        """X's TensorC, after dropping the handle's caches if X is not the tensor of the last call."""
+        if X.serial != self._last_serial:
+            if self._last_serial is not None:
+                self.forget_tensor()
+            self._last_serial = X.serial
+        return X.c()
+
+    def forget_tensor(self):
+        """copa_forget_tensor: drop the data the handle derived from the tensors it has seen."""
+        self._call(_lib.copa_forget_tensor, self.h)
 
     def close(self):
         if getattr(self, "h", None):
@@ -265,7 +288,7 @@ class Copa:
         self._call(_lib.copa_sync, self.h)
 
     def validate(self, X: DeviceTensor):
-        self._call(_lib.copa_validate, self.h, byref(X.c()))
+        self._call(_lib.copa_validate, self.h, byref(self._xc(X)))
 
     def procrustes(self, X: DeviceTensor, R, H, V, W, tau=1e-8, want_pi=False, want_rank=False,
                    want_fh=True):
@@ -274,7 +297,7 @@ class Copa:
               "rank": self.empty(X.K, dtype=self.torch.int32) if want_rank else None}
         fh = self.empty(R, R) if want_fh else None
         po = self.proc_c(st)
-        self._call(_lib.copa_procrustes, self.h, byref(X.c()), R, _ptr(H), _ptr(V), _ptr(W), tau,
+        self._call(_lib.copa_procrustes, self.h, byref(self._xc(X)), R, _ptr(H), _ptr(V), _ptr(W), tau,
                                          byref(po), _ptr(fh))
         st["F_H"] = fh
         return st
@@ -287,7 +310,7 @@ class Copa:
         rows = {"H": R, "V": X.J, "W": X.K}[mode]
         F = self.empty(rows, R)
         utu = self.empty(R, R, dtype=self.torch.float64) if want_utu else None
-        self._call(_lib.copa_mttkrp, self.h, MODE[mode], byref(X.c()), R, byref(self.proc_c(st)), _ptr(H),
+        self._call(_lib.copa_mttkrp, self.h, MODE[mode], byref(self._xc(X)), R, byref(self.proc_c(st)), _ptr(H),
                                      _ptr(W), _ptr(F), _ptr(utu))
         return (F, utu) if want_utu else F
 
@@ -312,7 +335,7 @@ class Copa:
 
     def fit_value(self, X: DeviceTensor, R, V, F_V, UtU, x_norm2=0.0):
         out = self.empty(1, dtype=self.torch.float64)
-        self._call(_lib.copa_fit_value, self.h, byref(X.c()), R, _ptr(V), _ptr(F_V), _ptr(UtU), x_norm2,
+        self._call(_lib.copa_fit_value, self.h, byref(self._xc(X)), R, _ptr(V), _ptr(F_V), _ptr(UtU), x_norm2,
                                         _ptr(out))
         return out
 
@@ -324,7 +347,7 @@ class Copa:
         DW = self.torch.zeros_like(W) if DW is None else DW
         hist = np.zeros(max(1, opt.n_outer), dtype=np.float64)
         po = byref(self.proc_c(state)) if state is not None else None
-        self._call(_lib.copa_fit, self.h, byref(X.c()), byref(opt.c()), _ptr(H), _ptr(V), _ptr(W), _ptr(DH),
+        self._call(_lib.copa_fit, self.h, byref(self._xc(X)), byref(opt.c()), _ptr(H), _ptr(V), _ptr(W), _ptr(DH),
                                   _ptr(DV), _ptr(DW), hist.ctypes.data, po)
         return hist[:self.fit_stats(opt.n_outer)[0]]
 
@@ -344,14 +367,14 @@ class Copa:
         ptrs = [(c_void_p * G)(*[_ptr(st[i]) for st in full]) for i in range(6)]
         n_outer = opts[0].n_outer
         hist = np.zeros((G, max(1, n_outer)), dtype=np.float64)
-        self._call(_lib.copa_fit_batch, self.h, byref(X.c()), G, arr, *ptrs, hist.ctypes.data)
+        self._call(_lib.copa_fit_batch, self.h, byref(self._xc(X)), G, arr, *ptrs, hist.ctypes.data)
         return hist[:, :n_outer]
 
     def tune(self, X: DeviceTensor, R, H, V, W, force=False):
         """copa_tune: times the schedule candidates on X (or reuses the table's choice) and
         applies the fastest to this handle's later calls on X at rank R; returns it."""
         out = TuneC()
-        self._call(_lib.copa_tune, self.h, byref(X.c()), R, _ptr(H), _ptr(V), _ptr(W), 1 if force else 0,
+        self._call(_lib.copa_tune, self.h, byref(self._xc(X)), R, _ptr(H), _ptr(V), _ptr(W), 1 if force else 0,
                    byref(out))
         return out.as_dict()
 
@@ -370,7 +393,7 @@ class Copa:
         DV = self.torch.zeros_like(V) if DV is None else DV
         DW = self.torch.zeros_like(W) if DW is None else DW
         hist = np.zeros(max(1, opt.n_outer), dtype=np.float64)
-        self._call(_lib.copa_fit_plain, self.h, byref(X.c()), byref(opt.c()), _ptr(H), _ptr(V), _ptr(W), _ptr(DH),
+        self._call(_lib.copa_fit_plain, self.h, byref(self._xc(X)), byref(opt.c()), _ptr(H), _ptr(V), _ptr(W), _ptr(DH),
                    _ptr(DV), _ptr(DW), hist.ctypes.data)
         return hist[:opt.n_outer]
 
@@ -397,7 +420,7 @@ class Copa:
         "uniform" (equally spaced in days)."""
         S_out, nnz_out = c_int64(), c_int64()
         kr = KNOTS[knots]
-        self._call(_lib.copa_smooth_plan, self.h, byref(X.c()), _ptr(days), n_basis, degree, kr, byref(S_out),
+        self._call(_lib.copa_smooth_plan, self.h, byref(self._xc(X)), _ptr(days), n_basis, degree, kr, byref(S_out),
                                           byref(nnz_out))
         torch = self.torch
         tdt = torch.float32 if out_dtype == "f32" else torch.float64
@@ -407,7 +430,7 @@ class Copa:
                           self.empty(max(nnz_out.value, 1), dtype=tdt)[:nnz_out.value], out_dtype)
         C = self.empty(X.S, n_basis, dtype=torch.float64) if want_C else None
         xc = Xp.c()
-        self._call(_lib.copa_smooth_project, self.h, byref(X.c()), _ptr(days), n_basis, degree, kr, byref(xc),
+        self._call(_lib.copa_smooth_project, self.h, byref(self._xc(X)), _ptr(days), n_basis, degree, kr, byref(xc),
                                              _ptr(C))
         return Xp, C
 
@@ -466,7 +489,7 @@ class Copa:
     def loss_grad(self, X: DeviceTensor, R, st, H, V, W):
         loss = self.empty(1, dtype=self.torch.float64)
         gH, gV, gW = self.empty(*H.shape), self.empty(*V.shape), self.empty(*W.shape)
-        self._call(_lib.copa_loss_grad, self.h, byref(X.c()), R, byref(self.proc_c(st)), _ptr(H), _ptr(V),
+        self._call(_lib.copa_loss_grad, self.h, byref(self._xc(X)), R, byref(self.proc_c(st)), _ptr(H), _ptr(V),
                                         _ptr(W), _ptr(loss), _ptr(gH), _ptr(gV), _ptr(gW))
         return loss, gH, gV, gW
 

@@ -43,6 +43,38 @@ copa_status_t ws_get(copa_ctx* h, int slot, size_t bytes, void** out) {
   return COPA_OK;
 }
 
+void forget_tensor_caches(copa_ctx* h) {
+  h->sched_key = nullptr;
+  h->sched_K = h->sched_S = 0;
+  h->warm_key = nullptr;
+  h->warm_valid = false;
+  h->csc_key = nullptr;
+  h->csc_nnz = h->csc_S = -1;
+  h->rmap_key = nullptr;
+  h->rmap_nnz = h->rmap_S = h->rmap_K = -1;
+  h->tune_valid = false;
+  h->tune_ptr = nullptr;
+  h->host_x_valid = false;
+  for (copa_ctx* c : h->children) forget_tensor_caches(c);
+}
+
+// The same for the caches keyed by one tensor's subj_ptr / col_idx addresses only.
+static void forget_caches_of(copa_ctx* h, const void* subj_ptr, const void* col) {
+  if (!subj_ptr && !col) return;
+  if (h->sched_key == subj_ptr) h->sched_key = nullptr;
+  if (h->warm_key == subj_ptr) {
+    h->warm_key = nullptr;
+    h->warm_valid = false;
+  }
+  if (h->tune_ptr == subj_ptr) {
+    h->tune_valid = false;
+    h->tune_ptr = nullptr;
+  }
+  if (h->csc_key == col) h->csc_key = nullptr;
+  if (h->rmap_key == col) h->rmap_key = nullptr;
+  for (copa_ctx* c : h->children) forget_caches_of(c, subj_ptr, col);
+}
+
 TensorView view_of(const copa_tensor_t* X) {
   TensorView v;
   v.K = X->K; v.J = X->J; v.S = X->S; v.nnz = X->nnz;
@@ -115,6 +147,31 @@ __global__ void k_validate(TensorView X, int* __restrict__ status) {
       if (!(fabsf(v) <= 256.0f) || v != rintf(v)) set_status(status, 107, (int)t);
     }
   }
+}
+
+// Sets *flag if any byte of a[q] differs from b[q] (q < 4; n[q] bytes each; both
+// cudaMalloc'd, hence 16-byte aligned).
+struct ByteCmp {
+  const unsigned char* a[4];
+  const unsigned char* b[4];
+  int64_t n[4];
+};
+
+__global__ void k_bytes_differ(ByteCmp c, int* __restrict__ flag) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nt = gridDim.x * (int64_t)blockDim.x;
+  bool diff = false;
+  for (int q = 0; q < 4; ++q) {
+    const int64_t n16 = c.n[q] >> 4;
+    const uint4* a = reinterpret_cast<const uint4*>(c.a[q]);
+    const uint4* b = reinterpret_cast<const uint4*>(c.b[q]);
+    for (int64_t i = tid; i < n16; i += nt) {
+      const uint4 x = __ldcs(a + i), y = __ldcs(b + i);
+      diff |= (x.x != y.x) | (x.y != y.y) | (x.z != y.z) | (x.w != y.w);
+    }
+    for (int64_t i = (n16 << 4) + tid; i < c.n[q]; i += nt) diff |= c.a[q][i] != c.b[q][i];
+  }
+  if (__any_sync(0xffffffffu, diff) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
 }
 
 __global__ void k_xnorm2(TensorView X, double* __restrict__ out) {
@@ -414,6 +471,15 @@ copa_status_t copa_validate(copa_handle_t h, const copa_tensor_t* X) {
   TRY(check_tensor_args(h, X));
   TRY(launch_validate(h, view_of(X)));
   return sync_status(h);
+}
+
+copa_status_t copa_forget_tensor(copa_handle_t h) {
+  CHECK_H(h);
+  TRY(set_dev(h));
+  // work already queued may still read the caches: let it finish first
+  TRY(cuda_check(h, cudaStreamSynchronize(h->stream), "sync"));
+  forget_tensor_caches(h);
+  return COPA_OK;
 }
 
 copa_status_t copa_procrustes(copa_handle_t h, const copa_tensor_t* X, int32_t R, const void* H,
@@ -1044,22 +1110,70 @@ copa_status_t copa_fit_host(copa_handle_t h, const copa_tensor_t* Xh, const copa
                             es * (size_t)Xh->J * R,          es * (size_t)Xh->K * R};
   const void* src[10] = {Xh->subj_ptr, Xh->row_ptr, Xh->col_idx, Xh->vals, H_host, V_host, W_host,
                          DH_host,      DV_host,     DW_host};
-  void* dst[10];
-  for (int i = 0; i < 10; ++i) {
-    if (h->host_slot_bytes[i] < sizes[i] + 16) {
+  auto slot = [&](int i, size_t bytes) -> copa_status_t {
+    if (h->host_slot_bytes[i] < bytes + 16) {
       if (h->host_slot_ptr[i]) cudaFree(h->host_slot_ptr[i]);
       h->host_slot_ptr[i] = nullptr;
       h->host_slot_bytes[i] = 0;
-      if (cudaMalloc(&h->host_slot_ptr[i], sizes[i] + 16) != cudaSuccess) {
+      if (cudaMalloc(&h->host_slot_ptr[i], bytes + 16) != cudaSuccess) {
         cudaGetLastError();
         return fail(h, COPA_ERR_OOM, "copa_fit_host: device allocation failed");
       }
-      h->host_slot_bytes[i] = sizes[i] + 16;
+      h->host_slot_bytes[i] = bytes + 16;
     }
-    dst[i] = h->host_slot_ptr[i];
+    return COPA_OK;
+  };
+  // X goes to the staging slots 10..13 and is compared on the device with the copy in
+  // slots 0..3 that the last call left there: the handle's caches derived from X (subject
+  // schedule, warm-start rotations, column-sorted copy) are keyed by device address, so
+  // they carry over to this call only if the contents are unchanged.
+  for (int i = 0; i < 10; ++i) {
+    const int d = i < 4 ? 10 + i : i;
+    TRY(slot(d, sizes[i]));
     if (sizes[i])
-      TRY(cuda_check(h, cudaMemcpyAsync(dst[i], src[i], sizes[i], cudaMemcpyHostToDevice, h->stream), "H2D"));
+      TRY(cuda_check(h, cudaMemcpyAsync(h->host_slot_ptr[d], src[i], sizes[i], cudaMemcpyHostToDevice, h->stream),
+                     "H2D"));
   }
+  bool same = h->host_x_valid && h->host_K == Xh->K && h->host_J == Xh->J && h->host_S == Xh->S &&
+              h->host_nnz == Xh->nnz && h->host_vdt == Xh->val_dtype;
+  for (int i = 0; i < 4 && same; ++i) same = h->host_slot_bytes[i] >= sizes[i] + 16;
+  if (same) {
+    TRY(slot(14, sizeof(int)));
+    int* flag = reinterpret_cast<int*>(h->host_slot_ptr[14]);
+    TRY(cuda_check(h, cudaMemsetAsync(flag, 0, sizeof(int), h->stream), "memset"));
+    ByteCmp c;
+    int64_t most = 0;
+    for (int q = 0; q < 4; ++q) {
+      c.a[q] = reinterpret_cast<const unsigned char*>(h->host_slot_ptr[q]);
+      c.b[q] = reinterpret_cast<const unsigned char*>(h->host_slot_ptr[10 + q]);
+      c.n[q] = (int64_t)sizes[q];
+      most = std::max<int64_t>(most, c.n[q] >> 4);
+    }
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((most + 255) / 256, (int64_t)h->num_sms * 8));
+    k_bytes_differ<<<blocks, 256, 0, h->stream>>>(c, flag);
+    TRY(cuda_check(h, cudaGetLastError(), "k_bytes_differ"));
+    int differ = 1;
+    TRY(cuda_check(h, cudaMemcpyAsync(&differ, flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "D2H"));
+    TRY(cuda_check(h, cudaStreamSynchronize(h->stream), "sync"));
+    same = differ == 0;
+  }
+  if (!same) {   // the staged copy becomes the resident one; nothing derived from either is kept
+    TRY(cuda_check(h, cudaStreamSynchronize(h->stream), "sync"));
+    for (int q : {0, 10})
+      forget_caches_of(h, h->host_slot_ptr[q], h->host_slot_ptr[q + 2]);
+    for (int q = 0; q < 4; ++q) {
+      std::swap(h->host_slot_ptr[q], h->host_slot_ptr[10 + q]);
+      std::swap(h->host_slot_bytes[q], h->host_slot_bytes[10 + q]);
+    }
+    h->host_x_valid = true;
+    h->host_K = Xh->K;
+    h->host_J = Xh->J;
+    h->host_S = Xh->S;
+    h->host_nnz = Xh->nnz;
+    h->host_vdt = Xh->val_dtype;
+  }
+  void* dst[10];
+  for (int i = 0; i < 10; ++i) dst[i] = h->host_slot_ptr[i];
   copa_tensor_t Xd = *Xh;
   Xd.subj_ptr = (const int64_t*)dst[0];
   Xd.row_ptr = (const int64_t*)dst[1];

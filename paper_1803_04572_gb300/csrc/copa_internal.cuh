@@ -116,9 +116,13 @@ struct copa_ctx {
   const int64_t* sched_key = nullptr;
   int64_t sched_K = 0;
   int64_t sched_S = 0;
-  // copa_fit_host device copies
+  // copa_fit_host device copies: [0..3] X as the last call left it, [4..9] the state,
+  // [10..13] the X arrays of the current call before the comparison, [14] a flag
   void* host_slot_ptr[16] = {nullptr};
   size_t host_slot_bytes[16] = {0};
+  bool host_x_valid = false;   // [0..3] hold the X of the last copa_fit_host call
+  int64_t host_K = -1, host_J = -1, host_S = -1, host_nnz = -1;
+  int host_vdt = -1;
   // CUDA graph of one outer iteration
   cudaGraphExec_t graph_exec = nullptr;
   uint64_t graph_key = 0;
@@ -212,6 +216,11 @@ inline TuneChoice active_tune(const copa_ctx* h, const TensorView& X, int R) {
 }
 
 copa_status_t ws_get(copa_ctx* h, int slot, size_t bytes, void** out);
+// Drops everything the handle (and its batch children) derived from a tensor's contents:
+// subject schedule, warm-start offsets and rotations, column-sorted copy, row maps, tuned
+// schedule. The caches are keyed by device address and sizes, which a tensor rewritten in
+// place (or a new one at a freed one's address) does not change.
+void forget_tensor_caches(copa_ctx* h);
 copa_status_t fail(copa_ctx* h, copa_status_t code, const std::string& msg);
 copa_status_t cuda_check(copa_ctx* h, cudaError_t e, const char* what);
 TensorView view_of(const copa_tensor_t* X);

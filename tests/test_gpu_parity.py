@@ -742,6 +742,80 @@ def test_host_entry_point_matches_device_fit(P):
     np.testing.assert_allclose(Vh, Vt.cpu().numpy(), atol=1e-3 * np.abs(Vh).max())
 
 
+def _same_sizes_other_contents():
+    """A tensor and the same visits with the subjects in reverse order: equal K, J, S and
+    nnz, other subject sizes (on both sides of 32 rows) at each position."""
+    X = synth.ehr_custom(300, 120, median=12, lo=1, hi=90, lam=3.0, cmax=20, seed=5)
+    Xr = X.subset(np.arange(X.K)[::-1])
+    assert X.nnz == Xr.nnz and X.S == Xr.S and not np.array_equal(X.subj_ptr, Xr.subj_ptr)
+    return X, Xr
+
+
+def _assert_same_fit(a, b):
+    hist_a, fac_a = a
+    hist_b, fac_b = b
+    np.testing.assert_allclose(hist_a, hist_b, rtol=1e-10, atol=1e-12)
+    for x, y in zip(fac_a, fac_b):
+        np.testing.assert_allclose(x, y, rtol=0, atol=1e-9 * np.abs(y).max())
+
+
+def test_host_entry_point_follows_a_changed_tensor(P):
+    """copa_fit_host compares the uploaded tensor with the previous call's on the device.
+    Called again with the same tensor it keeps the schedule, the column-sorted copy and the
+    warm start (fewer set-up launches); called with a tensor of the same sizes but other
+    contents it rebuilds them, and the fit equals that of a fresh handle."""
+    X, Xr = _same_sizes_other_contents()
+    R = 8
+    H0, V0, W0 = synth.init_factors(X.K, X.J, R)
+    opt = P.Options(R, n_outer=2, n_inner=5)
+
+    def run(h, Xh):
+        fac = tuple(np.array(a, dtype=np.float64) for a in (H0, V0, W0))
+        hist = h.fit_host(Xh, opt, *fac)
+        return (hist, fac), h.fit_launches()
+
+    ha = P.Copa(0, "fp64")
+    _, l_first = run(ha, X)
+    _, l_again = run(ha, X)
+    got, l_changed = run(ha, Xr)
+    ref, l_fresh = run(P.Copa(0, "fp64"), Xr)
+    assert 0 < l_again < l_first
+    assert l_changed == l_fresh == l_first
+    _assert_same_fit(got, ref)
+
+
+def test_forget_tensor_after_rewrite_in_place(P):
+    """A device tensor rewritten in place keeps its addresses and sizes; after
+    forget_tensor() the fit on it equals a fresh handle's. A new DeviceTensor object (which
+    may sit at a freed one's addresses) does the same without the call."""
+    torch = pytest.importorskip("torch")
+    X, Xr = _same_sizes_other_contents()
+    R = 8
+    H0, V0, W0 = synth.init_factors(X.K, X.J, R)
+    opt = P.Options(R, n_outer=3, n_inner=5)
+
+    def run(h, Xd):
+        fac = tuple(torch.as_tensor(np.array(a, dtype=np.float64), device=h.device) for a in (H0, V0, W0))
+        hist = h.fit(Xd, opt, *fac)
+        return hist, tuple(N(t) for t in fac)
+
+    hf = P.Copa(0, "fp64")
+    ref = run(hf, P.DeviceTensor.from_host(Xr, hf.device, "f64"))
+    h = P.Copa(0, "fp64")
+    Xd = P.DeviceTensor.from_host(X, h.device, "f64")
+    run(h, Xd)
+    src = P.DeviceTensor.from_host(Xr, h.device, "f64")
+    for dst_t, src_t in ((Xd.subj_ptr, src.subj_ptr), (Xd.row_ptr, src.row_ptr), (Xd.col, src.col),
+                         (Xd.vals, src.vals)):
+        dst_t.copy_(src_t)
+    h.forget_tensor()
+    _assert_same_fit(run(h, Xd), ref)
+    # a new object for the original tensor, then again for the reversed one
+    del Xd, src
+    run(h, P.DeviceTensor.from_host(X, h.device, "f64"))
+    _assert_same_fit(run(h, P.DeviceTensor.from_host(Xr, h.device, "f64")), ref)
+
+
 def test_tensor_core_wait_timeout_is_reported(P):
     """The bounded mbarrier waits of the tensor-core V-mode kernel: a test hook makes the
     first wait of every CTA run out (an mbarrier that nothing arrives at, 2 ms). The kernel

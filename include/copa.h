@@ -305,10 +305,13 @@ copa_status_t copa_fit_plain(copa_handle_t handle, const copa_tensor_t* X, const
  *                  1 <= split <= min(R, 32) (default min(R, 32));
  *   blocks_per_sm  cap on the resident blocks per SM of those persistent kernels (0 = as
  *                  many as fit, the default);
- *   fv_path        F_V by the row-order kernel (0, default where it applies) or over the
- *                  column-sorted copy of X (1).
+ *   fv_path        F_V (mixed precision) by the row-order kernel with the sums in L2 (2,
+ *                  the default; R a multiple of 4, 2, or R <= 32), by the row-order kernel
+ *                  with shared-memory sums (0; J x 32 floats must fit), or over the
+ *                  column-sorted copy of X (1). A path that does not apply falls back to
+ *                  the next in that order.
  * copa_tune times the candidates (every split in {min(R,32), 24, 16, 8} below min(R,32) with
- * blocks_per_sm in {0, 2}; then both F_V kernels) on X with the factors H, V, W, with CUDA
+ * blocks_per_sm in {0, 2}; then the F_V kernels that apply) on X with the factors H, V, W, with CUDA
  * events on the handle's stream, and keeps the fastest: in a process-wide table keyed by
  * copa_tune_key(R, precision, size histogram) and on the handle, whose later calls on the
  * same X (same subj_ptr, K, S) and R use it. A key already in the table is applied without
@@ -328,7 +331,7 @@ copa_status_t copa_tune(copa_handle_t handle, const copa_tensor_t* X, int32_t R,
 copa_status_t copa_tune_key(const int64_t* subj_ptr_host, int64_t K, int32_t R, int32_t precision,
                             uint64_t* key);
 /* Table access (host only): lookup sets *found (0/1) and, if found, *out; store inserts or
- * replaces (split >= 1, blocks_per_sm >= 0, fv_path 0 or 1, else COPA_ERR_INVALID_ARG). */
+ * replaces (split >= 1, blocks_per_sm >= 0, fv_path 0, 1 or 2, else COPA_ERR_INVALID_ARG). */
 copa_status_t copa_tune_lookup(uint64_t key, int32_t* found, copa_tune_t* out);
 copa_status_t copa_tune_store(uint64_t key, const copa_tune_t* choice);
 

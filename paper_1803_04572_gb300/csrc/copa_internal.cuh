@@ -200,13 +200,14 @@ copa_status_t get_warm_offsets(copa_ctx* h, const TensorView& X, int R, const in
 
 // The schedule knobs of the Procrustes and V-mode launches: subjects with I_k > split take
 // the tall-subject kernels; bps caps the resident blocks per SM of the persistent
-// Procrustes kernels (0: as many as fit); fv = 1 takes the column-sorted F_V kernel where
-// the row-order one would apply. Defaults unless copa_tune chose them for (X, R).
+// Procrustes kernels (0: as many as fit); fv selects the F_V kernel: 2 (default) row order
+// with the sums in L2, 0 row order with shared-memory sums, 1 the column-sorted copy (each
+// falls back to the next that applies). Defaults unless copa_tune chose them for (X, R).
 struct TuneChoice {
   int split, bps, fv;
 };
 inline TuneChoice active_tune(const copa_ctx* h, const TensorView& X, int R) {
-  TuneChoice c{R < 32 ? R : 32, 0, 0};
+  TuneChoice c{R < 32 ? R : 32, 0, 2};
   if (h->tune_valid && h->tune_ptr == X.subj_ptr && h->tune_K == X.K && h->tune_S == X.S && h->tune_R == R) {
     c.split = h->tune_split;
     c.bps = h->tune_bps;

@@ -1149,6 +1149,81 @@ __global__ void k_reduce_fv(const float* __restrict__ part, int nblocks, int npa
   }
 }
 
+// F_V in row order with the sums kept in L2 instead of shared memory: the lanes of a warp
+// take VW-wide slices of the U rows of 32 / (R / VW) nonzeros at a time (VW the largest of
+// 4, 2, 1 dividing R) and add x u_i into a partial copy of F_V (FP32, one per group of
+// CTAs, small enough to stay in L2) with vector reductions, so that every column of U is
+// read in one pass, whatever J is.
+constexpr int kRedT = 512;   // threads per CTA
+template <int VW> struct RedVec;
+template <> struct RedVec<4> {
+  static __device__ __forceinline__ void add(float* dst, const float* src, float x) {
+    const float4 u = __ldg(reinterpret_cast<const float4*>(src));
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(x * u.x), "f"(x * u.y),
+                 "f"(x * u.z), "f"(x * u.w)
+                 : "memory");
+  }
+};
+template <> struct RedVec<2> {
+  static __device__ __forceinline__ void add(float* dst, const float* src, float x) {
+    const float2 u = __ldg(reinterpret_cast<const float2*>(src));
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(dst), "f"(x * u.x), "f"(x * u.y) : "memory");
+  }
+};
+template <> struct RedVec<1> {
+  static __device__ __forceinline__ void add(float* dst, const float* src, float x) {
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(dst), "f"(x * __ldg(src)) : "memory");
+  }
+};
+
+template <int VW>
+__global__ void __launch_bounds__(kRedT) k_spmm_rows_red(TensorView X, int R, const float* __restrict__ U,
+                                                           const int32_t* __restrict__ nzrow, float* __restrict__ part,
+                                                           int nparts) {
+  constexpr unsigned kFull = 0xffffffffu;
+  constexpr int nw = kRedT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int qv = R / VW, per = 32 / qv;   // lanes per nonzero (<= 32), nonzeros per step
+  const int sub = lane / qv, cv = lane - sub * qv;
+  const bool act = sub < per;
+  const int64_t per_cta = (X.nnz + gridDim.x - 1) / gridDim.x;
+  const int64_t p0 = min(X.nnz, (int64_t)blockIdx.x * per_cta), p1 = min(X.nnz, p0 + per_cta);
+  float* Fp = part + (size_t)(blockIdx.x % nparts) * (size_t)X.J * R;
+  constexpr int64_t step = (int64_t)nw * 32;
+  for (int64_t base = p0 + (int64_t)warp * 32; base < p1; base += step) {
+    const int64_t p = base + lane;
+    const bool v = p < p1;
+    const int jj = v ? __ldg(X.col + p) : 0;
+    const float xx = v ? load_valf(X, p) : 0.f;
+    const int ii = v ? __ldg(nzrow + p) : 0;
+    const int cnt = (int)min((int64_t)32, p1 - base);
+#pragma unroll 2
+    for (int q = 0; q < cnt; q += per) {
+      const int src = q + sub;
+      const int j = __shfl_sync(kFull, jj, src & 31);
+      const float x = __shfl_sync(kFull, xx, src & 31);
+      const int i = __shfl_sync(kFull, ii, src & 31);
+      if (act && src < cnt) RedVec<VW>::add(Fp + (int64_t)j * R + VW * cv, U + (int64_t)i * R + VW * cv, x);
+    }
+  }
+}
+
+static int red_width(int R) { return R % 4 == 0 ? 4 : (R % 2 == 0 ? 2 : 1); }
+
+// F(e) = sum over the nparts partial copies of element e, in FP64.
+template <typename Real>
+__global__ void k_reduce_fv_red(const float* __restrict__ part, int nparts, int64_t n, Real* __restrict__ F) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += gridDim.x * (int64_t)blockDim.x) {
+    double acc = 0.0;
+    for (int b = 0; b < nparts; ++b) acc += (double)part[(size_t)b * n + e];
+    F[e] = (Real)acc;
+  }
+}
+
+static bool spmm_red_applies(int R, const TensorView& X) {
+  return R <= 32 * red_width(R) && X.nnz < (int64_t)INT32_MAX && X.S < (int64_t)INT32_MAX;
+}
+
 // Shared memory the row-order F_V kernel needs (J x 32 floats); the path is taken when it fits.
 static size_t spmm_rows_smem(int J) { return sizeof(float) * 32 * (size_t)J; }
 static bool spmm_rows_fits(const copa_ctx* h, const TensorView& X) {
@@ -1197,16 +1272,20 @@ copa_status_t launch_mttkrp_v(copa_ctx* h, const TensorView& X, int R, const Rea
   const int32_t* nzrow = nullptr;
   // F_V in row order (FP32, when J x 32 floats fit in shared memory), else over the
   // column-sorted copy of X
-  bool rows_fv = false;
-  if constexpr (std::is_same<Real, float>::value) rows_fv = spmm_rows_fits(h, X) && active_tune(h, X, R).fv != 1;
-  if (rows_fv) {
+  bool rows_fv = false, red_fv = false;
+  if constexpr (std::is_same<Real, float>::value) {
+    const int fv = active_tune(h, X, R).fv;
+    red_fv = fv == 2 && spmm_red_applies(R, X);
+    rows_fv = !red_fv && spmm_rows_fits(h, X) && fv != 1;
+  }
+  if (rows_fv || red_fv) {
     if ((st = get_rowmaps(h, X, reuse_csc, &nzrow, &rsubj)) != COPA_OK) return st;
   } else if ((st = get_csc<Real>(h, X, reuse_csc, &cptr, &crow, &cval, &rsubj)) != COPA_OK) {
     return st;
   }
   Real* U = nullptr;
   if ((st = ws_get(h, SLOT_UVEC, sizeof(Real) * ((size_t)X.S * R + 16), (void**)&U)) != COPA_OK) return st;
-  if (!rows_fv &&
+  if (!rows_fv && !red_fv &&
       (st = cuda_check(h, cudaMemsetAsync(F, 0, sizeof(Real) * (size_t)X.J * R, h->stream), "memset F")) != COPA_OK)
     return st;
   double* part = nullptr;
@@ -1255,7 +1334,29 @@ copa_status_t launch_mttkrp_v(copa_ctx* h, const TensorView& X, int R, const Rea
     kern<<<(unsigned)blocks, kUNT, smem, h->stream>>>(X, R, Q, H, W, U, part, order, counter + 1);
     if ((st = cuda_check(h, cudaGetLastError(), "k_uvec")) != COPA_OK) return st;
   }
-  if (rows_fv) {
+  if (red_fv) {
+    if constexpr (std::is_same<Real, float>::value) {
+      const int vw = red_width(R);
+      auto kern = vw == 4 ? k_spmm_rows_red<4> : (vw == 2 ? k_spmm_rows_red<2> : k_spmm_rows_red<1>);
+      int per_sm = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRedT, 0);
+      const int fblocks = h->num_sms * std::max(per_sm, 1);
+      // partial copies: one per SM, fewer if that would exceed 64 MB
+      const int64_t jr = (int64_t)X.J * R;
+      const int nparts_fv = (int)std::max<int64_t>(1, std::min<int64_t>(h->num_sms, (64ll << 20) / (4 * jr)));
+      float* fpart = nullptr;
+      if ((st = ws_get(h, SLOT_FV_PART, sizeof(float) * (size_t)nparts_fv * jr + 16, (void**)&fpart)) != COPA_OK)
+        return st;
+      if ((st = cuda_check(h, cudaMemsetAsync(fpart, 0, sizeof(float) * (size_t)nparts_fv * jr, h->stream),
+                           "memset")) != COPA_OK)
+        return st;
+      kern<<<fblocks, kRedT, 0, h->stream>>>(X, R, U, nzrow, fpart, nparts_fv);
+      if ((st = cuda_check(h, cudaGetLastError(), "k_spmm_rows_red")) != COPA_OK) return st;
+      const int rb = (int)std::max<int64_t>(1, std::min<int64_t>((jr + 255) / 256, 4096));
+      k_reduce_fv_red<Real><<<rb, 256, 0, h->stream>>>(fpart, nparts_fv, jr, F);
+      if ((st = cuda_check(h, cudaGetLastError(), "k_reduce_fv_red")) != COPA_OK) return st;
+    }
+  } else if (rows_fv) {
     if constexpr (std::is_same<Real, float>::value) {
       const int npass = (R + 31) / 32;
       const int fblocks = std::max(1, h->num_sms);

@@ -92,11 +92,13 @@ copa_status_t tune_impl(copa_ctx* h, const TensorView& X, int R, const Real* H, 
       }
     }
   }
-  // the F_V kernel (both apply in FP32 with J x 32 floats in shared memory)
-  best->fv_path = 0;
+  // the F_V kernel (FP32): row order with shared-memory sums (J x 32 floats), over the
+  // column-sorted copy, or row order with the sums in L2
+  best->fv_path = 2;
   if (std::is_same<Real, float>::value) {
-    float t_path[2] = {0.f, 0.f};
-    for (int fv = 0; fv < 2; ++fv) {
+    float t_path[3] = {INFINITY, INFINITY, INFINITY};
+    const int n_fv = 3;
+    for (int fv = 0; fv < n_fv; ++fv) {
       copa_tune_t c = *best;
       c.fv_path = fv;
       apply(h, X, R, c);
@@ -105,7 +107,8 @@ copa_status_t tune_impl(copa_ctx* h, const TensorView& X, int R, const Real* H, 
            }, &t_path[fv])) != COPA_OK)
         return st;
     }
-    best->fv_path = t_path[1] < t_path[0] ? 1 : 0;
+    for (int fv = 0; fv < n_fv; ++fv)
+      if (t_path[fv] < t_path[best->fv_path]) best->fv_path = fv;
     best->ms += t_path[best->fv_path];
   }
   return COPA_OK;
@@ -149,7 +152,7 @@ extern "C" copa_status_t copa_tune_lookup(uint64_t key, int32_t* found, copa_tun
 }
 
 extern "C" copa_status_t copa_tune_store(uint64_t key, const copa_tune_t* choice) {
-  if (!choice || choice->split < 1 || choice->blocks_per_sm < 0 || choice->fv_path < 0 || choice->fv_path > 1)
+  if (!choice || choice->split < 1 || choice->blocks_per_sm < 0 || choice->fv_path < 0 || choice->fv_path > 2)
     return COPA_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lock(g_tune_mu);
   g_tune_table[key] = *choice;

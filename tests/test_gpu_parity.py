@@ -307,6 +307,32 @@ def test_mttkrp_steps(h, P, case):
         assert rel(N(FW), O.mttkrp_W(sl, H2, V)) <= tol
 
 
+@pytest.mark.parametrize("case", [CASES[2], (30, 1700, 40, 20, 1, 80), (40, 90, 12, 20, 1, 80)])
+def test_mttkrp_v_every_fv_path(P, case):
+    """F_V of the mixed handle by each of its kernels (row order with shared-memory sums,
+    column-sorted copy, row order with the sums in L2), chosen through the schedule table,
+    element by element against the oracle."""
+    h = P.Copa(0, "mixed")
+    K, J, R, med, lo, hi = case
+    X, H, V, W = make_case(K, J, R, med, lo, hi, seed=2)
+    H, V, W = inputs_for(h, H, V, W)
+    Xd = dev_tensor(h, P, X)
+    Q, st = oracle_state(h, X, H, V, W)
+    Qr = [q.astype(np.float32).astype(np.float64) for q in Q]
+    sl = O.project_all(X, Qr)
+    sl_abs = O.project_all(X, [np.abs(q) for q in Qr])
+    H2, _, W2 = inputs_for(h, *synth.random_state(X.K, X.J, R, seed=98))
+    key = P.tune_key(X.subj_ptr, R, "mixed")
+    ref = O.mttkrp_V(sl, H2, W2, X.J)
+    mag = O.mttkrp_V(sl_abs, np.abs(H2), np.abs(W2), X.J)
+    for fv in (0, 1, 2):
+        P.tune_store(key, split=min(R, 32), blocks_per_sm=0, fv_path=fv)
+        assert h.tune(Xd, R, T(h, H), T(h, V), T(h, W))["fv_path"] == fv
+        FV, _ = h.mttkrp("V", Xd, R, st, H=T(h, H2), W=T(h, W2), want_utu=True)
+        h.sync()
+        assert_elementwise(N(FV), ref, mag, TOL["mixed"], f"F_V path {fv}")
+
+
 def _admm_margins(F, G, Zb0, D0, n_inner, kind, lam):
     """The oracle's ADMM run one inner iteration at a time, returning the final state and,
     per element, the smallest relative distance |v^2 - 2 lam/rho| / (2 lam/rho) of the prox

@@ -47,8 +47,10 @@ def test_tune_table_store_and_lookup():
     assert P.tune_lookup(key)["split"] == 7 and P.tune_lookup(key)["fv_path"] == 0
     with pytest.raises(P.CopaError):
         P.tune_store(key, split=0)
+    P.tune_store(key, split=3, fv_path=2)
+    assert P.tune_lookup(key)["fv_path"] == 2
     with pytest.raises(P.CopaError):
-        P.tune_store(key, split=3, fv_path=2)
+        P.tune_store(key, split=3, fv_path=3)
 
 
 @pytest.mark.gpu

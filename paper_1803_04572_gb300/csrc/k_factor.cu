@@ -808,13 +808,49 @@ __global__ void __launch_bounds__(256) k_admm_w(const Real* __restrict__ T,
 }
 
 // W update for R <= 48, batched: a block takes kWS subjects at once and runs every inner
-// iteration as one small GEMM Z = (G + rho I)^{-1} B over the tile (B = F_W + rho (Wbar + D)
-// column by subject), so Ginv is read from shared memory once per tile and iteration
+// iteration as one small GEMM Z = (G + rho I)^{-1} B over the tile (B = F_W + rho (Wbar + D),
+// a row per subject), so Ginv is read from shared memory once per tile and iteration
 // instead of once per subject. A thread owns NC components of two subjects (state in
-// registers). F_W(k, s) = sum_r H(r, s) T_k(r, s) comes first, one warp per subject with
-// coalesced reads of T_k.
+// registers); Ginv and B sit in shared memory with 16-byte aligned, zero-padded rows, read
+// with vector loads along the contraction. F_W(k, s) = sum_r H(r, s) T_k(r, s) comes
+// first, one warp per subject with coalesced (FP32, R % 4 == 0: float4 streaming) reads of
+// T_k.
 constexpr int kWS = 64;      // subjects per block
 constexpr int kWNTH = 256;   // threads per block
+
+// 16-byte loads from shared memory (4 floats or 2 doubles)
+template <typename Real>
+struct V16;
+template <>
+struct V16<float> {
+  static constexpr int n = 4;
+  static __device__ __forceinline__ void ld(const float* p, float* o) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+};
+template <>
+struct V16<double> {
+  static constexpr int n = 2;
+  static __device__ __forceinline__ void ld(const double* p, double* o) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    o[0] = v.x; o[1] = v.y;
+  }
+};
+
+// Shared memory of k_admm_w_tiled: Ginv (R rows, stride RP + VN), B (kWS subject rows, same
+// stride), H (R x R), F_W (R x (kWS + 1)); RP = R rounded up to the vector width VN.
+template <typename Real>
+__host__ __device__ inline int wt_rp(int R) {
+  constexpr int VN = 16 / (int)sizeof(Real);
+  return (R + VN - 1) / VN * VN;
+}
+template <typename Real>
+__host__ __device__ inline size_t wt_smem_elems(int R) {
+  constexpr int VN = 16 / (int)sizeof(Real);
+  const int ld = wt_rp<Real>(R) + VN;
+  return (size_t)R * ld + (size_t)kWS * ld + (size_t)R * R + (size_t)R * (kWS + 1);
+}
 
 template <typename Real, int NC>
 __global__ void __launch_bounds__(kWNTH) k_admm_w_tiled(const Real* __restrict__ T, const Real* __restrict__ H,
@@ -822,30 +858,74 @@ __global__ void __launch_bounds__(kWNTH) k_admm_w_tiled(const Real* __restrict__
                                                         const double* __restrict__ rho_dev, int n_inner, int c,
                                                         double lam, Real* __restrict__ Wbar, Real* __restrict__ DW,
                                                         int64_t K, int R) {
+  using Vl = V16<Real>;
+  constexpr int VN = Vl::n;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int ldg = R + 1;
-  Real* Gs = reinterpret_cast<Real*>(smem_raw);   // R x (R+1): Ginv
-  Real* Hs = Gs + R * ldg;                         // R x R
+  const int RP = wt_rp<Real>(R), ld = RP + VN;
+  Real* Gs = reinterpret_cast<Real*>(smem_raw);   // R x ld: Ginv, zero-padded
+  Real* Bq = Gs + R * ld;                          // kWS x ld: B, row per subject, zero-padded
+  Real* Hs = Bq + kWS * ld;                        // R x R
   constexpr int ldw = kWS + 1;                     // odd stride: conflict-free columns
-  Real* Bs = Hs + R * R;                           // R x ldw: B, column per subject
-  Real* Fs = Bs + R * ldw;                         // R x ldw: F_W
+  Real* Fs = Hs + R * R;                           // R x ldw: F_W
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int sr = tid & 7, kc = tid >> 3;           // components sr*NC.., subjects 2kc, 2kc+1
-  for (int e = tid; e < R * ldg; e += kWNTH) Gs[e] = Ginv[e];
+  for (int e = tid; e < R * ld; e += kWNTH) {
+    const int r = e / ld, t = e - r * ld;
+    Gs[e] = t < R ? Ginv[r * (R + 1) + t] : Real(0);
+  }
+  for (int e = tid; e < kWS * ld; e += kWNTH) Bq[e] = Real(0);
   for (int e = tid; e < R * R; e += kWNTH) Hs[e] = H[e];
   const double rho = *rho_dev;
   const Real rr = (Real)rho, lor = (Real)(lam / rho);
   for (int64_t k0 = (int64_t)blockIdx.x * kWS; k0 < K; k0 += (int64_t)gridDim.x * kWS) {
     const int nk = (int)min((int64_t)kWS, K - k0);
     __syncthreads();   // Gs/Hs ready; the previous tile's reads of Fs/Bs are done
-    for (int q = warp; q < kWS; q += kWNTH / 32) {
-      for (int s = lane; s < R; s += 32) {
-        Real acc = Real(0);
-        if (q < nk) {
-          const Real* Tk = T + (k0 + q) * R * R;
-          for (int r = 0; r < R; ++r) acc += Hs[r * R + s] * Tk[r * R + s];
+    if (std::is_same<Real, float>::value && R % 4 == 0) {
+      // FP32, R % 4 == 0: lanes take float4 slices of 32 / (R / 4) rows of T_k at a time
+      // (independent streaming loads), then add up the row groups by shuffles
+      const int q4 = R >> 2, per = 32 / q4, rg = lane / q4, c4 = lane - rg * q4;
+      for (int q = warp; q < kWS; q += kWNTH / 32) {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (q < nk && rg < per) {
+          const float4* T4 = reinterpret_cast<const float4*>(T + (k0 + q) * R * R);
+          const float4* H4 = reinterpret_cast<const float4*>(Hs);
+#pragma unroll 4
+          for (int r = rg; r < R; r += per) {
+            const float4 t = __ldcs(T4 + r * q4 + c4), hv = H4[r * q4 + c4];
+            acc.x += t.x * hv.x;
+            acc.y += t.y * hv.y;
+            acc.z += t.z * hv.z;
+            acc.w += t.w * hv.w;
+          }
         }
-        Fs[s * ldw + q] = acc;
+        for (int o = 1; o < per; ++o) {
+          const int src = min(lane + o * q4, 31);
+          const float ax = __shfl_sync(0xffffffffu, acc.x, src), ay = __shfl_sync(0xffffffffu, acc.y, src),
+                      az = __shfl_sync(0xffffffffu, acc.z, src), aw = __shfl_sync(0xffffffffu, acc.w, src);
+          if (rg == 0) {
+            acc.x += ax;
+            acc.y += ay;
+            acc.z += az;
+            acc.w += aw;
+          }
+        }
+        if (rg == 0) {
+          Fs[(4 * c4) * ldw + q] = (Real)acc.x;
+          Fs[(4 * c4 + 1) * ldw + q] = (Real)acc.y;
+          Fs[(4 * c4 + 2) * ldw + q] = (Real)acc.z;
+          Fs[(4 * c4 + 3) * ldw + q] = (Real)acc.w;
+        }
+      }
+    } else {
+      for (int q = warp; q < kWS; q += kWNTH / 32) {
+        for (int s = lane; s < R; s += 32) {
+          Real acc = Real(0);
+          if (q < nk) {
+            const Real* Tk = T + (k0 + q) * R * R;
+            for (int r = 0; r < R; ++r) acc += Hs[r * R + s] * Tk[r * R + s];
+          }
+          Fs[s * ldw + q] = acc;
+        }
       }
     }
     __syncthreads();
@@ -866,23 +946,34 @@ __global__ void __launch_bounds__(kWNTH) k_admm_w_tiled(const Real* __restrict__
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
           const int s = sr * NC + a;
-          if (s < R) Bs[s * ldw + 2 * kc + b] = f[a][b] + rr * (zb[a][b] + d[a][b]);
+          if (s < R) Bq[(2 * kc + b) * ld + s] = f[a][b] + rr * (zb[a][b] + d[a][b]);
         }
       __syncthreads();
       Real z[NC][2];
 #pragma unroll
       for (int a = 0; a < NC; ++a) z[a][0] = z[a][1] = Real(0);
-      for (int t = 0; t < R; ++t) {
-        const Real b0 = Bs[t * ldw + 2 * kc], b1 = Bs[t * ldw + 2 * kc + 1];
+      for (int t = 0; t < RP; t += VN) {
+        Real b0[VN], b1[VN];
+        Vl::ld(Bq + (2 * kc) * ld + t, b0);
+        Vl::ld(Bq + (2 * kc + 1) * ld + t, b1);
 #pragma unroll
         for (int a = 0; a < NC; ++a) {
           const int s = sr * NC + a;
-          const Real g = s < R ? Gs[s * ldg + t] : Real(0);
-          z[a][0] += g * b0;
-          z[a][1] += g * b1;
+          Real g[VN];
+          if (s < R) {
+            Vl::ld(Gs + s * ld + t, g);
+          } else {
+#pragma unroll
+            for (int v = 0; v < VN; ++v) g[v] = Real(0);
+          }
+#pragma unroll
+          for (int v = 0; v < VN; ++v) {
+            z[a][0] += g[v] * b0[v];
+            z[a][1] += g[v] * b1[v];
+          }
         }
       }
-      __syncthreads();   // every read of Bs is done before the next iteration writes it
+      __syncthreads();   // every read of B is done before the next iteration writes it
 #pragma unroll
       for (int a = 0; a < NC; ++a)
 #pragma unroll
@@ -1463,7 +1554,7 @@ copa_status_t launch_admm_w(copa_ctx* h, const Real* T, const Real* H, const Rea
       case 5: kern = k_admm_w_tiled<Real, 5>; break;
       default: kern = k_admm_w_tiled<Real, 6>; break;
     }
-    const size_t tsm = sizeof(Real) * ((size_t)R * (R + 1) + (size_t)R * R + 2 * (size_t)R * (kWS + 1));
+    const size_t tsm = sizeof(Real) * wt_smem_elems<Real>(R);
     if ((st = cuda_check(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm),
                          "cudaFuncSetAttribute")) != COPA_OK)
       return st;

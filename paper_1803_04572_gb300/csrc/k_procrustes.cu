@@ -33,8 +33,8 @@ namespace copa {
 
 namespace {
 
-constexpr int kNT = 128;          // threads per CTA (one subject)
-constexpr int kNW = kNT / 32;     // warps per CTA = rows handled at once
+constexpr int kNT = 128;          // threads per CTA (one subject); 256 for R > 64
+constexpr int kNWMax = 8;         // most warps per CTA (rows handled at once)
 constexpr int kMaxSweeps = 30;
 // After a sweep whose rotations all had |tan| below this, the next sweep would most likely
 // only confirm convergence; the Jacobi kernels test every pair once from shared memory
@@ -94,10 +94,10 @@ __host__ __device__ inline Lay lay_of(int R) {
   L.Zb = o; o += 2 * m;
   L.Pb = o; o += m;
   L.Ub = o; o += m;
-  L.rv = o; o += (size_t)kNW * 3 * R;   // per-warp p, a, q vectors of one row
+  L.rv = o; o += (size_t)kNWMax * 3 * R;   // per-warp p, a, q vectors of one row
   L.al = o; o += R;
   L.vb = o; o += R + 1;
-  L.misc = o; o += 8 + kNW;
+  L.misc = o; o += 8 + kNWMax;
   L.total = o;
   return L;
 }
@@ -230,7 +230,7 @@ __device__ __forceinline__ void vec_times_mat(const Real* __restrict__ p, const 
 // Householder QR update of the stacked [R_A (R x R, rows 0..R-1 of Z); block (nb rows,
 // rows R..R+nb-1 of Z)]: afterwards Z[0..R-1] holds the new R factor and the block is 0.
 // Thread c owns column c; warp 0 forms each reflector.
-template <typename Real>
+template <typename Real, int NT>
 __device__ void tsqr_block(Real* Z, int ld, int R, int nb, Real* vb, Real* misc) {
   const int tid = threadIdx.x, lane = tid & 31;
   for (int j = 0; j < R; ++j) {
@@ -262,7 +262,7 @@ __device__ void tsqr_block(Real* Z, int ld, int R, int nb, Real* vb, Real* misc)
     __syncthreads();
     const Real tau = misc[0];
     if (tau != Real(0)) {
-      for (int c = j + 1 + threadIdx.x; c < R; c += kNT) {
+      for (int c = j + 1 + threadIdx.x; c < R; c += NT) {
         Real w0 = Z[j * ld + c], w1 = Real(0);
         int i = 0;
         for (; i + 1 < nb; i += 2) {
@@ -317,8 +317,8 @@ __device__ void mgs2_rows_block(Real* U, int m, int ld, Real* red) {
 // the block with LP = 128 / pairs threads per pair (a power of two), each thread holding
 // R / LP components of the two vectors and the pair's dot products reduced by shuffles;
 // one barrier per round.
-template <typename Real>
-__global__ void __launch_bounds__(kNT, 5) k_procrustes(
+template <typename Real, int NT>
+__global__ void __launch_bounds__(NT, NT == 128 ? 5 : 2) k_procrustes(
     TensorView X, int R, const Real* __restrict__ H, const Real* __restrict__ V,
     const Real* __restrict__ W, double tau_rank, Real* __restrict__ Q, Real* T,
     Real* __restrict__ Pi, int32_t* __restrict__ rank, double* __restrict__ fh_partial,
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(kNT, 5) k_procrustes(
 
   double* fh = fh_partial ? fh_partial + (size_t)blockIdx.x * R * R : nullptr;
   if (fh)
-    for (int i = tid; i < R * R; i += kNT) fh[i] = 0.0;
+    for (int i = tid; i < R * R; i += NT) fh[i] = 0.0;
 
   while (true) {
     __syncthreads();
@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(kNT, 5) k_procrustes(
     }
 
     // ---- E = S_k H^T; tall: clear R_A ----
-    for (int e = tid; e < R * R; e += kNT) {
+    for (int e = tid; e < R * R; e += NT) {
       const int r = e / R, t = e - r * R;
       Es[r * ld + t] = W[k * R + r] * __ldg(H + t * R + r);
       if (!wide) Zb[r * ld + t] = Real(0);
@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(kNT, 5) k_procrustes(
     //      tall: fill a QR block of up to R rows, then fold it into R_A ----
     int nb = 0;   // rows in the QR block (tall); always < R before a group
     for (int64_t g = r0; g < r1;) {
-      int nrow = (int)min((int64_t)kNW, r1 - g);
+      int nrow = (int)min((int64_t)(NT / 32), r1 - g);
       if (!wide && nrow > R - nb) nrow = R - nb;   // the block holds at most R rows
       const int64_t i = g + warp;
       if (warp < nrow) {
@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(kNT, 5) k_procrustes(
       if (!wide) {
         nb += nrow;
         if (nb == R || g >= r1) {
-          tsqr_block<Real>(Zb, ld, R, nb, vb, misc);
+          tsqr_block<Real, NT>(Zb, ld, R, nb, vb, misc);
           nb = 0;
         }
       }
@@ -413,21 +413,21 @@ __global__ void __launch_bounds__(kNT, 5) k_procrustes(
     const bool accU = wide;
     Real* Uk = (wide && Uw) ? Uw + woff[k] : nullptr;
     if (accU) {
-      for (int e = tid; e < m * m; e += kNT) {
+      for (int e = tid; e < m * m; e += NT) {
         const int r = e / m, t = e - r * m;
         Ub[r * ld + t] = (Uk && warm_in) ? Uk[e] : ((r == t) ? Real(1) : Real(0));
       }
       __syncthreads();
       if (Uk && warm_in && epoch && ((unsigned)__ldg(epoch) % kReorth) == 0u) mgs2_rows_block<Real>(Ub, m, ld, misc);
       if (Uk && warm_in) {
-        for (int e = tid; e < m * R; e += kNT) {
+        for (int e = tid; e < m * R; e += NT) {
           const int i = e / R, t = e - i * R;
           Real acc = Real(0);
           for (int j = 0; j < m; ++j) acc += Ub[i * ld + j] * Zb[j * ld + t];
           Zb[(R + i) * ld + t] = acc;
         }
         __syncthreads();
-        for (int e = tid; e < m * R; e += kNT) {
+        for (int e = tid; e < m * R; e += NT) {
           const int i = e / R, t = e - i * R;
           Zb[i * ld + t] = Zb[(R + i) * ld + t];
         }
@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(kNT, 5) k_procrustes(
     const int n2 = m + (m & 1);
     const int npairs = n2 / 2;
     int LP = 1;
-    while (LP < 32 && npairs * LP * 2 <= kNT) LP <<= 1;
+    while (LP < 32 && npairs * LP * 2 <= NT) LP <<= 1;
     const int pj = tid / LP, sl = tid % LP;
     const bool act = pj < npairs;
     const bool few = (R + LP - 1) / LP <= kEPL && (m + LP - 1) / LP <= kEPL;
@@ -540,10 +540,10 @@ __global__ void __launch_bounds__(kNT, 5) k_procrustes(
       if (nrot == 0) break;
     }
     if (Uk)
-      for (int e = tid; e < m * m; e += kNT) Uk[e] = Ub[(e / m) * ld + (e % m)];
+      for (int e = tid; e < m * m; e += NT) Uk[e] = Ub[(e / m) * ld + (e % m)];
 
     // ---- singular values, rank cut, normalised right singular vectors c_j ----
-    for (int j = tid; j < m; j += kNT) {
+    for (int j = tid; j < m; j += NT) {
       Real acc = Real(0);
       for (int t = 0; t < R; ++t) acc += Zb[j * ld + t] * Zb[j * ld + t];
       al[j] = acc;
@@ -563,7 +563,7 @@ __global__ void __launch_bounds__(kNT, 5) k_procrustes(
       if (rank && lane == 0) rank[k] = kept;
     }
     __syncthreads();
-    for (int e = tid; e < m * R; e += kNT) {
+    for (int e = tid; e < m * R; e += NT) {
       const int j = e / R, t = e - j * R;
       Zb[j * ld + t] *= al[j];
     }
@@ -572,7 +572,7 @@ __global__ void __launch_bounds__(kNT, 5) k_procrustes(
     Real* Tk = T + k * R * R;
     if (wide) {
       // Q rows q_i = sum_j U[j][i] c_j; B = U P -> rows R.. of Zb
-      for (int e = tid; e < m * R; e += kNT) {
+      for (int e = tid; e < m * R; e += NT) {
         const int i = e / R, t = e - i * R;
         Real acc = Real(0), bacc = Real(0);
         for (int j = 0; j < m; ++j) {
@@ -583,7 +583,7 @@ __global__ void __launch_bounds__(kNT, 5) k_procrustes(
         Zb[(R + i) * ld + t] = bacc;
       }
       __syncthreads();
-      for (int e = tid; e < R * R; e += kNT) {
+      for (int e = tid; e < R * R; e += NT) {
         const int r = e / R, s = e - r * R;
         Real acc = Real(0), pacc = Real(0);
         for (int j = 0; j < m; ++j) {
@@ -596,7 +596,7 @@ __global__ void __launch_bounds__(kNT, 5) k_procrustes(
       }
     } else {
       // Omega = sum_j c_j c_j^T / sigma_j -> Pb; Pi -> global
-      for (int e = tid; e < R * R; e += kNT) {
+      for (int e = tid; e < R * R; e += NT) {
         const int r = e / R, t = e - r * R;
         Real acc = Real(0), pacc = Real(0);
         for (int j = 0; j < R; ++j) {
@@ -610,9 +610,9 @@ __global__ void __launch_bounds__(kNT, 5) k_procrustes(
       }
       __syncthreads();
       // pass 2, rows four at a time: q_i = (p_i E) Omega; T_k += q_i^T p_i
-      for (int64_t g = r0; g < r1; g += kNW) {
+      for (int64_t g = r0; g < r1; g += (NT / 32)) {
         const int64_t i = g + warp;
-        const int nrow = (int)min((int64_t)kNW, r1 - g);
+        const int nrow = (int)min((int64_t)(NT / 32), r1 - g);
         if (warp < nrow) {
           row_times_v<Real>(X, i, R, V, pvw);
           __syncwarp();
@@ -623,7 +623,7 @@ __global__ void __launch_bounds__(kNT, 5) k_procrustes(
           for (int t = lane; t < R; t += 32) Q[i * R + t] = qvw[t];
         }
         __syncthreads();
-        for (int e = tid; e < R * R; e += kNT) {
+        for (int e = tid; e < R * R; e += NT) {
           const int r = e / R, s = e - r * R;
           Real acc = Ub[r * ld + s];
           for (int w = 0; w < nrow; ++w) {
@@ -634,7 +634,7 @@ __global__ void __launch_bounds__(kNT, 5) k_procrustes(
         }
         __syncthreads();
       }
-      for (int e = tid; e < R * R; e += kNT) {
+      for (int e = tid; e < R * R; e += NT) {
         const int r = e / R, s = e - r * R;
         const Real acc = Ub[r * ld + s];
         Tk[e] = acc;
@@ -1877,16 +1877,19 @@ copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const R
                                 Real* Pi, int32_t* rank, Real* F_H, Real* Uw, const int64_t* woff,
                                 bool warm_in, const int* epoch) {
   const size_t smem = procrustes_smem<Real>(R);
-  if (R < 1 || R > kNT || smem > 227 * 1024)
+  if (R < 1 || R > 2 * kNT || smem > 227 * 1024)
     return fail(h, COPA_ERR_UNSUPPORTED, "Procrustes: R too large for shared memory at this precision");
   copa_status_t st;
-  if ((st = cuda_check(h, cudaFuncSetAttribute(k_procrustes<Real>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem), "cudaFuncSetAttribute")) != COPA_OK)
+  // block kernel: 256 threads above R = 64, where one CTA fills an SM's shared memory and
+  // the Jacobi pairs of a round need more threads (measured at K = 100k: R = 80 500 -> 334 ms
+  // per outer iteration; R = 56 and the FP64 handle are faster with 128)
+  const int nt = R > 64 ? 2 * kNT : kNT;
+  auto block_kern = nt == kNT ? k_procrustes<Real, kNT> : k_procrustes<Real, 2 * kNT>;
+  if ((st = cuda_check(h, cudaFuncSetAttribute(block_kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                       "cudaFuncSetAttribute")) != COPA_OK)
     return st;
   int per_sm = 0;
-  if ((st = cuda_check(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_procrustes<Real>,
-                                                                        kNT, smem),
+  if ((st = cuda_check(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, block_kern, nt, smem),
                        "occupancy")) != COPA_OK)
     return st;
   if (per_sm < 1) per_sm = 1;
@@ -1960,9 +1963,8 @@ copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const R
       if ((st = cuda_check(h, cudaGetLastError(), "F_H stream launch")) != COPA_OK) return st;
     }
   } else {
-    k_procrustes<Real><<<(unsigned)blocks, kNT, smem, h->stream>>>(X, R, H, V, W, tau, Q, T, Pi, rank, part, order,
-                                                                  counter, fma_count, Uw, woff, warm_in ? 1 : 0, epoch,
-                                                                  nullptr, nullptr);
+    block_kern<<<(unsigned)blocks, nt, smem, h->stream>>>(X, R, H, V, W, tau, Q, T, Pi, rank, part, order, counter,
+                                                         fma_count, Uw, woff, warm_in ? 1 : 0, epoch, nullptr, nullptr);
     if ((st = cuda_check(h, cudaGetLastError(), "k_procrustes launch")) != COPA_OK) return st;
   }
   if (F_H) {

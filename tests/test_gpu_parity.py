@@ -253,6 +253,16 @@ def test_procrustes_tall_subjects(h, P):
     _check_procrustes(h, P, X, H, V, W, 40)
 
 
+def test_procrustes_step_rank_80(P):
+    """R = 80 (mixed handle; the FP64 block kernel's shared memory holds R <= 56): the
+    256-thread block kernel on subjects of 1 to 40 visits, at the bars of
+    test_procrustes_step. (At R = 80 the synthetic subjects with more visits than R have
+    kappa_k above 1e3, where only the per-subject bound says anything.)"""
+    h = P.Copa(0, "mixed")
+    X, H, V, W = make_case(40, 800, 80, 12, 1, 40, seed=5)
+    _check_procrustes(h, P, X, H, V, W, 80)
+
+
 def _state_after_procrustes(X, H, V, W):
     Q = [O.procrustes(X.dense(k), V, W[k], H) for k in range(X.K)]
     return Q, O.project_all(X, Q)

@@ -205,9 +205,10 @@ copa_status_t get_warm_offsets(copa_ctx* h, const TensorView& X, int R, const in
 // falls back to the next that applies). Defaults unless copa_tune chose them for (X, R).
 struct TuneChoice {
   int split, bps, fv;
+  bool pair;   // two subjects of I_k <= 16 per warp in the warp-per-subject Procrustes path
 };
 inline TuneChoice active_tune(const copa_ctx* h, const TensorView& X, int R) {
-  TuneChoice c{R < 32 ? R : 32, 0, 2};
+  TuneChoice c{R < 32 ? R : 32, 0, 2, true};
   if (h->tune_valid && h->tune_ptr == X.subj_ptr && h->tune_K == X.K && h->tune_S == X.S && h->tune_R == R) {
     c.split = h->tune_split;
     c.bps = h->tune_bps;

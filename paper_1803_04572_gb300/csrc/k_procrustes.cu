@@ -685,7 +685,10 @@ __device__ __forceinline__ int row_p(const TensorView& X, int R, const Real* __r
 // under the rotations. Shared-memory rows have a 16-byte aligned stride, so that the
 // warp-wide (broadcast) row reads are vector loads; the stride is chosen so that the
 // lane-per-row vector stores of a quarter warp fall in distinct banks.
-// Outputs are the same as the block path's wide branch.
+// Outputs are the same as the block path's wide branch. With kSeg = 16 a warp takes two
+// subjects of I_k <= 16, one per half (lane = row within the half, partners and reductions
+// inside the half); both halves run the rounds of the larger, the outputs go out one subject
+// at a time. It runs the schedule's smallest subjects at half the instructions per subject.
 constexpr int kWNT = 128;   // threads per block of the warp path (4 subjects at a time)
 
 template <typename Real>
@@ -721,18 +724,19 @@ struct WarpLay {
   static constexpr int VN = Vec16<Real>::n;
   static constexpr int ld = kR + VN;             // row stride of the row buffers
   static constexpr int ldu = kM + 1;             // U: odd stride, read by columns
-  static constexpr int per_warp = 2 * kM * ld + kM * ldu + kR + VN;
+  static constexpr int per_warp = 2 * kM * ld + kM * ldu + 2 * kR + VN;   // two W rows (paired subjects)
   static constexpr size_t bytes = sizeof(Real) * ((size_t)kR * kR + (kWNT / 32) * (size_t)per_warp) + 16;
   static_assert(kM * ld + kM * ldu >= kR * kR && kM * ld + kM * ldu >= kM * kR,
                 "the B2 and U buffers stage T_k and the Q rows");
 };
 
-template <typename Real, int kR>
+template <typename Real, int kR, int kSeg>
 __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
     TensorView X, int R, const Real* __restrict__ H, const Real* __restrict__ V,
     const Real* __restrict__ W, double tau_rank, Real* __restrict__ Q, Real* __restrict__ T,
     Real* __restrict__ Pi, int32_t* __restrict__ rank,
-    const int64_t* __restrict__ order, const int* __restrict__ first, int* __restrict__ counter,
+    const int64_t* __restrict__ order, const int* __restrict__ first, const int* __restrict__ last,
+    int* __restrict__ counter,
     unsigned long long* __restrict__ fma_count, Real* __restrict__ Uw,
     const int64_t* __restrict__ woff, int warm_in, const int* __restrict__ epoch, int* __restrict__ status) {
   using Lw = WarpLay<Real, kR>;
@@ -743,39 +747,50 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* Hs = reinterpret_cast<Real*>(smem_raw);   // Hs[r * kR + t] = H(t, r), zero-padded
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // kSeg = 16: two subjects (I_k <= 16) per warp, one per half, lane = row within the half
+  constexpr int kMs = kM < kSeg ? kM : kSeg;   // rows of a subject
+  constexpr int kNS = 32 / kSeg;               // subjects per warp
+  static_assert(kSeg == 32 || kM == 32, "paired subjects need 32 buffer rows");
+  const int seg = lane / kSeg, sl = lane - seg * kSeg, sb = seg * kSeg;
+  const unsigned segmask = kSeg == 32 ? kFull : (0xffffu << sb);
   Real* B1 = Hs + kR * kR + (size_t)warp * Lw::per_warp;   // A rows, then c_j rows
   Real* B2 = B1 + kM * ld;                                  // p rows, then b = U P rows
   Real* Us = B2 + kM * ld;                                  // U, for its transpose
-  Real* Wb = Us + kM * ldu;                                 // this subject's row of W
+  Real* Wb = Us + kM * ldu;                                 // the subjects' rows of W
   for (int e = threadIdx.x; e < kR * kR; e += kWNT) {
     const int r = e / kR, t = e - r * kR;
     Hs[e] = (t < R && r < R) ? H[t * R + r] : Real(0);
   }
   __syncthreads();
   const Real tol = Tol<Real>::v();
-  const int64_t k0 = min((int64_t)max(*first, 0), X.K);
+  // schedule positions [first, last) (last NULL: to the end)
+  const int64_t k1 = last ? min((int64_t)max(*last, 0), X.K) : X.K;
+  const int64_t k0 = min((int64_t)max(*first, 0), k1);
   const int tr = lane >> 2, tc = lane & 3;
   unsigned long long fma = 0;
 
   while (true) {
     int claim = 0;
-    if (lane == 0) claim = atomicAdd(counter, 1);
-    const int64_t idx = k0 + __shfl_sync(kFull, claim, 0);
-    if (idx >= X.K) break;
-    const int64_t k = order[idx];
+    if (lane == 0) claim = atomicAdd(counter, kNS);
+    const int64_t idx0 = k0 + __shfl_sync(kFull, claim, 0);
+    if (idx0 >= k1) break;
+    const int64_t idx = idx0 + seg;
+    const bool has = idx < k1;   // a half without a subject runs on m = 0 and writes nothing
+    const int64_t k = order[has ? idx : idx0];
     const int64_t r0 = X.subj_ptr[k];
-    const int64_t ik = X.subj_ptr[k + 1] - r0;
-    if (ik > kM) {   // the schedule split guarantees I_k <= kM; record and skip otherwise
-      if (lane == 0) set_status(status, COPA_ERR_CUDA, (int)k);
-      continue;
-    }
-    const int m = (int)ik;
+    const int64_t ik = has ? X.subj_ptr[k + 1] - r0 : 0;
+    if (ik > kMs && sl == 0)   // the schedule split guarantees I_k <= kMs; record and skip
+      set_status(status, COPA_ERR_CUDA, (int)k);
+    const bool out = has && ik <= kMs;
+    const int m = out ? (int)ik : 0;
+    const int mmax = kNS == 1 ? m : __reduce_max_sync(kFull, m);
     const Real* wk = W + k * R;
-    for (int r = lane; r < kR; r += 32) Wb[r] = r < R ? wk[r] : Real(0);
+    Real* Wbs = Wb + seg * kR;
+    for (int r = sl; r < kR; r += kSeg) Wbs[r] = r < R ? wk[r] : Real(0);
 
     // ---- p_i = x_i V (lane i); a_i = (p_i * w) H^T ----
     Real p[kR];
-    const int nnz_row = row_p<Real, kR>(X, R, V, r0 + lane, lane < m, p);
+    const int nnz_row = row_p<Real, kR>(X, R, V, r0 + sl, sl < m, p);
     if (lane < kM) {
 #pragma unroll
       for (int t = 0; t < kR; t += VN) Vc::st(B2 + lane * ld + t, p + t);
@@ -784,10 +799,10 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
     Real z[kR];
 #pragma unroll
     for (int t = 0; t < kR; ++t) z[t] = Real(0);
-    if (lane < m) {
+    if (sl < m) {
 #pragma unroll 1
       for (int r = 0; r < R; ++r) {
-        const Real pw = B2[lane * ld + r] * Wb[r];
+        const Real pw = B2[lane * ld + r] * Wbs[r];
 #pragma unroll
         for (int t = 0; t < kR; t += VN) {
           Real hv[VN];
@@ -801,21 +816,21 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
     // ---- U: identity, or the previous outer iteration's rotation (then Z = U_prev A) ----
     Real* Uk = Uw ? Uw + woff[k] : nullptr;
     const bool warm = Uk != nullptr && warm_in != 0;
-    Real u[kM];
+    Real u[kMs];
 #pragma unroll
-    for (int j = 0; j < kM; ++j) u[j] = (!warm && j == lane && lane < m) ? Real(1) : Real(0);
+    for (int j = 0; j < kMs; ++j) u[j] = (!warm && j == sl && sl < m) ? Real(1) : Real(0);
     if (warm) {
       if (lane < kM) {
 #pragma unroll
         for (int t = 0; t < kR; t += VN) Vc::st(B1 + lane * ld + t, z + t);
       }
       // U_prev (m x m, contiguous) through Us: contiguous row copies, then lane = row
-      for (int r = 0; r < m; ++r)
-        if (lane < m) Us[r * ldu + lane] = Uk[r * m + lane];
+      for (int r = 0; r < mmax; ++r)
+        if (r < m && sl < m) Us[(sb + r) * ldu + sl] = Uk[r * m + sl];
       __syncwarp();
-      if (lane < m) {
+      if (sl < m) {
 #pragma unroll
-        for (int j = 0; j < kM; ++j)
+        for (int j = 0; j < kMs; ++j)
           if (j < m) u[j] = Us[lane * ldu + j];
       }
       if (epoch && ((unsigned)__ldg(epoch) % kReorth) == 0u) {
@@ -823,36 +838,38 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
 #pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
 #pragma unroll 1
-          for (int i = 0; i < m; ++i) {
+          for (int i = 0; i < mmax; ++i) {
+            const bool act = i < m;   // row i exists in this lane's subject
             Real ss = Real(0);
 #pragma unroll
-            for (int jj = 0; jj < kM; ++jj) ss += u[jj] * u[jj];
-            const Real inv = Real(1) / sqrt(__shfl_sync(kFull, ss, i));
+            for (int jj = 0; jj < kMs; ++jj) ss += u[jj] * u[jj];
+            const Real si = __shfl_sync(kFull, ss, sb + i);
+            const Real inv = act ? Real(1) / sqrt(si) : Real(0);
             Real d = Real(0);
 #pragma unroll
-            for (int jj = 0; jj < kM; ++jj) {
-              const Real ui = __shfl_sync(kFull, u[jj], i) * inv;
-              if (lane == i) u[jj] = ui;
+            for (int jj = 0; jj < kMs; ++jj) {
+              const Real ui = __shfl_sync(kFull, u[jj], sb + i) * inv;
+              if (act && sl == i) u[jj] = ui;
               d += u[jj] * ui;
             }
             // (lane i's d is its own squared norm, 1; it does not update)
-            const Real dd = lane > i && lane < m ? d : Real(0);
+            const Real dd = act && sl > i && sl < m ? d : Real(0);
 #pragma unroll
-            for (int jj = 0; jj < kM; ++jj) u[jj] -= dd * __shfl_sync(kFull, u[jj], i);
+            for (int jj = 0; jj < kMs; ++jj) u[jj] -= dd * __shfl_sync(kFull, u[jj], sb + i);
           }
         }
       }
       __syncwarp();
 #pragma unroll
       for (int t = 0; t < kR; ++t) z[t] = Real(0);
-      if (lane < m) {
+      if (sl < m) {
 #pragma unroll
-        for (int j = 0; j < kM; ++j) {
+        for (int j = 0; j < kMs; ++j) {
           if (j < m) {
 #pragma unroll
             for (int t = 0; t < kR; t += VN) {
               Real av[VN];
-              Vc::ld(B1 + j * ld + t, av);
+              Vc::ld(B1 + (sb + j) * ld + t, av);
 #pragma unroll
               for (int q = 0; q < VN; ++q) z[t + q] += u[j] * av[q];
             }
@@ -872,29 +889,30 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
 #pragma unroll
       for (int t = 0; t < kR; ++t) z[t] *= f;
 #pragma unroll
-      for (int jj = 0; jj < kM; ++jj) u[jj] *= f;
+      for (int jj = 0; jj < kMs; ++jj) u[jj] *= f;
     };
     Real al = Real(0), f = Real(1);
-    const int n2 = m + (m & 1);
+    const int n2 = m + (m & 1), n2max = mmax + (mmax & 1);
     unsigned long long nrot = 0;
     int sweeps = 0;
-    for (int sweep = 0; sweep < kMaxSweeps && n2 > 1; ++sweep) {
+    for (int sweep = 0; sweep < kMaxSweeps && n2max > 1; ++sweep) {
       ++sweeps;
       bool any = false;
       Real tmx = Real(0);   // largest |tan| of this lane's rotations in the sweep
       fold(f);
       f = Real(1);
       al = sq_sum<Real, kR>(z);
-      for (int rd = 0; rd < n2 - 1; ++rd) {
-        int j;
-        if (lane >= n2) j = lane;
-        else if (lane == n2 - 1) j = rd;
-        else if (lane == rd) j = n2 - 1;
+      for (int rd = 0; rd < n2max - 1; ++rd) {
+        int jl;   // partner row within the subject
+        if (sl >= n2 || rd >= n2 - 1) jl = sl;
+        else if (sl == n2 - 1) jl = rd;
+        else if (sl == rd) jl = n2 - 1;
         else {
-          j = 2 * rd - lane;
-          if (j < 0) j += n2 - 1;
-          else if (j >= n2 - 1) j -= n2 - 1;
+          jl = 2 * rd - sl;
+          if (jl < 0) jl += n2 - 1;
+          else if (jl >= n2 - 1) jl -= n2 - 1;
         }
+        const int j = sb + jl;
         Real zp[kR];
         Real g[4] = {Real(0), Real(0), Real(0), Real(0)};
 #pragma unroll
@@ -910,7 +928,7 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
         const unsigned rmask = __ballot_sync(kFull, rot);
         if (rmask == 0u) continue;
         any = true;
-        if (lane == 0) nrot += __popc(rmask) / 2;
+        nrot += __popc(rmask) / 2;
         // lower row x, upper row y: x' = c x - s y, y' = s x + c y; in the scaled form
         // the own row takes -+ t (fp / f) times the partner's and the scale takes c
         Real mu = Real(0);
@@ -927,8 +945,8 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
         }
         // U rows, in chunks of 8 entries up to m
 #pragma unroll
-        for (int c8 = 0; c8 < kM; c8 += 8) {
-          if (c8 < m) {
+        for (int c8 = 0; c8 < kMs; c8 += 8) {
+          if (c8 < mmax) {
 #pragma unroll
             for (int jj = c8; jj < c8 + 8; ++jj) {
               const Real up = __shfl_sync(kFull, u[jj], j);
@@ -951,19 +969,19 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
         }
         __syncwarp();
         bool bad = false;
-        if (lane < m) {
+        if (sl < m) {
 #pragma unroll 1
           for (int jj = 0; jj < m; ++jj) {
             Real g4[4] = {Real(0), Real(0), Real(0), Real(0)};
 #pragma unroll
             for (int t = 0; t < kR; t += VN) {
               Real rv[VN];
-              Vc::ld(B1 + jj * ld + t, rv);
+              Vc::ld(B1 + (sb + jj) * ld + t, rv);
 #pragma unroll
               for (int q = 0; q < VN; ++q) g4[(t + q) & 3] += z[t + q] * rv[q];
             }
             const Real gg = (g4[0] + g4[1]) + (g4[2] + g4[3]);
-            bad |= jj != lane && gg != Real(0) && fabs(gg) > tol * sqrt(al * Us[jj]);
+            bad |= jj != sl && gg != Real(0) && fabs(gg) > tol * sqrt(al * Us[sb + jj]);
           }
         }
         __syncwarp();
@@ -977,10 +995,12 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
     al = sq_sum<Real, kR>(z);
 
     // ---- rank cut; c_i = z_i / sigma_i for kept rows, 0 otherwise ----
-    const Real amax = warp_max(al);
-    const bool keep = lane < m && amax > Real(0) && (double)al > tau_rank * (double)amax;
-    const int kept = __popc(__ballot_sync(kFull, keep));
-    if (rank && lane == 0) rank[k] = kept;
+    Real amax = al;   // largest squared row norm of the subject
+#pragma unroll
+    for (int o = kSeg / 2; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(kFull, amax, o));
+    const bool keep = sl < m && amax > Real(0) && (double)al > tau_rank * (double)amax;
+    const int kept = __popc(__ballot_sync(kFull, keep) & segmask);
+    if (rank && sl == 0 && out) rank[k] = kept;
     const Real inv = keep ? rsqrt_(al) : Real(0);
     if (lane < kM) {
 #pragma unroll
@@ -988,26 +1008,26 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
 #pragma unroll
       for (int t = 0; t < kR; t += VN) Vc::st(B1 + lane * ld + t, z + t);
 #pragma unroll
-      for (int jj = 0; jj < kM; ++jj) Us[lane * ldu + jj] = u[jj];
+      for (int jj = 0; jj < kMs; ++jj) Us[lane * ldu + jj] = u[jj];
     }
     __syncwarp();
-    if (Uk) {   // this iteration's U for the next one: contiguous row copies from Us
+    if (Uk && out) {   // this iteration's U for the next one: contiguous row copies from Us
       for (int r = 0; r < m; ++r)
-        if (lane < m) Uk[r * m + lane] = Us[r * ldu + lane];
+        if (sl < m) Uk[r * m + sl] = Us[(sb + r) * ldu + sl];
     }
 
     // ---- q_i = sum_j U(j, i) c_j and b_i = sum_j U(i, j) p_j ----
 #pragma unroll
     for (int t = 0; t < kR; ++t) { z[t] = Real(0); p[t] = Real(0); }
-    if (lane < m) {
+    if (sl < m) {
 #pragma unroll 1
       for (int jj = 0; jj < m; ++jj) {
-        const Real uji = Us[jj * ldu + lane], uij = Us[lane * ldu + jj];
+        const Real uji = Us[(sb + jj) * ldu + sl], uij = Us[lane * ldu + jj];
 #pragma unroll
         for (int t = 0; t < kR; t += VN) {
           Real cv[VN], pv[VN];
-          Vc::ld(B1 + jj * ld + t, cv);
-          Vc::ld(B2 + jj * ld + t, pv);
+          Vc::ld(B1 + (sb + jj) * ld + t, cv);
+          Vc::ld(B2 + (sb + jj) * ld + t, pv);
 #pragma unroll
           for (int q = 0; q < VN; ++q) {
             z[t + q] += uji * cv[q];
@@ -1023,94 +1043,127 @@ __global__ void __launch_bounds__(kWNT, 3) k_procrustes_warp(
     }
     __syncwarp();
 
-    // ---- T_k = sum_j c_j^T b_j (lane tile kTR x kTC), optional Pi_k. T_k and the rows
-    //      q_i go out through shared memory (the B2 and U buffers, free by then), so that
-    //      the global stores are contiguous. ----
+    // ---- T_k = sum_j c_j^T b_j (lane tile kTR x kTC), optional Pi_k, one subject at a
+    //      time (the whole warp). With one subject per warp, T_k and the rows q_i go out
+    //      through shared memory (the B2 and U buffers, free by then), so that the global
+    //      stores are contiguous; with two, T_k and Pi_k go out from the tiles (rows of kTC
+    //      contiguous values) and the q rows of both subjects through shared memory. ----
     Real* St = B2;   // staging: B2 and Us are adjacent and hold >= max(R * R, kM * R) values
-    {
+#pragma unroll 1
+    for (int s2 = 0; s2 < kNS; ++s2) {
+      const int base = s2 * kSeg;
+      const int ms = kNS == 1 ? m : __shfl_sync(kFull, m, base);
+      const bool outs = kNS == 1 ? out : __shfl_sync(kFull, (int)out, base) != 0;
+      const int64_t ks = kNS == 1 ? k : __shfl_sync(kFull, (long long)k, base);
       Real acc[kTR][kTC];
 #pragma unroll
       for (int a = 0; a < kTR; ++a)
 #pragma unroll
         for (int b = 0; b < kTC; ++b) acc[a][b] = Real(0);
-      for (int jj = 0; jj < m; ++jj) {
+      for (int jj = 0; jj < ms; ++jj) {
         Real cr[kTR], bs[kTC];
 #pragma unroll
-        for (int a = 0; a < kTR; ++a) cr[a] = B1[jj * ld + tr * kTR + a];
+        for (int a = 0; a < kTR; ++a) cr[a] = B1[(base + jj) * ld + tr * kTR + a];
 #pragma unroll
-        for (int b = 0; b < kTC; ++b) bs[b] = B2[jj * ld + tc * kTC + b];
+        for (int b = 0; b < kTC; ++b) bs[b] = B2[(base + jj) * ld + tc * kTC + b];
 #pragma unroll
         for (int a = 0; a < kTR; ++a)
 #pragma unroll
           for (int b = 0; b < kTC; ++b) acc[a][b] += cr[a] * bs[b];
       }
-      __syncwarp();   // every lane is done reading B2
+      Real* Tk = T + ks * R * R;
+      if constexpr (kNS == 1) {
+        __syncwarp();   // every lane is done reading B2
 #pragma unroll
-      for (int a = 0; a < kTR; ++a) {
-        const int r = tr * kTR + a;
-        if (r < R) {
+        for (int a = 0; a < kTR; ++a) {
+          const int r = tr * kTR + a;
+          if (r < R) {
 #pragma unroll
-          for (int b = 0; b < kTC; ++b) {
-            const int s = tc * kTC + b;
-            if (s < R) St[r * R + s] = acc[a][b];
+            for (int b = 0; b < kTC; ++b) {
+              const int s = tc * kTC + b;
+              if (s < R) St[r * R + s] = acc[a][b];
+            }
+          }
+        }
+        __syncwarp();
+        if (outs)
+          for (int e = lane; e < R * R; e += 32) Tk[e] = St[e];
+        __syncwarp();
+      } else if (outs) {
+#pragma unroll
+        for (int a = 0; a < kTR; ++a) {
+          const int r = tr * kTR + a;
+          if (r < R) {
+#pragma unroll
+            for (int b = 0; b < kTC; ++b) {
+              const int s = tc * kTC + b;
+              if (s < R) Tk[r * R + s] = acc[a][b];
+            }
           }
         }
       }
-      __syncwarp();
-      Real* Tk = T + k * R * R;
-      for (int e = lane; e < R * R; e += 32) Tk[e] = St[e];
-      __syncwarp();
-      if (lane < m) {
-#pragma unroll
-        for (int t = 0; t < kR; ++t)
-          if (t < R) St[lane * R + t] = z[t];
-      }
-      __syncwarp();
-      Real* Qk = Q + r0 * R;
-      for (int e = lane; e < m * R; e += 32) Qk[e] = St[e];
-    }
-    if (Pi) {
-      Real acc[kTR][kTC];
-#pragma unroll
-      for (int a = 0; a < kTR; ++a)
-#pragma unroll
-        for (int b = 0; b < kTC; ++b) acc[a][b] = Real(0);
-      for (int jj = 0; jj < m; ++jj) {
-        Real cr[kTR], cs[kTC];
-#pragma unroll
-        for (int a = 0; a < kTR; ++a) cr[a] = B1[jj * ld + tr * kTR + a];
-#pragma unroll
-        for (int b = 0; b < kTC; ++b) cs[b] = B1[jj * ld + tc * kTC + b];
+      if (Pi) {
 #pragma unroll
         for (int a = 0; a < kTR; ++a)
 #pragma unroll
-          for (int b = 0; b < kTC; ++b) acc[a][b] += cr[a] * cs[b];
-      }
-      Real* Pk = Pi + k * R * R;
+          for (int b = 0; b < kTC; ++b) acc[a][b] = Real(0);
+        for (int jj = 0; jj < ms; ++jj) {
+          Real cr[kTR], cs[kTC];
 #pragma unroll
-      for (int a = 0; a < kTR; ++a) {
-        const int r = tr * kTR + a;
-        if (r < R) {
+          for (int a = 0; a < kTR; ++a) cr[a] = B1[(base + jj) * ld + tr * kTR + a];
 #pragma unroll
-          for (int b = 0; b < kTC; ++b) {
-            const int s = tc * kTC + b;
-            if (s < R) Pk[r * R + s] = acc[a][b];
+          for (int b = 0; b < kTC; ++b) cs[b] = B1[(base + jj) * ld + tc * kTC + b];
+#pragma unroll
+          for (int a = 0; a < kTR; ++a)
+#pragma unroll
+            for (int b = 0; b < kTC; ++b) acc[a][b] += cr[a] * cs[b];
+        }
+        if (outs) {
+          Real* Pk = Pi + ks * R * R;
+#pragma unroll
+          for (int a = 0; a < kTR; ++a) {
+            const int r = tr * kTR + a;
+            if (r < R) {
+#pragma unroll
+              for (int b = 0; b < kTC; ++b) {
+                const int s = tc * kTC + b;
+                if (s < R) Pk[r * R + s] = acc[a][b];
+              }
+            }
           }
         }
       }
     }
+    // the q rows, contiguous in Q, through St
+    __syncwarp();   // every lane is done reading B2
+    if (sl < m) {
+#pragma unroll
+      for (int t = 0; t < kR; ++t)
+        if (t < R) St[lane * R + t] = z[t];
+    }
+    __syncwarp();
+#pragma unroll 1
+    for (int s2 = 0; s2 < kNS; ++s2) {
+      const int base = s2 * kSeg;
+      const int ms = kNS == 1 ? m : __shfl_sync(kFull, m, base);
+      const int64_t r0s = kNS == 1 ? r0 : __shfl_sync(kFull, (long long)r0, base);
+      Real* Qk = Q + r0s * R;
+      for (int e = lane; e < ms * R; e += 32) Qk[e] = St[base * R + e];
+    }
     __syncwarp();
     if (fma_count) {
-      const int nnzk = __reduce_add_sync(kFull, nnz_row);
-      if (lane == 0) {
+      int nz = nnz_row;
+#pragma unroll
+      for (int o = kSeg / 2; o > 0; o >>= 1) nz += __shfl_xor_sync(kFull, nz, o);
+      if (sl == 0 && out) {
         const unsigned long long mm = (unsigned long long)m, RR = (unsigned long long)R * R;
-        fma += (unsigned long long)nnzk * R + mm * RR + 2ull * mm * R + 2ull * mm * mm * R + 2ull * RR * mm;
+        fma += (unsigned long long)nz * R + mm * RR + 2ull * mm * R + 2ull * mm * mm * R + 2ull * RR * mm;
         if (warm) fma += mm * mm * R;
-        fma += (unsigned long long)sweeps * (mm * (mm > 0 ? mm - 1 : 0) / 2) * 3 * R + nrot * 4 * (R + mm);
+        fma += (unsigned long long)sweeps * (mm * (mm > 0 ? mm - 1 : 0) / 2) * 3 * R + nrot / kNS * 4 * (R + mm);
       }
     }
   }
-  if (fma_count && lane == 0) atomicAdd(fma_count, fma);
+  if (fma_count && sl == 0) atomicAdd(fma_count, fma);
 }
 
 // ---- tall form (I_k > min(R, 32)), in three warp-per-subject launches ----
@@ -1780,7 +1833,7 @@ __global__ void __launch_bounds__(kFh4Threads) k_fh_stream4(int64_t K, int R, co
 
 template <typename Real>
 using WarpKernel = void (*)(TensorView, int, const Real*, const Real*, const Real*, double, Real*, Real*, Real*,
-                            int32_t*, const int64_t*, const int*, int*, unsigned long long*, Real*,
+                            int32_t*, const int64_t*, const int*, const int*, int*, unsigned long long*, Real*,
                             const int64_t*, int, const int*, int*);
 template <typename Real>
 using TallQrKernel = void (*)(TensorView, int, const Real*, const Real*, const Real*, const int64_t*, const int*, int*,
@@ -1796,6 +1849,7 @@ using TallPass2Kernel = void (*)(TensorView, int, const Real*, const Real*, cons
 template <typename Real>
 struct RowKernels {
   WarpKernel<Real> small = nullptr;
+  WarpKernel<Real> pair = nullptr;   // two subjects of I_k <= 16 per warp (kR >= 32)
   TallQrKernel<Real> qr = nullptr;
   TallJacobiKernel<Real> jac = nullptr;
   TallPass2Kernel<Real> pass2 = nullptr;
@@ -1805,7 +1859,8 @@ struct RowKernels {
 template <typename Real, int KR>
 RowKernels<Real> row_kernels_of() {
   RowKernels<Real> r;
-  r.small = k_procrustes_warp<Real, KR>;
+  r.small = k_procrustes_warp<Real, KR, 32>;
+  if constexpr (KR >= 32) r.pair = k_procrustes_warp<Real, KR, 16>;
   r.qr = k_tall_qr<Real, KR>;
   r.jac = k_tall_jacobi<Real, KR>;
   r.jac_smem = TallJLay<Real, KR>::bytes;
@@ -1913,6 +1968,11 @@ copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const R
   // I_k > split (min(R, 32) unless tuned lower) take the tall-subject kernels
   const int split = std::max(1, std::min(tc.split, std::min(R, 32)));
   const int* n_big = rows ? schedule_count_above(h, split) : nullptr;
+  // subjects with I_k <= 16 (and <= the split), two to a warp where the rows allow it
+  const bool pair = rows && rk.pair != nullptr && tc.pair;
+  const int* n_small = pair ? schedule_count_above(h, std::min(16, split)) : nullptr;
+  int64_t pair_blocks = 0;
+  if (pair && (st = row_grid(h, rk.pair, rk.small_smem, (X.K + 1) / 2, &pair_blocks, tc.bps)) != COPA_OK) return st;
   int* counter = nullptr;
   if ((st = ws_get(h, SLOT_COUNTER, 64, (void**)&counter)) != COPA_OK) return st;
   unsigned long long* fma_count = reinterpret_cast<unsigned long long*>(counter + 2);
@@ -1938,7 +1998,7 @@ copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const R
   }
   // counter[0]: block kernel, [2..3]: work tally, [4]: small subjects, [5]: tall QR, [6]: tall pass 2,
   // [7]: tall Jacobi
-  if ((st = cuda_check(h, cudaMemsetAsync(counter, 0, 32, h->stream), "memset")) != COPA_OK)
+  if ((st = cuda_check(h, cudaMemsetAsync(counter, 0, 64, h->stream), "memset")) != COPA_OK)
     return st;
   if (rows) {
     rk.qr<<<(unsigned)qblocks, kWNT, rk.qr_smem, h->stream>>>(X, R, H, V, W, order, n_big, counter + 5, T, fma_count);
@@ -1950,9 +2010,15 @@ copa_status_t launch_procrustes(copa_ctx* h, const TensorView& X, int R, const R
                                                                      fma_count);
     if ((st = cuda_check(h, cudaGetLastError(), "k_tall_pass2 launch")) != COPA_OK) return st;
     rk.small<<<(unsigned)sblocks, kWNT, rk.small_smem, h->stream>>>(
-        X, R, H, V, W, tau, Q, T, Pi, rank, order, n_big, counter + 4, fma_count, Uw, woff,
+        X, R, H, V, W, tau, Q, T, Pi, rank, order, n_big, n_small, counter + 4, fma_count, Uw, woff,
         warm_in ? 1 : 0, epoch, h->d_status);
     if ((st = cuda_check(h, cudaGetLastError(), "k_procrustes_warp launch")) != COPA_OK) return st;
+    if (pair) {
+      rk.pair<<<(unsigned)pair_blocks, kWNT, rk.small_smem, h->stream>>>(
+          X, R, H, V, W, tau, Q, T, Pi, rank, order, n_small, nullptr, counter + 8, fma_count, Uw, woff,
+          warm_in ? 1 : 0, epoch, h->d_status);
+      if ((st = cuda_check(h, cudaGetLastError(), "k_procrustes_warp (paired) launch")) != COPA_OK) return st;
+    }
     if (F_H && X.K > 0) {
       if constexpr (std::is_same<Real, float>::value) {
         if (fh4) k_fh_stream4<<<(unsigned)fblocks, kFh4Threads, 0, h->stream>>>(X.K, R, T, W, part);

@@ -162,11 +162,28 @@ class DeviceTensor:
                        _ptr(self.col), _ptr(self.vals), VAL_DTYPE[self.val_dtype])
 
 
+def bf16_bits(values) -> np.ndarray:
+    """The bf16 bit patterns (uint16) of integer counts |x| <= 256, for host tensors whose
+    values are passed as val_dtype "bf16" (exact for such counts; half the bytes of f32)."""
+    import torch
+    v = torch.as_tensor(np.ascontiguousarray(values, dtype=np.float32))
+    if not bool(torch.all((v == torch.round(v)) & (v.abs() <= 256))):
+        raise ValueError("bf16 values must be integers of magnitude <= 256")
+    return v.to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+
+
 def host_tensor_c(X, val_dtype="f32"):
-    """TensorC over HOST numpy arrays (for copa_fit_host); returns (struct, keep-alive)."""
-    dt = {"f32": np.float32, "f64": np.float64}[val_dtype]
+    """TensorC over HOST numpy arrays (for copa_fit_host); returns (struct, keep-alive).
+    val_dtype "bf16": X.val holds bf16 bit patterns (a 2-byte integer array, see bf16_bits)."""
+    if val_dtype == "bf16":
+        val = np.asarray(X.val)
+        if val.dtype.itemsize != 2 or val.dtype.kind not in "ui":
+            raise ValueError("val_dtype bf16 takes the values as bf16 bit patterns (uint16), see bf16_bits")
+        val = np.ascontiguousarray(val)
+    else:
+        val = np.ascontiguousarray(X.val, dtype={"f32": np.float32, "f64": np.float64}[val_dtype])
     arrs = [np.ascontiguousarray(X.subj_ptr, dtype=np.int64), np.ascontiguousarray(X.row_ptr, dtype=np.int64),
-            np.ascontiguousarray(X.col, dtype=np.int32), np.ascontiguousarray(X.val, dtype=dt)]
+            np.ascontiguousarray(X.col, dtype=np.int32), val]
     if len(arrs[0]) != X.K + 1:
         raise ValueError("subj_ptr must have K + 1 entries")
     tc = TensorC(X.K, X.J, len(arrs[1]) - 1, len(arrs[2]), *(a.ctypes.data for a in arrs),

@@ -60,3 +60,28 @@ def test_host_tensor_sizes_from_arrays():
     X = synth.ehr_custom(9, 6, median=5, lo=2, hi=9, seed=2)
     tc, keep = P.host_tensor_c(X, "f32")
     assert (tc.K, tc.J, tc.S, tc.nnz) == (X.K, X.J, X.S, X.nnz)
+
+
+def test_bf16_host_values():
+    """bf16_bits gives the bf16 patterns of integer counts and refuses anything else; the
+    host tensor for copa_fit_host takes them as val_dtype "bf16" and nothing wider."""
+    import numpy as np
+    import pytest
+    _build()
+    import paper_1803_04572_gb300 as P
+    b = P.bf16_bits(np.array([1.0, 2.0, 50.0, 256.0, -3.0]))
+    assert b.dtype == np.uint16
+    assert list(b) == [0x3F80, 0x4000, 0x4248, 0x4380, 0xC040]
+    with pytest.raises(ValueError):
+        P.bf16_bits(np.array([1.5]))
+    with pytest.raises(ValueError):
+        P.bf16_bits(np.array([257.0]))
+    X = type("Xh", (), {})()
+    X.K, X.J = 1, 4
+    X.subj_ptr, X.row_ptr = np.array([0, 1]), np.array([0, 2])
+    X.col, X.val = np.array([0, 3]), b[:2]
+    tc, _ = P.host_tensor_c(X, "bf16")
+    assert tc.nnz == 2 and tc.val_dtype == P.VAL_DTYPE["bf16"]
+    X.val = np.array([1.0, 2.0], dtype=np.float32)
+    with pytest.raises(ValueError):
+        P.host_tensor_c(X, "bf16")

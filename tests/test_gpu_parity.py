@@ -778,6 +778,26 @@ def test_host_entry_point_matches_device_fit(P):
     np.testing.assert_allclose(Vh, Vt.cpu().numpy(), atol=1e-3 * np.abs(Vh).max())
 
 
+def test_host_entry_point_bf16_counts(P):
+    """copa_fit_host with the counts passed as bf16 bit patterns (half the bytes) gives the
+    fit of the same counts passed as f32."""
+    X = synth.ehr_custom(200, 60, median=12, lo=1, hi=60, lam=3.0, cmax=20, seed=8)
+    R = 8
+    H0, V0, W0 = synth.init_factors(X.K, X.J, R)
+    opt = P.Options(R, n_outer=3, n_inner=5)
+    hists = []
+    for vd in ("f32", "bf16"):
+        h = P.Copa(0, "fp64")
+        Xh = type("Xh", (), {})()
+        Xh.K, Xh.J, Xh.subj_ptr, Xh.row_ptr, Xh.col = X.K, X.J, X.subj_ptr, X.row_ptr, X.col
+        Xh.val = P.bf16_bits(X.val) if vd == "bf16" else X.val
+        fac = tuple(np.array(a, dtype=np.float64) for a in (H0, V0, W0))
+        hists.append((h.fit_host(Xh, opt, *fac, val_dtype=vd), fac))
+    np.testing.assert_allclose(hists[1][0], hists[0][0], rtol=1e-10, atol=1e-12)
+    for a, b in zip(hists[1][1], hists[0][1]):
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-9 * np.abs(b).max())
+
+
 def _same_sizes_other_contents():
     """A tensor and the same visits with the subjects in reverse order: equal K, J, S and
     nnz, other subject sizes (on both sides of 32 rows) at each position."""

@@ -115,12 +115,22 @@ __device__ __forceinline__ double fdiv_(double a, double b) { return a / b; }
 // Jacobi rotation (c, s) that makes the pair with squared norms aa, bb and dot product gg
 // orthogonal: x' = c x - s y, y' = s x + c y. Then |x'|^2 = aa - t gg and |y'|^2 = bb + t gg
 // with t = s / c (returned in *t).
+// The tangent is the smaller root of t^2 + 2 zeta t - 1 = 0, zeta = (bb - aa) / (2 gg), in
+// the form t = sign(h) gg / (|h| + sqrt(h^2 + gg^2)), h = (bb - aa) / 2, which needs one
+// division fewer on the dependent path of a Jacobi round; where h^2 + gg^2 overflows it
+// falls back to the form in zeta.
 template <typename Real>
 __device__ __forceinline__ void rotation_of(Real aa, Real bb, Real gg, Real* c, Real* s, Real* t = nullptr) {
-  const Real zeta = fdiv_(bb - aa, Real(2) * gg);
+  const Real h = Real(0.5) * (bb - aa);
+  const Real q = h * h + gg * gg;
   Real tt;
-  if (fabs(zeta) > Real(1e15)) tt = fdiv_(Real(0.5), zeta);
-  else tt = fdiv_(zeta >= Real(0) ? Real(1) : Real(-1), fabs(zeta) + sqrt_r(Real(1) + zeta * zeta));
+  if (isfinite(q)) {
+    tt = fdiv_(h >= Real(0) ? gg : -gg, fabs(h) + sqrt_r(q));
+  } else {
+    const Real zeta = fdiv_(bb - aa, Real(2) * gg);
+    if (fabs(zeta) > Real(1e15)) tt = fdiv_(Real(0.5), zeta);
+    else tt = fdiv_(zeta >= Real(0) ? Real(1) : Real(-1), fabs(zeta) + sqrt_r(Real(1) + zeta * zeta));
+  }
   *c = rsqrt_(Real(1) + tt * tt);
   *s = *c * tt;
   if (t) *t = tt;

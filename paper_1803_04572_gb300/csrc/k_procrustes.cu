@@ -1298,10 +1298,13 @@ __global__ void __launch_bounds__(kWNT, sizeof(Real) == 4 ? 4 : 3) k_tall_qr(
         const Real x0 = Rs[j * ldr + j];
         Real tau = Real(0), scale = Real(0), beta = x0;
         if (ss > Real(0)) {
-          const Real nrm = sqrt(x0 * x0 + ss);
+          // (FP32: x rsqrt(x) and approximate reciprocals, as in the rotation set-up; the
+          // reflector is formed from them consistently, v = x / (x0 - beta) with tau from
+          // the same beta)
+          const Real nrm = sqrt_r(x0 * x0 + ss);
           beta = x0 >= Real(0) ? -nrm : nrm;
-          tau = (beta - x0) / beta;
-          scale = Real(1) / (x0 - beta);
+          tau = fdiv_(beta - x0, beta);
+          scale = fdiv_(Real(1), x0 - beta);
         }
         if (tau != Real(0)) {
           Real v[32];

@@ -674,6 +674,25 @@ __device__ __forceinline__ int row_p(const TensorView& X, int R, const Real* __r
       c[u] = in ? __ldg(X.col + q0 + u) : 0;
       x[u] = in ? load_x<Real>(X, q0 + u) : Real(0);
     }
+    if constexpr (std::is_same<Real, float>::value && kR % 4 == 0) {
+      if ((R & 3) == 0) {   // 16-byte rows of V: float4 loads
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float4* vr = reinterpret_cast<const float4*>(V + (int64_t)c[u] * R);
+#pragma unroll
+          for (int t4 = 0; t4 < kR / 4; ++t4) {
+            if (4 * t4 < R) {
+              const float4 v = __ldg(vr + t4);
+              p[4 * t4] += x[u] * v.x;
+              p[4 * t4 + 1] += x[u] * v.y;
+              p[4 * t4 + 2] += x[u] * v.z;
+              p[4 * t4 + 3] += x[u] * v.w;
+            }
+          }
+        }
+        continue;
+      }
+    }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const Real* vr = V + (int64_t)c[u] * R;

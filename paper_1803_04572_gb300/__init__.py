@@ -35,7 +35,7 @@ EXPORTED = ["copa_create", "copa_destroy", "copa_last_error", "copa_sync", "copa
             "copa_smooth_project", "copa_loss_grad", "copa_procrustes_work", "copa_gram_noalloc",
             "copa_fit_launches", "copa_debug_set", "copa_partition", "copa_set_allreduce", "copa_factor_U",
             "copa_fit_stats", "copa_fit_batch", "copa_tune", "copa_tune_key", "copa_tune_lookup",
-            "copa_tune_store", "copa_fit_plain", "copa_forget_tensor"]
+            "copa_tune_store", "copa_fit_plain", "copa_forget_tensor", "copa_stage_host"]
 KNOTS = {"uniform": 0, "quantile": 1}
 
 
@@ -89,6 +89,7 @@ _sig = {
     "copa_fit": [_V, POINTER(TensorC), POINTER(OptionsC), _V, _V, _V, _V, _V, _V, _V,
                  POINTER(ProcOutC)],
     "copa_fit_host": [_V, POINTER(TensorC), POINTER(OptionsC), _V, _V, _V, _V, _V, _V, _V],
+    "copa_stage_host": [_V, POINTER(TensorC)],
     "copa_smooth_plan": [_V, POINTER(TensorC), _V, c_int32, c_int32, c_int32, POINTER(c_int64),
                          POINTER(c_int64)],
     "copa_smooth_project": [_V, POINTER(TensorC), _V, c_int32, c_int32, c_int32, POINTER(TensorC), _V],
@@ -191,6 +192,11 @@ def host_tensor_c(X, val_dtype="f32"):
     return tc, arrs
 
 
+def _tensor_key(tc) -> tuple:
+    """What copa_fit_host matches a staged copy by: sizes, value type, host addresses."""
+    return (tc.K, tc.J, tc.S, tc.nnz, tc.val_dtype, tc.subj_ptr, tc.row_ptr, tc.col_idx, tc.vals)
+
+
 def partition(subj_ptr, row_ptr, nshards: int) -> np.ndarray:
     """copa_partition on host arrays: the first subject of each of nshards contiguous
     shards balanced by nonzeros (nshards + 1 bounds). Needs no GPU."""
@@ -258,6 +264,7 @@ class Copa:
         self._check(_lib.copa_create(byref(h), device, c_void_p(self.stream.cuda_stream), PREC[precision]), None)
         self.h = h
         self._last_serial = None
+        self._staged = []   # (key, arrays) of the pending copa_stage_host copies, oldest first
 
     def _xc(self, X: DeviceTensor) -> TensorC:
         """X's TensorC, after dropping the handle's caches if X is not the tensor of the last call."""
@@ -424,11 +431,24 @@ class Copa:
         DW = np.zeros_like(W) if DW is None else DW
         tc, keep = host_tensor_c(Xh, val_dtype)
         hist = np.zeros(max(1, opt.n_outer), dtype=np.float64)
+        # the library takes the oldest staged copy if it is of these arrays, else drops all
+        if self._staged and self._staged[0][0] == _tensor_key(tc):
+            taken = [self._staged.pop(0)]
+        else:
+            taken, self._staged = self._staged, []
         self._call(_lib.copa_fit_host, self.h, byref(tc), byref(opt.c()), H.ctypes.data, V.ctypes.data,
                                        W.ctypes.data, DH.ctypes.data, DV.ctypes.data, DW.ctypes.data,
                                        hist.ctypes.data)
-        del keep
+        del keep, taken
         return hist[:self.fit_stats(opt.n_outer)[0]]
+
+    def stage_host(self, Xh, val_dtype="f32"):
+        """copa_stage_host: start copying a host tensor for the next fit_host call with the
+        same arrays (pinned memory overlaps the copy with the work queued before it). The
+        arrays are kept referenced until that call, and must not be written meanwhile."""
+        tc, keep = host_tensor_c(Xh, val_dtype)
+        self._check(_lib.copa_stage_host(self.h, byref(tc)))
+        self._staged.append((_tensor_key(tc), keep))
 
     def smooth(self, X: DeviceTensor, days, n_basis=7, degree=3, out_dtype="f32", want_C=False,
                knots="quantile"):

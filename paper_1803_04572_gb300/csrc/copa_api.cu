@@ -440,7 +440,13 @@ static void release_ctx(copa_ctx* h, bool own_stream) {
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
   for (int i = 0; i < 20; ++i)
     if (h->slot_ptr[i]) cudaFree(h->slot_ptr[i]);
-  for (int i = 0; i < 16; ++i)
+  if (h->copy_stream) {   // staged copies still in flight read host memory: end them first
+    cudaStreamSynchronize(h->copy_stream);
+    cudaStreamDestroy(h->copy_stream);
+  }
+  for (cudaEvent_t e : h->stage_ev)
+    if (e) cudaEventDestroy(e);
+  for (int i = 0; i < copa_ctx::kHostSlots; ++i)
     if (h->host_slot_ptr[i]) cudaFree(h->host_slot_ptr[i]);
   cudaFree(h->d_status);
   if (own_stream) cudaStreamDestroy(h->stream);
@@ -1091,45 +1097,131 @@ copa_status_t copa_set_allreduce(copa_handle_t h, copa_allreduce_fn fn, void* us
   return COPA_OK;
 }
 
+namespace {
+
+// Bytes of the four arrays of a tensor (subj_ptr, row_ptr, col_idx, vals).
+void tensor_bytes(const copa_tensor_t* X, size_t out[4]) {
+  const size_t vs = X->val_dtype == COPA_VAL_F64 ? 8 : (X->val_dtype == COPA_VAL_F32 ? 4 : 2);
+  out[0] = sizeof(int64_t) * (X->K + 1);
+  out[1] = sizeof(int64_t) * (X->S + 1);
+  out[2] = sizeof(int32_t) * X->nnz;
+  out[3] = vs * X->nnz;
+}
+
+// Device buffer of at least `bytes` (+16) in host slot i; a smaller one is replaced.
+copa_status_t host_slot(copa_ctx* h, int i, size_t bytes) {
+  if (h->host_slot_bytes[i] < bytes + 16) {
+    if (h->host_slot_ptr[i]) cudaFree(h->host_slot_ptr[i]);
+    h->host_slot_ptr[i] = nullptr;
+    h->host_slot_bytes[i] = 0;
+    if (cudaMalloc(&h->host_slot_ptr[i], bytes + 16) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, COPA_ERR_OOM, "copa_fit_host: device allocation failed");
+    }
+    h->host_slot_bytes[i] = bytes + 16;
+  }
+  return COPA_OK;
+}
+
+bool staged_matches(const copa_ctx::StagedX& s, const copa_tensor_t* X) {
+  return s.K == X->K && s.J == X->J && s.S == X->S && s.nnz == X->nnz && s.vdt == X->val_dtype &&
+         s.src[0] == X->subj_ptr && s.src[1] == X->row_ptr && s.src[2] == X->col_idx && s.src[3] == X->vals;
+}
+
+// Waits for every pending staged copy and forgets them (their buffers stay allocated).
+copa_status_t drop_staged(copa_ctx* h) {
+  for (int q = 0; q < h->n_staged; ++q)
+    TRY(cuda_check(h, cudaEventSynchronize(h->stage_ev[h->staged[q].set]), "cudaEventSynchronize"));
+  h->n_staged = 0;
+  return COPA_OK;
+}
+
+}  // namespace
+
+copa_status_t copa_stage_host(copa_handle_t h, const copa_tensor_t* Xh) {
+  CHECK_H(h);
+  TRY(set_dev(h));
+  TRY(check_tensor_args(h, Xh));
+  if (h->n_staged >= 2) return fail(h, COPA_ERR_INVALID_ARG, "copa_stage_host: two staged copies are pending");
+  if (!h->copy_stream)
+    TRY(cuda_check(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking), "cudaStreamCreate"));
+  // the set that the pending copy (if any) does not use; its buffers are free: a set is
+  // reused only after copa_fit_host took its copy (and synchronised) or dropped it
+  const int set = h->n_staged == 1 ? 1 - h->staged[0].set : 0;
+  if (!h->stage_ev[set])
+    TRY(cuda_check(h, cudaEventCreateWithFlags(&h->stage_ev[set], cudaEventDisableTiming), "cudaEventCreate"));
+  size_t sizes[4];
+  tensor_bytes(Xh, sizes);
+  const void* src[4] = {Xh->subj_ptr, Xh->row_ptr, Xh->col_idx, Xh->vals};
+  for (int i = 0; i < 4; ++i) {
+    const int d = 15 + 4 * set + i;
+    TRY(host_slot(h, d, sizes[i]));
+    if (sizes[i])
+      TRY(cuda_check(h, cudaMemcpyAsync(h->host_slot_ptr[d], src[i], sizes[i], cudaMemcpyHostToDevice,
+                                        h->copy_stream),
+                     "H2D"));
+  }
+  TRY(cuda_check(h, cudaEventRecord(h->stage_ev[set], h->copy_stream), "cudaEventRecord"));
+  copa_ctx::StagedX& e = h->staged[h->n_staged++];
+  e.set = set;
+  for (int i = 0; i < 4; ++i) e.src[i] = src[i];
+  e.K = Xh->K;
+  e.J = Xh->J;
+  e.S = Xh->S;
+  e.nnz = Xh->nnz;
+  e.vdt = Xh->val_dtype;
+  return COPA_OK;
+}
+
 copa_status_t copa_fit_host(copa_handle_t h, const copa_tensor_t* Xh, const copa_options_t* opt, void* H_host,
                             void* V_host, void* W_host, void* DH_host, void* DV_host, void* DW_host,
                             double* fit_history_host) {
   CHECK_H(h);
   TRY(set_dev(h));
+  if (!Xh) return fail(h, COPA_ERR_INVALID_ARG, "X is NULL");
+  // First (before any check can fail, so that a caller can track the pending copies): if
+  // the oldest copy started by copa_stage_host is of this X (same host arrays and sizes),
+  // its buffers become slots 10..13 (the stream waits for its copies) and X is not copied
+  // again; otherwise every pending copy is waited for and discarded.
+  bool took = false;
+  if (h->n_staged > 0) {
+    if (staged_matches(h->staged[0], Xh)) {
+      const int set = h->staged[0].set;
+      TRY(cuda_check(h, cudaStreamWaitEvent(h->stream, h->stage_ev[set], 0), "cudaStreamWaitEvent"));
+      for (int q = 0; q < 4; ++q) {
+        std::swap(h->host_slot_ptr[10 + q], h->host_slot_ptr[15 + 4 * set + q]);
+        std::swap(h->host_slot_bytes[10 + q], h->host_slot_bytes[15 + 4 * set + q]);
+      }
+      h->staged[0] = h->staged[1];
+      --h->n_staged;
+      took = true;
+    } else {
+      TRY(drop_staged(h));
+    }
+  }
   TRY(check_tensor_args(h, Xh));
   TRY(check_options(h, opt));
   if (!H_host || !V_host || !W_host || !DH_host || !DV_host || !DW_host)
     return fail(h, COPA_ERR_INVALID_ARG, "copa_fit_host: NULL factor or dual");
   const size_t es = h->precision == COPA_PREC_MIXED ? sizeof(float) : sizeof(double);
-  const size_t vs = Xh->val_dtype == COPA_VAL_F64 ? 8 : (Xh->val_dtype == COPA_VAL_F32 ? 4 : 2);
   const int R = opt->R;
-  const size_t sizes[10] = {sizeof(int64_t) * (Xh->K + 1), sizeof(int64_t) * (Xh->S + 1),
-                            sizeof(int32_t) * Xh->nnz,      vs * Xh->nnz,
-                            es * R * R,                      es * (size_t)Xh->J * R,
-                            es * (size_t)Xh->K * R,          es * R * R,
-                            es * (size_t)Xh->J * R,          es * (size_t)Xh->K * R};
+  size_t sizes[10];
+  tensor_bytes(Xh, sizes);
+  sizes[4] = es * R * R;
+  sizes[5] = es * (size_t)Xh->J * R;
+  sizes[6] = es * (size_t)Xh->K * R;
+  sizes[7] = es * R * R;
+  sizes[8] = es * (size_t)Xh->J * R;
+  sizes[9] = es * (size_t)Xh->K * R;
   const void* src[10] = {Xh->subj_ptr, Xh->row_ptr, Xh->col_idx, Xh->vals, H_host, V_host, W_host,
                          DH_host,      DV_host,     DW_host};
-  auto slot = [&](int i, size_t bytes) -> copa_status_t {
-    if (h->host_slot_bytes[i] < bytes + 16) {
-      if (h->host_slot_ptr[i]) cudaFree(h->host_slot_ptr[i]);
-      h->host_slot_ptr[i] = nullptr;
-      h->host_slot_bytes[i] = 0;
-      if (cudaMalloc(&h->host_slot_ptr[i], bytes + 16) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(h, COPA_ERR_OOM, "copa_fit_host: device allocation failed");
-      }
-      h->host_slot_bytes[i] = bytes + 16;
-    }
-    return COPA_OK;
-  };
   // X goes to the staging slots 10..13 and is compared on the device with the copy in
   // slots 0..3 that the last call left there: the handle's caches derived from X (subject
   // schedule, warm-start rotations, column-sorted copy) are keyed by device address, so
   // they carry over to this call only if the contents are unchanged.
-  for (int i = 0; i < 10; ++i) {
+  for (int i = took ? 4 : 0; i < 10; ++i) {
     const int d = i < 4 ? 10 + i : i;
-    TRY(slot(d, sizes[i]));
+    TRY(host_slot(h, d, sizes[i]));
     if (sizes[i])
       TRY(cuda_check(h, cudaMemcpyAsync(h->host_slot_ptr[d], src[i], sizes[i], cudaMemcpyHostToDevice, h->stream),
                      "H2D"));
@@ -1138,7 +1230,7 @@ copa_status_t copa_fit_host(copa_handle_t h, const copa_tensor_t* Xh, const copa
               h->host_nnz == Xh->nnz && h->host_vdt == Xh->val_dtype;
   for (int i = 0; i < 4 && same; ++i) same = h->host_slot_bytes[i] >= sizes[i] + 16;
   if (same) {
-    TRY(slot(14, sizeof(int)));
+    TRY(host_slot(h, 14, sizeof(int)));
     int* flag = reinterpret_cast<int*>(h->host_slot_ptr[14]);
     TRY(cuda_check(h, cudaMemsetAsync(flag, 0, sizeof(int), h->stream), "memset"));
     ByteCmp c;

@@ -117,9 +117,23 @@ struct copa_ctx {
   int64_t sched_K = 0;
   int64_t sched_S = 0;
   // copa_fit_host device copies: [0..3] X as the last call left it, [4..9] the state,
-  // [10..13] the X arrays of the current call before the comparison, [14] a flag
-  void* host_slot_ptr[16] = {nullptr};
-  size_t host_slot_bytes[16] = {0};
+  // [10..13] the X arrays of the current call before the comparison, [14] a flag,
+  // [15..18] and [19..22] the two sets of copa_stage_host copies
+  static constexpr int kHostSlots = 23;
+  void* host_slot_ptr[kHostSlots] = {nullptr};
+  size_t host_slot_bytes[kHostSlots] = {0};
+  // copa_stage_host: copies of host tensors started on copy_stream, oldest first; each
+  // names its slot set (0: [15..18], 1: [19..22]) and the event recorded after its copies
+  struct StagedX {
+    int set = 0;
+    const void* src[4] = {nullptr, nullptr, nullptr, nullptr};
+    int64_t K = -1, J = -1, S = -1, nnz = -1;
+    int vdt = -1;
+  };
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t stage_ev[2] = {nullptr, nullptr};
+  StagedX staged[2];
+  int n_staged = 0;
   bool host_x_valid = false;   // [0..3] hold the X of the last copa_fit_host call
   int64_t host_K = -1, host_J = -1, host_S = -1, host_nnz = -1;
   int host_vdt = -1;

@@ -840,6 +840,61 @@ def test_host_entry_point_follows_a_changed_tensor(P):
     _assert_same_fit(got, ref)
 
 
+def _pinned_host_tensor(X):
+    """The four arrays of X in pinned host memory (so that staged copies run asynchronously)."""
+    torch = pytest.importorskip("torch")
+    Xh = type("Xh", (), {})()
+    Xh.K, Xh.J = X.K, X.J
+    Xh._pin = [torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).pin_memory()
+               for a, dt in ((X.subj_ptr, np.int64), (X.row_ptr, np.int64), (X.col, np.int32),
+                             (X.val, np.float64))]
+    Xh.subj_ptr, Xh.row_ptr, Xh.col, Xh.val = (t.numpy() for t in Xh._pin)
+    return Xh
+
+
+def test_staged_host_copies(P):
+    """copa_stage_host: successive copa_fit_host calls whose tensor copies were started
+    ahead (up to two pending) give the fit of the same calls copying the tensor themselves,
+    with the same set-up launches (the copy taken is compared like an own copy); a staged
+    copy of another tensor is waited for and discarded; a third pending copy is refused."""
+    X, Xr = _same_sizes_other_contents()
+    Xh, Xrh = _pinned_host_tensor(X), _pinned_host_tensor(Xr)
+    R = 8
+    H0, V0, W0 = synth.init_factors(X.K, X.J, R)
+    opt = P.Options(R, n_outer=2, n_inner=5)
+
+    def state():
+        fac = [np.array(a, dtype=np.float64) for a in (H0, V0, W0)]
+        return fac + [np.zeros_like(a) for a in fac]
+
+    def call(h, Xs, st):
+        hist = h.fit_host(Xs, opt, *st, val_dtype="f64")
+        return hist, h.fit_launches()
+
+    # reference: three calls on X, then one on Xr, each copying its tensor itself
+    href, st_ref = P.Copa(0, "fp64"), state()
+    ref = [call(href, Xh, st_ref) for _ in range(3)] + [call(href, Xrh, st_ref)]
+    # staged: the copy of call c + 1 started before call c
+    h, st = P.Copa(0, "fp64"), state()
+    h.stage_host(Xh, "f64")
+    h.stage_host(Xh, "f64")
+    with pytest.raises(P.CopaError) as e:
+        h.stage_host(Xh, "f64")
+    assert e.value.code == P.ERR_INVALID_ARG
+    got = [call(h, Xh, st)]
+    h.stage_host(Xh, "f64")
+    got.append(call(h, Xh, st))
+    got.append(call(h, Xh, st))
+    h.stage_host(Xh, "f64")      # not the tensor of the next call: waited for and discarded
+    got.append(call(h, Xrh, st))
+    assert [g[1] for g in got] == [r[1] for r in ref]
+    for (hg, _), (hr, _) in zip(got, ref):
+        np.testing.assert_allclose(hg, hr, rtol=1e-10, atol=1e-12)
+    for a, b in zip(st, st_ref):
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-9 * max(np.abs(b).max(), 1e-300))
+    assert h._staged == []
+
+
 def test_forget_tensor_after_rewrite_in_place(P):
     """A device tensor rewritten in place keeps its addresses and sizes; after
     forget_tensor() the fit on it equals a fresh handle's. A new DeviceTensor object (which

@@ -477,8 +477,9 @@ def gpu_leg(args, X, init, rank, world):
         if world > 1:
             torch.distributed.barrier()
         # each step's X is copied from pinned host memory inside the timed region: the
-        # first before its step, every later one while the step before it runs
-        # (copa_stage_host); the factors and duals are copied in and out by each call
+        # first by its own call, every later one beside the step before it (queued by
+        # copa_stage_host, issued by that step's call after its own copies); the factors
+        # and duals are copied in and out by each call
         t0 = time.perf_counter()
         h.stage_host(Xh, val_dtype="bf16")
         for s in range(args.e2e_steps):
@@ -495,8 +496,8 @@ def gpu_leg(args, X, init, rank, world):
         out["e2e"] = {"value": 1.0 / dt, "unit": "iter/s", "h2d_bytes_per_step": int(h2d),
                       "d2h_bytes_per_step": int(d2h),
                       "note": "copa_fit_host, one outer iteration per call, X (bf16 counts) and state from "
-                              "pinned host memory; the X of step s+1 is copied (copa_stage_host) while step s "
-                              "runs" + (" (per rank: its shard; max over ranks)" if world > 1 else "")}
+                              "pinned host memory; the X of step s+1 is copied (queued by copa_stage_host) "
+                              "beside step s" + (" (per rank: its shard; max over ranks)" if world > 1 else "")}
     if world > 1:
         h.set_allreduce(None)
     return out, h, P

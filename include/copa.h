@@ -368,19 +368,21 @@ copa_status_t copa_fit_host(copa_handle_t handle, const copa_tensor_t* X_host,
                             void* W_host, void* DH_host, void* DV_host, void* DW_host,
                             double* fit_history_host);
 
-/* Pipelined input for copa_fit_host (no counterpart in the paper): starts the copy of the
- * four arrays of a HOST tensor (pinned memory, or the copy runs synchronously) into
- * device buffers of the handle, on a copy stream of the handle's own, and returns without
- * waiting. The next copa_fit_host call whose X_host names the same four host pointers with
- * the same K, J, S, nnz and val_dtype takes that copy (its stream waits for it) instead of
- * copying X itself, so that the copy for one call runs while the previous call computes.
- * At most two copies are pending; copa_fit_host takes the oldest, or, when its X_host does
- * not match the oldest, waits for every pending copy and discards them. The copy reads the
- * arrays while it runs: the caller must not write them until the copa_fit_host call that
- * takes (or discards) the copy has returned, or the handle is destroyed. A NULL X_host or
- * array, negative sizes, an unknown val_dtype and a third pending copy return
- * COPA_ERR_INVALID_ARG; COPA_ERR_OOM if the buffers cannot be allocated. The contents are
- * checked by the copa_fit_host call that takes the copy, as for its own copies. */
+/* Pipelined input for copa_fit_host (no counterpart in the paper): queues the copy of the
+ * four arrays of a HOST tensor (pinned memory, or the copy is synchronous) into device
+ * buffers of the handle (allocated here) and returns. The next copa_fit_host call issues
+ * the queued copies on a copy stream of the handle's own, behind its own host-to-device
+ * copies, so that they run while its kernels do; a later copa_fit_host call whose X_host
+ * names the same four host pointers with the same K, J, S, nnz and val_dtype as the oldest
+ * queued copy takes it (its stream waits for the copy) instead of copying X itself (if the
+ * oldest was not issued yet, that call copies X itself). At most two copies are queued; a
+ * copa_fit_host call whose X_host does not match the oldest waits for the issued ones and
+ * discards them all. The copy reads the arrays while it runs: the caller must not write
+ * them until the copa_fit_host call that takes (or discards) the copy has returned, or the
+ * handle is destroyed. A NULL X_host or array, negative sizes, an unknown val_dtype and a
+ * third queued copy return COPA_ERR_INVALID_ARG; COPA_ERR_OOM if the buffers cannot be
+ * allocated. The contents are checked by the copa_fit_host call that takes the copy, as
+ * for its own copies. */
 copa_status_t copa_stage_host(copa_handle_t handle, const copa_tensor_t* X_host);
 
 /* Smoothness on U_k (Sec. 3.3.1), set-up step. For every subject, the B-spline basis of

@@ -443,9 +443,10 @@ class Copa:
         return hist[:self.fit_stats(opt.n_outer)[0]]
 
     def stage_host(self, Xh, val_dtype="f32"):
-        """copa_stage_host: start copying a host tensor for the next fit_host call with the
-        same arrays (pinned memory overlaps the copy with the work queued before it). The
-        arrays are kept referenced until that call, and must not be written meanwhile."""
+        """copa_stage_host: queue the copy of a host tensor for a later fit_host call with the
+        same arrays; the next fit_host call issues it beside its own work (pinned memory
+        makes it asynchronous). The arrays are kept referenced until the call that takes or
+        discards the copy, and must not be written meanwhile."""
         tc, keep = host_tensor_c(Xh, val_dtype)
         self._check(_lib.copa_stage_host(self.h, byref(tc)))
         self._staged.append((_tensor_key(tc), keep))

@@ -446,6 +446,7 @@ static void release_ctx(copa_ctx* h, bool own_stream) {
   }
   for (cudaEvent_t e : h->stage_ev)
     if (e) cudaEventDestroy(e);
+  if (h->stage_go) cudaEventDestroy(h->stage_go);
   for (int i = 0; i < copa_ctx::kHostSlots; ++i)
     if (h->host_slot_ptr[i]) cudaFree(h->host_slot_ptr[i]);
   cudaFree(h->d_status);
@@ -1116,7 +1117,7 @@ copa_status_t host_slot(copa_ctx* h, int i, size_t bytes) {
     h->host_slot_bytes[i] = 0;
     if (cudaMalloc(&h->host_slot_ptr[i], bytes + 16) != cudaSuccess) {
       cudaGetLastError();
-      return fail(h, COPA_ERR_OOM, "copa_fit_host: device allocation failed");
+      return fail(h, COPA_ERR_OOM, "device allocation for the copies of host arrays failed");
     }
     h->host_slot_bytes[i] = bytes + 16;
   }
@@ -1128,11 +1129,40 @@ bool staged_matches(const copa_ctx::StagedX& s, const copa_tensor_t* X) {
          s.src[0] == X->subj_ptr && s.src[1] == X->row_ptr && s.src[2] == X->col_idx && s.src[3] == X->vals;
 }
 
-// Waits for every pending staged copy and forgets them (their buffers stay allocated).
+// Waits for every pending staged copy that was issued and forgets them all (their buffers
+// stay allocated).
 copa_status_t drop_staged(copa_ctx* h) {
   for (int q = 0; q < h->n_staged; ++q)
-    TRY(cuda_check(h, cudaEventSynchronize(h->stage_ev[h->staged[q].set]), "cudaEventSynchronize"));
+    if (h->staged[q].issued)
+      TRY(cuda_check(h, cudaEventSynchronize(h->stage_ev[h->staged[q].set]), "cudaEventSynchronize"));
   h->n_staged = 0;
+  return COPA_OK;
+}
+
+// Issues the copies of the pending staged tensors not issued yet, on the copy stream after
+// the work queued so far on the handle's stream (a copa_fit_host call's own copies), so
+// that they take the host link after those and run beside the call's kernels.
+copa_status_t issue_staged(copa_ctx* h) {
+  bool first = true;
+  for (int q = 0; q < h->n_staged; ++q) {
+    copa_ctx::StagedX& e = h->staged[q];
+    if (e.issued) continue;
+    if (first) {
+      TRY(cuda_check(h, cudaEventRecord(h->stage_go, h->stream), "cudaEventRecord"));
+      TRY(cuda_check(h, cudaStreamWaitEvent(h->copy_stream, h->stage_go, 0), "cudaStreamWaitEvent"));
+      first = false;
+    }
+    const size_t vs = e.vdt == COPA_VAL_F64 ? 8 : (e.vdt == COPA_VAL_F32 ? 4 : 2);
+    const size_t sizes[4] = {sizeof(int64_t) * (e.K + 1), sizeof(int64_t) * (e.S + 1), sizeof(int32_t) * e.nnz,
+                             vs * e.nnz};
+    for (int i = 0; i < 4; ++i)
+      if (sizes[i])
+        TRY(cuda_check(h, cudaMemcpyAsync(h->host_slot_ptr[15 + 4 * e.set + i], e.src[i], sizes[i],
+                                          cudaMemcpyHostToDevice, h->copy_stream),
+                       "H2D"));
+    TRY(cuda_check(h, cudaEventRecord(h->stage_ev[e.set], h->copy_stream), "cudaEventRecord"));
+    e.issued = true;
+  }
   return COPA_OK;
 }
 
@@ -1142,9 +1172,11 @@ copa_status_t copa_stage_host(copa_handle_t h, const copa_tensor_t* Xh) {
   CHECK_H(h);
   TRY(set_dev(h));
   TRY(check_tensor_args(h, Xh));
-  if (h->n_staged >= 2) return fail(h, COPA_ERR_INVALID_ARG, "copa_stage_host: two staged copies are pending");
+  if (h->n_staged >= 2) return fail(h, COPA_ERR_INVALID_ARG, "copa_stage_host: two copies are queued already");
   if (!h->copy_stream)
     TRY(cuda_check(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking), "cudaStreamCreate"));
+  if (!h->stage_go)
+    TRY(cuda_check(h, cudaEventCreateWithFlags(&h->stage_go, cudaEventDisableTiming), "cudaEventCreate"));
   // the set that the pending copy (if any) does not use; its buffers are free: a set is
   // reused only after copa_fit_host took its copy (and synchronised) or dropped it
   const int set = h->n_staged == 1 ? 1 - h->staged[0].set : 0;
@@ -1153,17 +1185,10 @@ copa_status_t copa_stage_host(copa_handle_t h, const copa_tensor_t* Xh) {
   size_t sizes[4];
   tensor_bytes(Xh, sizes);
   const void* src[4] = {Xh->subj_ptr, Xh->row_ptr, Xh->col_idx, Xh->vals};
-  for (int i = 0; i < 4; ++i) {
-    const int d = 15 + 4 * set + i;
-    TRY(host_slot(h, d, sizes[i]));
-    if (sizes[i])
-      TRY(cuda_check(h, cudaMemcpyAsync(h->host_slot_ptr[d], src[i], sizes[i], cudaMemcpyHostToDevice,
-                                        h->copy_stream),
-                     "H2D"));
-  }
-  TRY(cuda_check(h, cudaEventRecord(h->stage_ev[set], h->copy_stream), "cudaEventRecord"));
+  for (int i = 0; i < 4; ++i) TRY(host_slot(h, 15 + 4 * set + i, sizes[i]));
   copa_ctx::StagedX& e = h->staged[h->n_staged++];
   e.set = set;
+  e.issued = false;
   for (int i = 0; i < 4; ++i) e.src[i] = src[i];
   e.K = Xh->K;
   e.J = Xh->J;
@@ -1180,21 +1205,24 @@ copa_status_t copa_fit_host(copa_handle_t h, const copa_tensor_t* Xh, const copa
   TRY(set_dev(h));
   if (!Xh) return fail(h, COPA_ERR_INVALID_ARG, "X is NULL");
   // First (before any check can fail, so that a caller can track the pending copies): if
-  // the oldest copy started by copa_stage_host is of this X (same host arrays and sizes),
-  // its buffers become slots 10..13 (the stream waits for its copies) and X is not copied
-  // again; otherwise every pending copy is waited for and discarded.
+  // the oldest copy staged by copa_stage_host is of this X (same host arrays and sizes), it
+  // leaves the queue, and if it was issued, its buffers become slots 10..13 (the stream
+  // waits for its copies) and X is not copied again; otherwise every pending copy is
+  // waited for (where issued) and discarded.
   bool took = false;
   if (h->n_staged > 0) {
     if (staged_matches(h->staged[0], Xh)) {
       const int set = h->staged[0].set;
-      TRY(cuda_check(h, cudaStreamWaitEvent(h->stream, h->stage_ev[set], 0), "cudaStreamWaitEvent"));
-      for (int q = 0; q < 4; ++q) {
-        std::swap(h->host_slot_ptr[10 + q], h->host_slot_ptr[15 + 4 * set + q]);
-        std::swap(h->host_slot_bytes[10 + q], h->host_slot_bytes[15 + 4 * set + q]);
+      if (h->staged[0].issued) {   // not issued yet: this call copies X itself
+        TRY(cuda_check(h, cudaStreamWaitEvent(h->stream, h->stage_ev[set], 0), "cudaStreamWaitEvent"));
+        for (int q = 0; q < 4; ++q) {
+          std::swap(h->host_slot_ptr[10 + q], h->host_slot_ptr[15 + 4 * set + q]);
+          std::swap(h->host_slot_bytes[10 + q], h->host_slot_bytes[15 + 4 * set + q]);
+        }
+        took = true;
       }
       h->staged[0] = h->staged[1];
       --h->n_staged;
-      took = true;
     } else {
       TRY(drop_staged(h));
     }
@@ -1226,6 +1254,7 @@ copa_status_t copa_fit_host(copa_handle_t h, const copa_tensor_t* Xh, const copa
       TRY(cuda_check(h, cudaMemcpyAsync(h->host_slot_ptr[d], src[i], sizes[i], cudaMemcpyHostToDevice, h->stream),
                      "H2D"));
   }
+  TRY(issue_staged(h));   // the next calls' tensors, behind this call's own copies
   bool same = h->host_x_valid && h->host_K == Xh->K && h->host_J == Xh->J && h->host_S == Xh->S &&
               h->host_nnz == Xh->nnz && h->host_vdt == Xh->val_dtype;
   for (int i = 0; i < 4 && same; ++i) same = h->host_slot_bytes[i] >= sizes[i] + 16;

@@ -122,16 +122,19 @@ struct copa_ctx {
   static constexpr int kHostSlots = 23;
   void* host_slot_ptr[kHostSlots] = {nullptr};
   size_t host_slot_bytes[kHostSlots] = {0};
-  // copa_stage_host: copies of host tensors started on copy_stream, oldest first; each
-  // names its slot set (0: [15..18], 1: [19..22]) and the event recorded after its copies
+  // copa_stage_host: pending copies of host tensors, oldest first; each names its slot set
+  // (0: [15..18], 1: [19..22]) and, once issued on copy_stream, has stage_ev[set] recorded
+  // after its copies
   struct StagedX {
     int set = 0;
+    bool issued = false;
     const void* src[4] = {nullptr, nullptr, nullptr, nullptr};
     int64_t K = -1, J = -1, S = -1, nnz = -1;
     int vdt = -1;
   };
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t stage_ev[2] = {nullptr, nullptr};
+  cudaEvent_t stage_go = nullptr;   // recorded on `stream` after a copa_fit_host call's own copies
   StagedX staged[2];
   int n_staged = 0;
   bool host_x_valid = false;   // [0..3] hold the X of the last copa_fit_host call

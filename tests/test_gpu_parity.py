@@ -853,10 +853,11 @@ def _pinned_host_tensor(X):
 
 
 def test_staged_host_copies(P):
-    """copa_stage_host: successive copa_fit_host calls whose tensor copies were started
-    ahead (up to two pending) give the fit of the same calls copying the tensor themselves,
-    with the same set-up launches (the copy taken is compared like an own copy); a staged
-    copy of another tensor is waited for and discarded; a third pending copy is refused."""
+    """copa_stage_host: successive copa_fit_host calls whose tensor copies were queued
+    ahead (up to two; each issued by the call before the one that takes it, or copied by
+    that call if none came between) give the fit of the same calls copying the tensor
+    themselves, with the same set-up launches (the copy taken is compared like an own
+    copy); a queued copy of another tensor is discarded; a third queued copy is refused."""
     X, Xr = _same_sizes_other_contents()
     Xh, Xrh = _pinned_host_tensor(X), _pinned_host_tensor(Xr)
     R = 8
@@ -874,7 +875,7 @@ def test_staged_host_copies(P):
     # reference: three calls on X, then one on Xr, each copying its tensor itself
     href, st_ref = P.Copa(0, "fp64"), state()
     ref = [call(href, Xh, st_ref) for _ in range(3)] + [call(href, Xrh, st_ref)]
-    # staged: the copy of call c + 1 started before call c
+    # staged: the copy for call c + 1 queued before call c, which issues it
     h, st = P.Copa(0, "fp64"), state()
     h.stage_host(Xh, "f64")
     h.stage_host(Xh, "f64")
@@ -885,7 +886,7 @@ def test_staged_host_copies(P):
     h.stage_host(Xh, "f64")
     got.append(call(h, Xh, st))
     got.append(call(h, Xh, st))
-    h.stage_host(Xh, "f64")      # not the tensor of the next call: waited for and discarded
+    h.stage_host(Xh, "f64")      # not the tensor of the next call: discarded
     got.append(call(h, Xrh, st))
     assert [g[1] for g in got] == [r[1] for r in ref]
     for (hg, _), (hr, _) in zip(got, ref):
